@@ -1,0 +1,426 @@
+"""Pins for the FP64 CPU oracle: closed forms, brute force, library routines and
+invariants that do not come from the oracle itself.
+
+Each test targets a plausible mistake (dropped term, wrong sign, wrong index,
+transposed axis) in one oracle function.  Sizes are small so the whole file
+runs in well under a minute.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_24543_gb300 import inputs as I
+
+
+def _prm(g=((0, 0), (0, 0)), gdd=((0, 0), (0, 0)), kappa=0.0, eta_s=1.0, nodes=32, trap=(1, 1, 1)):
+    return O.Params(np.array(g, float), np.array(gdd, float), kappa, eta_s, nodes, trap)
+
+
+# ---------------------------------------------------------------- transforms
+def test_fft_convention_matches_brute_force_dft():
+    """numpy's 3D transform over (z,y,x) equals the O(N^2) DFT sum with x fastest."""
+    nz, ny, nx = 3, 4, 5
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal((nz, ny, nx)) + 1j * rng.standard_normal((nz, ny, nx))
+    F = np.zeros_like(f)
+    for kz in range(nz):
+        for ky in range(ny):
+            for kx in range(nx):
+                acc = 0j
+                for z in range(nz):
+                    for y in range(ny):
+                        for x in range(nx):
+                            acc += f[z, y, x] * np.exp(-2j * np.pi * (kx * x / nx + ky * y / ny + kz * z / nz))
+                F[kz, ky, kx] = acc
+    assert np.max(np.abs(O.egpe.dft(f) - F)) < 1e-12
+    assert np.max(np.abs(O.egpe.idft(F) - f)) < 1e-13
+
+
+def test_parseval():
+    g = O.Grid((8, 6, 10), (3.0, 2.0, 4.0))
+    f = I.random_fields(g.shape, 3)
+    lhs = O.inner(g, f, f).real
+    rhs = g.dV / g.N * np.sum(np.abs(O.egpe.dft(f)) ** 2)
+    assert abs(lhs - rhs) < 1e-12 * lhs
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_kinetic_plane_wave(axis):
+    """T exp(i k.x) = |k|^2/2 exp(i k.x) on a non-cubic grid, for each axis and the
+    Nyquist mode (pins the wavenumber convention and axis order)."""
+    g = O.Grid((8, 12, 16), (2.0, 3.0, 5.0))
+    X = [g.x[0][None, None, :], g.x[1][None, :, None], g.x[2][:, None, None]]
+    for m in (1, 3, g.n[axis] // 2):
+        k = math.pi / g.L[axis] * m
+        f = np.exp(1j * k * X[axis]) * np.ones(g.shape)
+        Tf = O.kinetic_apply(g, f)
+        assert np.max(np.abs(Tf - 0.5 * k * k * f)) < 1e-10 * max(1.0, k * k)
+
+
+# ---------------------------------------------------------------- harmonic closed forms
+def _harmonic_gs(g, trap):
+    X = [g.x[0][None, None, :], g.x[1][None, :, None], g.x[2][:, None, None]]
+    G = np.ones(g.shape)
+    for a in range(3):
+        G = G * (trap[a] / np.pi) ** 0.25 * np.exp(-0.5 * trap[a] * X[a] ** 2)
+    return np.stack([G, G]).astype(np.complex128)
+
+
+def test_harmonic_energy_terms_closed_form():
+    """Non-interacting Gaussian: E_kin = E_trap = sum_a lambda_a/4 per component,
+    mu_i = sum_a lambda_a/2 and H psi = mu psi (Sec. II trap, Eq. 1)."""
+    trap = (1.0, 1.5, 2.0)
+    g = O.Grid((48, 56, 64), (8.0, 8.0, 8.0))
+    psi = _harmonic_gs(g, trap)
+    ev = O.evaluate(g, _prm(trap=trap), psi)
+    q = sum(trap) / 4.0
+    assert abs(ev.terms["kin1"] - q) < 1e-12 and abs(ev.terms["kin2"] - q) < 1e-12
+    assert abs(ev.terms["trap"] - 2 * q) < 1e-12
+    assert abs(ev.E - 4 * q) < 1e-12
+    assert np.allclose(ev.mu, 2 * q, atol=1e-12, rtol=0)
+    assert np.max(np.abs(ev.Hpsi - 2 * q * psi)) < 1e-10
+
+
+def test_ncg_reaches_harmonic_ground_state():
+    """g = g_dd = kappa = 0: NCG from a noisy start reaches E = sum_i (lx+ly+lz)/2 = 4."""
+    trap = (1.0, 1.0, 2.0)
+    # h_x = 0.39, h_z = 0.25: spectral and truncation errors of the Gaussian < 1e-13
+    w = I.Workload("h", (36, 36, 48), (7.0, 7.0, 6.0), trap, ((0, 0), (0, 0)), ((0, 0), (0, 0)), 0.0, 11)
+    g = O.Grid(w.n, w.L)
+    psi0 = I.gaussian_start(w, noise=0.05)
+    psi, rep = O.ncg_solve(g, _prm(trap=trap, nodes=1), psi0,
+                           O.SolveOpts(precond="kinetic+diagonal", tol_res=1e-9))
+    assert rep["status"] == "converged"
+    assert abs(rep["E"] - 4.0) < 1e-12
+    assert np.allclose(rep["mu"], 2.0, atol=1e-9, rtol=0)
+
+
+# ---------------------------------------------------------------- dipolar kernel
+@pytest.mark.parametrize("axis,mult", [(2, 2.0), (0, -1.0), (1, -1.0)])
+def test_dipolar_plane_wave_multiplier(axis, mult):
+    """A density modulated along z sees +2 g_dd, along x or y -g_dd (3cos^2-1 with
+    dipoles along z); the uniform part has no dipolar potential (K(0) = 0)."""
+    g = O.Grid((8, 10, 12), (3.0, 4.0, 5.0))
+    X = [g.x[0][None, None, :], g.x[1][None, :, None], g.x[2][:, None, None]]
+    k = math.pi / g.L[axis] * 2
+    n1 = 0.7 + 0.1 * np.cos(k * X[axis]) * np.ones(g.shape)
+    n2 = 0.2 * np.ones(g.shape)
+    gdd = np.array([[300.0, 120.0], [120.0, 50.0]])
+    Phi = O.dipolar_potentials(g, _prm(gdd=gdd), np.stack([n1, n2]))
+    for i in range(2):
+        expect = gdd[i, 0] * mult * 0.1 * np.cos(k * X[axis]) * np.ones(g.shape)
+        assert np.max(np.abs(Phi[i] - expect)) < 1e-11
+
+
+def test_dipolar_oblique_wave():
+    """k along (1,0,1)/sqrt2: 3cos^2(45deg)-1 = 1/2."""
+    g = O.Grid((8, 8, 8), (4.0, 4.0, 4.0))
+    X = [g.x[0][None, None, :], g.x[1][None, :, None], g.x[2][:, None, None]]
+    k = math.pi / 4.0 * 2
+    n1 = 1.0 + 0.3 * np.cos(k * (X[0] + X[2]))
+    n = np.stack([n1 * np.ones(g.shape), np.zeros(g.shape)])
+    Phi = O.dipolar_potentials(g, _prm(gdd=((100.0, 0), (0, 0))), n)
+    assert np.max(np.abs(Phi[0] - 100.0 * 0.5 * 0.3 * np.cos(k * (X[0] + X[2])))) < 1e-11
+
+
+def test_isotropic_density_on_cubic_grid_has_zero_dipolar_energy():
+    """Cubic symmetry of the lattice sum: sum_k (3kz^2/k^2 - 1)|n^(k)|^2 = 0."""
+    g = O.Grid((16, 16, 16), (6.0, 6.0, 6.0))
+    X = [g.x[0][None, None, :], g.x[1][None, :, None], g.x[2][:, None, None]]
+    G = np.exp(-0.5 * (X[0] ** 2 + X[1] ** 2 + X[2] ** 2))
+    psi = np.stack([G, 0.5 * G]).astype(np.complex128)
+    ev = O.evaluate(g, _prm(gdd=((300.0, 200.0), (200.0, 100.0)), trap=(1, 1, 1)), psi)
+    assert abs(ev.terms["dipolar"]) < 1e-12 * abs(ev.terms["kin1"]) * 300
+
+
+# ---------------------------------------------------------------- LHY
+def test_lhy_without_dipoles_is_node_independent_and_matches_eigenvalues():
+    """g_dd = 0: eta does not depend on u, so any Q gives the same F; and
+    V_+- = 2 * eigenvalues of [[g11 n1, g12 sqrt(n1 n2)], [g12 sqrt(n1 n2), g22 n2]]."""
+    rng = np.random.default_rng(4)
+    n1 = rng.uniform(0.0, 0.3, 50)
+    n2 = rng.uniform(0.0, 0.3, 50)
+    g = np.array([[400.0, 380.0], [380.0, 300.0]])
+    F32, m1, m2 = O.lhy_density_and_mu(_prm(g=g, kappa=1.3, eta_s=2.0, nodes=32), n1, n2)
+    F1, _, _ = O.lhy_density_and_mu(_prm(g=g, kappa=1.3, eta_s=2.0, nodes=1), n1, n2)
+    assert np.max(np.abs(F32 - F1)) < 1e-12 * np.max(np.abs(F32))
+    ref = np.empty_like(n1)
+    for k in range(len(n1)):
+        M = np.array([[g[0, 0] * n1[k], g[0, 1] * math.sqrt(n1[k] * n2[k])],
+                      [g[0, 1] * math.sqrt(n1[k] * n2[k]), g[1, 1] * n2[k]]])
+        lam = np.linalg.eigvalsh(M)
+        ref[k] = 1.3 * 2.0 ** -2.5 * sum(max(2 * l, 0.0) ** 2.5 for l in lam)
+    assert np.max(np.abs(F32 - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def _q5_closed_form(eps):
+    """int_0^1 (1 + eps (3u^2 - 1))^{5/2} du, 0 < eps < 1, by the standard reduction
+    of int (a + b u^2)^{m/2} du (a = 1 - eps, b = 3 eps)."""
+    a, b = 1.0 - eps, 3.0 * eps
+    f = lambda m: (a + b) ** (m / 2.0)  # value of (a + b u^2)^{m/2} at u = 1
+    I1 = math.asinh(math.sqrt(b / a)) / math.sqrt(b)          # int du / sqrt(a + b u^2)
+    I_half = f(1) / 2.0 + a / 2.0 * I1                         # int (a+bu^2)^{1/2}
+    I_3half = f(3) / 4.0 + 3.0 * a / 4.0 * I_half              # int (a+bu^2)^{3/2}
+    return f(5) / 6.0 + 5.0 * a / 6.0 * I_3half                # int (a+bu^2)^{5/2}
+
+
+@pytest.mark.parametrize("eps", [0.2, 0.5, 0.75, 0.9])
+def test_lhy_single_component_closed_form(eps):
+    """n2 = 0: V_+ = 2 eta11 n1, so F = C (2 g n)^{5/2} int_0^1 (1+eps(3u^2-1))^{5/2} du,
+    and (when g11 = g22, kappa = 2c/5, eta_s = g11+g22) mu = c n^{3/2} Q5(eps)."""
+    g11 = 400.0
+    gdd = eps * g11
+    c = 50.0
+    prm = _prm(g=((g11, 123.0), (123.0, g11)), gdd=((gdd, 77.0), (77.0, 9.0)),
+               kappa=0.4 * c, eta_s=2 * g11, nodes=32)
+    n1 = np.array([0.01, 0.1, 0.25])
+    F, m1, _ = O.lhy_density_and_mu(prm, n1, np.zeros(3))
+    q5 = _q5_closed_form(eps)
+    assert np.allclose(F, 0.4 * c * (2 * g11) ** -2.5 * (2 * g11 * n1) ** 2.5 * q5, rtol=1e-13, atol=0)
+    assert np.allclose(m1, c * n1 ** 1.5 * q5, rtol=1e-13, atol=0)
+
+
+def test_lhy_mu_is_derivative_of_density():
+    rng = np.random.default_rng(7)
+    n1 = rng.uniform(0.02, 0.3, 40)
+    n2 = rng.uniform(0.02, 0.3, 40)
+    prm = _prm(g=((300, 280), (280, 300)), gdd=((420, 400), (400, 420)), kappa=40.0, eta_s=600.0)
+    F, m1, m2 = O.lhy_density_and_mu(prm, n1, n2)
+    h = 1e-6
+    fd1 = (O.lhy_density_and_mu(prm, n1 + h, n2)[0] - O.lhy_density_and_mu(prm, n1 - h, n2)[0]) / (2 * h)
+    fd2 = (O.lhy_density_and_mu(prm, n1, n2 + h)[0] - O.lhy_density_and_mu(prm, n1, n2 - h)[0]) / (2 * h)
+    assert np.max(np.abs(fd1 - m1)) < 1e-7 * np.max(np.abs(m1))
+    assert np.max(np.abs(fd2 - m2)) < 1e-7 * np.max(np.abs(m2))
+
+
+def test_lhy_quadrature_against_adaptive_integral():
+    """For smooth integrands (all V > 0) the 32-node rule matches scipy.quad."""
+    from scipy.integrate import quad
+    g = np.array([[300.0, 100.0], [100.0, 300.0]])
+    gdd = np.array([[120.0, 40.0], [40.0, 120.0]])
+    prm = _prm(g=g, gdd=gdd, kappa=1.0, eta_s=1.0, nodes=32)
+    n1, n2 = 0.2, 0.1
+
+    def integrand(u):
+        e = g + gdd * (3 * u * u - 1)
+        d = e[0, 0] * n1 - e[1, 1] * n2
+        s = math.sqrt(d * d + 4 * e[0, 1] * e[1, 0] * n1 * n2)
+        A = e[0, 0] * n1 + e[1, 1] * n2
+        return max(A + s, 0) ** 2.5 + max(A - s, 0) ** 2.5
+    ref = quad(integrand, 0.0, 1.0, epsabs=0, epsrel=1e-13)[0]
+    F, _, _ = O.lhy_density_and_mu(prm, np.array([n1]), np.array([n2]))
+    assert abs(F[0] - ref) < 1e-12 * ref
+
+
+# ---------------------------------------------------------------- gradient and line search
+def _full_params():
+    return _prm(g=((400, 250), (250, 380)), gdd=((300, 280), (280, 260)), kappa=20.0, eta_s=780.0,
+                nodes=16, trap=(1.0, 1.3, 2.0))
+
+
+def test_gradient_matches_finite_differences():
+    """d/de E(psi + e phi) = 2 sum_i Re<phi_i, H_i psi_i> with every term on (8^3, complex)."""
+    n, L = (8, 8, 8), (3.0, 3.5, 2.5)
+    g = O.Grid(n, L)
+    prm = _full_params()
+    psi = I.random_state(n, L, 5)
+    phi = I.random_fields(psi.shape, 6, scale=0.1)
+    _, _, H = O.energy_grad(g, prm, psi)
+    eps = 1e-5
+    fd = (O.evaluate(g, prm, psi + eps * phi).E - O.evaluate(g, prm, psi - eps * phi).E) / (2 * eps)
+    an = 2 * sum(O.inner(g, phi[i], H[i]).real for i in range(2))
+    assert abs(fd - an) < 1e-9 * abs(an)
+
+
+def test_chemical_potential_and_tangent_residual():
+    n, L = (8, 8, 8), (3.0, 3.0, 3.0)
+    g = O.Grid(n, L)
+    psi = I.random_state(n, L, 8)
+    ev = O.evaluate(g, _full_params(), psi)
+    for i in range(2):
+        r = ev.Hpsi[i] - ev.mu[i] * psi[i]
+        assert abs(O.inner(g, r, psi[i]).real) < 1e-12 * abs(ev.mu[i])
+
+
+def test_line_coefficients_match_exact_geodesic():
+    """E' and E'' (Sec. V formulas) against central differences of E along
+    psi_i(alpha) = cos(alpha||p_i||) psi_i + sin(alpha||p_i||) p_i/||p_i||."""
+    n, L = (8, 8, 8), (3.0, 3.0, 3.0)
+    g = O.Grid(n, L)
+    prm = _full_params()
+    psi = I.random_state(n, L, 5)
+    p = O.project(g, psi, I.raw_direction(n, L, 7))
+    E0, Ep, Epp = O.line_coeffs(g, prm, psi, p)
+    pn = np.array([math.sqrt(O.inner(g, p[i], p[i]).real) for i in range(2)])
+
+    def E(a):
+        return O.evaluate(g, prm, O.retract(g, psi, p, a * pn)).E
+    def d1(h):
+        return (E(h) - E(-h)) / (2 * h)
+
+    def d2(h):
+        return (E(h) - 2 * E0 + E(-h)) / (h * h)
+    h = 2e-3  # Richardson extrapolation of the central differences: O(h^4)
+    fd1 = (4 * d1(h / 2) - d1(h)) / 3
+    fd2 = (4 * d2(h / 2) - d2(h)) / 3
+    assert abs(fd1 - Ep) < 1e-8 * abs(Ep)
+    assert abs(fd2 - Epp) < 1e-7 * abs(Epp)
+
+
+def test_line_coefficients_cross_terms_needed():
+    """Swapping the roles of the components (w_ij acting on psi_i) leaves E'' unchanged:
+    the mixture's cross terms are symmetric under relabelling 1 <-> 2."""
+    n, L = (8, 8, 8), (3.0, 3.0, 3.0)
+    g = O.Grid(n, L)
+    prm = _full_params()
+    psi = I.random_state(n, L, 15)
+    p = O.project(g, psi, I.raw_direction(n, L, 16))
+    a = O.line_coeffs(g, prm, psi, p)
+    prm_sw = O.Params(prm.g[::-1, ::-1], prm.gdd[::-1, ::-1], prm.kappa, prm.eta_s, prm.nodes, prm.trap)
+    b = O.line_coeffs(g, prm_sw, psi[::-1].copy(), p[::-1].copy())
+    assert np.allclose(a, b, rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------- manifold
+def test_retraction_projection_preserve_manifold():
+    n, L = (8, 8, 8), (3.0, 3.0, 3.0)
+    g = O.Grid(n, L)
+    psi = I.random_state(n, L, 21)
+    p = O.project(g, psi, I.raw_direction(n, L, 22))
+    for i in range(2):
+        assert abs(O.inner(g, p[i], psi[i]).real) < 1e-14
+    out = O.retract(g, psi, p, [0.3, 1.1])
+    for i in range(2):
+        assert abs(O.inner(g, out[i], out[i]).real - 1.0) < 1e-14
+    # exact geodesic without the renormalisation already has unit norm
+    pn = math.sqrt(O.inner(g, p[0], p[0]).real)
+    q = math.cos(0.3) * psi[0] + math.sin(0.3) * p[0] / pn
+    assert abs(O.inner(g, q, q).real - 1.0) < 1e-13
+
+
+def test_preconditioners_are_positive():
+    """Re<r, P^{-1} r> > 0 for every mode (descent direction) on a random residual,
+    and P_Delta acts on a plane wave as 1/(alpha + |k|^2/2)."""
+    w = I.PRESETS["c1"]
+    n, L = (16, 16, 16), w.L
+    g = O.Grid(n, L)
+    prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, 8, w.trap)
+    psi = I.random_state(n, L, 30, width=(2.0, 2.0, 1.0))
+    ev = O.evaluate(g, prm, psi)
+    r = np.stack([ev.Hpsi[i] - ev.mu[i] * psi[i] for i in range(2)])
+    for mode in O.PRECOND_MODES:
+        z = O.precondition(g, prm, ev, psi, r, mode)
+        assert sum(O.inner(g, r[i], z[i]).real for i in range(2)) > 0
+    alpha = np.abs(O.preconditioner_shift(g, ev, psi))
+    assert np.all(alpha > 0)
+    k = math.pi / L[2] * 3
+    wave = np.exp(1j * k * g.x[2][:, None, None]) * np.ones(g.shape)
+    z = O.precondition(g, prm, ev, psi, np.stack([wave, wave]), "kinetic")
+    for i in range(2):
+        assert np.max(np.abs(z[i] - wave / (alpha[i] + 0.5 * k * k))) < 1e-13
+
+
+# ---------------------------------------------------------------- solver invariants
+@pytest.fixture(scope="module")
+def c1_small():
+    """C1 physics on 16^3 (same box): cheap enough for solver invariants."""
+    w = I.PRESETS["c1"]
+    g = O.Grid((16, 16, 16), w.L)
+    prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, 16, w.trap)
+    ww = I.Workload("c1/16", (16, 16, 16), w.L, w.trap, w.g, w.gdd, w.lhy_c, w.seed)
+    return g, prm, I.gaussian_start(ww)
+
+
+def test_ncg_monotone_descent_and_norms(c1_small):
+    g, prm, psi0 = c1_small
+    tr = []
+    opts = O.SolveOpts(precond="kinetic+diagonal", tol_res=1e-9)
+    psi, rep = O.ncg_solve(g, prm, psi0, opts, trace=tr)
+    assert rep["status"] == "converged"
+    tau = opts.accept_rtol * abs(tr[0]["E"])
+    for t in tr:
+        assert t["E_new"] <= t["E"] + tau
+    for i in range(2):
+        assert abs(O.inner(g, psi[i], psi[i]).real - 1.0) < 1e-13
+
+
+def test_ncg_all_preconditioners_same_minimum(c1_small):
+    g, prm, psi0 = c1_small
+    Es = []
+    for mode in O.PRECOND_MODES:
+        _, rep = O.ncg_solve(g, prm, psi0, O.SolveOpts(precond=mode, tol_res=1e-9))
+        assert rep["status"] == "converged", mode
+        Es.append(rep["E"])
+    assert max(Es) - min(Es) < 1e-11 * abs(Es[0])
+
+
+def test_symmetric_mixture_keeps_components_equal():
+    """Symmetric couplings and psi1 = psi2 at the start give psi1 = psi2 throughout;
+    swapping the components leaves E unchanged."""
+    w = I.PRESETS["c1"]
+    g = O.Grid((16, 16, 16), w.L)
+    prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, 16, w.trap)
+    ww = I.Workload("sym", (16, 16, 16), w.L, w.trap, w.g, w.gdd, w.lhy_c, 3)
+    psi0 = I.gaussian_start(ww)
+    psi0[1] = psi0[0]
+    psi, rep = O.ncg_solve(g, prm, psi0, O.SolveOpts(precond="kinetic", tol_res=1e-8, max_iter=60))
+    assert np.max(np.abs(psi[0] - psi[1])) < 1e-12
+    a = O.evaluate(g, prm, I.random_state((16, 16, 16), w.L, 9)).E
+    b = O.evaluate(g, prm, I.random_state((16, 16, 16), w.L, 9)[::-1].copy()).E
+    assert abs(a - b) < 1e-12 * abs(a)
+
+
+def test_virial_identity_at_ground_state(c1_small):
+    """Scaling psi -> lambda^{3/2} psi(lambda r) gives, at a minimiser,
+    2 E_kin - 2 E_trap + 3 (E_c + E_dd) + 9/2 E_LHY = 0 (up to discretisation)."""
+    w = I.PRESETS["c1"]
+    g = O.Grid((32, 32, 48), w.L)
+    prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, 16, w.trap)
+    ww = I.Workload("vir", g.n, w.L, w.trap, w.g, w.gdd, w.lhy_c, 5)
+    psi, rep = O.ncg_solve(g, prm, I.gaussian_start(ww), O.SolveOpts(precond="kinetic+diagonal", tol_res=1e-8))
+    t = rep["terms"]
+    vir = 2 * (t["kin1"] + t["kin2"]) - 2 * t["trap"] + 3 * (t["contact"] + t["dipolar"]) + 4.5 * t["lhy"]
+    scale = 2 * (t["kin1"] + t["kin2"]) + 2 * t["trap"] + 3 * (t["contact"] + abs(t["dipolar"])) + 4.5 * t["lhy"]
+    assert abs(vir) < 2e-3 * scale
+
+
+def test_ite_and_ncg_reach_the_same_minimum():
+    """Strang ITE has an O(dtau^2) fixed-point bias: Richardson-extrapolate two
+    step sizes and compare with the NCG minimum."""
+    w = I.Workload("ite", (16, 16, 16), (6.0, 6.0, 6.0), (1.0, 1.0, 2.0), ((60, 30), (30, 50)),
+                   ((40, 30), (30, 40)), 5.0, 12)
+    g = O.Grid(w.n, w.L)
+    prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, 8, w.trap)
+    psi0 = I.gaussian_start(w)
+    _, rep = O.ncg_solve(g, prm, psi0, O.SolveOpts(precond="kinetic", tol_res=1e-10))
+    E_cg = rep["E"]
+    Es = []
+    for dt in (0.02, 0.01):
+        _, r = O.ite_solve(g, prm, psi0, dtau=dt, tol_dE=1e-13, max_steps=20000)
+        Es.append(r["E"])
+    E_extrap = (4 * Es[1] - Es[0]) / 3
+    assert Es[1] >= E_cg - 1e-12
+    assert abs(E_extrap - E_cg) < 0.05 * abs(Es[1] - E_cg) + 1e-9
+
+
+# ---------------------------------------------------------------- stored regression values
+def test_oracle_matches_stored_c1_values():
+    """The oracle's C1 numbers stored by tests/golden/make_golden.py (oracle only)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_c1.json")) as f:
+        gold = json.load(f)
+    w = I.PRESETS["c1"]
+    g = O.Grid(w.n, w.L)
+    prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
+    psi = I.gaussian_start(w)
+    ev = O.evaluate(g, prm, psi)
+    assert abs(ev.E - gold["initial"]["E"]) < 1e-12 * abs(ev.E)
+    for k, v in gold["initial"]["terms"].items():
+        assert abs(ev.terms[k] - v) < 1e-12 * max(1.0, abs(v))
+    p = O.project(g, psi, I.raw_direction(w.n, w.L, gold["line_coeffs"]["direction_seed"]))
+    E0, Ep, Epp = O.line_coeffs(g, prm, psi, p, ev)
+    assert abs(Ep - gold["line_coeffs"]["Ep"]) < 1e-11 * abs(Ep)
+    assert abs(Epp - gold["line_coeffs"]["Epp"]) < 1e-11 * abs(Epp)
