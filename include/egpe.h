@@ -1,0 +1,223 @@
+/*
+ * egpe.h -- C ABI of the GB300 (sm_103a) eGPE ground-state solver hot path.
+ *
+ * The library evaluates and minimises the extended Gross-Pitaevskii energy of
+ * a two-component dipolar Bose-Einstein condensate with Lee-Huang-Yang (LHY)
+ * correction (arXiv:2510.24543, Eq. 1) on a periodic 3D grid, with the
+ * preconditioned nonlinear conjugate-gradient method of its Algorithm 1.
+ * Every step runs in hand-written CUDA kernels (Stockham FFTs fused with the
+ * k-space multiplies, fused pointwise passes, deterministic FP64 reductions,
+ * an on-device controller).  No cuFFT and no host fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Fields:  psi = (psi_1, psi_2) is one contiguous array of 2 complex fields,
+ *          shape (2, nz, ny, nx), x fastest, interleaved (re, im).  Element
+ *          type: complex128 (double2) for EGPE_FP64 and EGPE_MIXED handles,
+ *          complex64 (float2) for EGPE_FP32 handles.  All field pointers are
+ *          DEVICE pointers on the handle's device unless stated otherwise;
+ *          the caller owns them; the library never frees them.
+ * Grid:    periodic box [-L_a, L_a) with n_a points per axis, h_a = 2L_a/n_a,
+ *          x_a[j] = -L_a + j h_a; wavenumbers k_a[j] = (pi/L_a)(j or j - n_a).
+ *          Supported n_a: 8, 16, 32, 64, 128, 256.
+ * Product: <a, b> = dV sum conj(a) b, dV = hx hy hz.
+ * Model:   per-particle normalised couplings (N_i -> 1 in Eq. 1):
+ *          E = sum_i <psi_i, T psi_i> + int V (n1+n2) + 1/2 int sum_ij g_ij n_i n_j
+ *            + 1/2 int sum_i n_i Phi_i + int F_LHY,
+ *          T = -Laplacian/2 (spectral), V = 1/2 sum_a trap_a^2 x_a^2,
+ *          Phi_i = IDFT( gdd-kernel * DFT(sum_j gdd_ij n_j) ) with the k-space
+ *          kernel gdd_ij (3 kz^2/|k|^2 - 1) and zero at k = 0 (dipoles along z),
+ *          F_LHY = kappa eta_s^{-5/2} sum_q w_q sum_+- max(V_+-(u_q), 0)^{5/2}
+ *          over a Q-point Gauss-Legendre rule on u in [0,1], with
+ *          V_+- = eta11 n1 + eta22 n2 +- sqrt(delta^2 + 4 eta12 eta21 n1 n2),
+ *          eta_ij(u) = g_ij + gdd_ij (3u^2 - 1)   (Sec. II, LHY branch potentials).
+ * Gradient: H_i psi_i = T psi_i + (V + sum_j g_ij n_j + Phi_i + mu_LHY^(i)) psi_i
+ *          (the coupled eGPE of Sec. II), so that
+ *          d/de E(psi + e phi) = 2 sum_i Re <phi_i, H_i psi_i>.
+ * Errors:  every function returns a status code; nothing aborts or throws.
+ *          Arguments are validated before any launch (EGPE_ERR_INVALID_ARG).
+ *          CUDA failures map to EGPE_ERR_CUDA (see egpe_last_error()).
+ * Streams: all work is enqueued on the stream given to egpe_create; calls that
+ *          return host scalars synchronise that stream before returning.
+ */
+#ifndef EGPE_H
+#define EGPE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EGPE_OK = 0,
+  EGPE_ERR_INVALID_ARG = 1,
+  EGPE_ERR_CUDA = 2,
+  EGPE_ERR_OOM = 3,
+  EGPE_ERR_NONFINITE = 4,
+  EGPE_ERR_NOT_CONVERGED = 5,
+  EGPE_ERR_STAGNATED = 6,
+  EGPE_ERR_TIMEOUT = 7,
+  EGPE_ERR_UNSUPPORTED = 8
+} egpe_status;
+
+typedef enum { EGPE_FP64 = 0, EGPE_FP32 = 1, EGPE_MIXED = 2 } egpe_precision;
+
+/* Preconditioner modes (Sec. IV.B). */
+enum {
+  EGPE_PRECOND_NONE = 0,            /* z = r                                  */
+  EGPE_PRECOND_KINETIC = 1,         /* z = P_Delta^{-1} r                     */
+  EGPE_PRECOND_DIAGONAL = 2,        /* z = P_V^{-1} r                         */
+  EGPE_PRECOND_KINETIC_DIAGONAL = 3 /* z = P_Delta^{-1} P_V^{-1} r (formula order) */
+};
+
+/* Periodic box [-L_a, L_a), n_a points per axis (a = x, y, z). */
+typedef struct {
+  int n[3];
+  double L[3];
+} egpe_grid;
+
+/* Couplings of Eq. 1 in per-particle normalised form. g and gdd must be
+ * symmetric; gdd is the k-space dipolar coefficient. lhy_nodes in [1, 64]. */
+typedef struct {
+  double g[2][2];
+  double gdd[2][2];
+  double lhy_kappa;      /* kappa; the paper's literal prefactor is sqrt(2)/(15 pi^2) */
+  double lhy_eta_scale;  /* eta_s > 0 (1 for the literal form)                       */
+  int lhy_nodes;         /* Q                                                         */
+  double trap[3];        /* (lambda_x, lambda_y, lambda_z)                            */
+} egpe_params;
+
+/* Energy terms and scalars of one evaluation (all FP64). */
+typedef struct {
+  double E;              /* total energy, Eq. 1                          */
+  double kin[2];         /* Re <psi_i, T psi_i> (Parseval)               */
+  double trap;           /* int V (n1 + n2)                              */
+  double contact;        /* 1/2 int sum_ij g_ij n_i n_j                  */
+  double dipolar;        /* 1/2 int sum_i n_i Phi_i                      */
+  double lhy;            /* int F_LHY                                    */
+  double mu[2];          /* mu_i = Re <psi_i, H_i psi_i> (Sec. III)      */
+  double norm2[2];       /* ||psi_i||^2                                  */
+  double shift[2];       /* alpha_i = mu_i - Re <psi_i, Phi_i psi_i>     */
+} egpe_energy_terms;
+
+/* Options of egpe_ncg_solve (Algorithm 1 with the readings named below). */
+typedef struct {
+  int precond;              /* EGPE_PRECOND_*                                        */
+  int beta_rule;            /* 0: Hestenes-Stiefel+ (Sec. IV.C); others reserved    */
+  int restart_period;       /* K_r: beta = 0 when n mod K_r == 0                     */
+  int max_iter;             /* accepted iterations                                   */
+  int armijo_max;           /* halvings after a rejected step (Sec. V, last para.)  */
+  int poll_every;           /* graph replays between host status polls              */
+  int use_graph;            /* capture one attempt as a CUDA graph and replay it    */
+  int psi_on_host;          /* psi_inout are HOST pointers (copied in and out)      */
+  double tol_res;           /* stop when ||r|| = sqrt(sum_i <r_i, r_i>) < tol_res    */
+  double tol_dE;            /* optional: stop when |E^{n+1} - E^n| < tol_dE (0 off) */
+  double armijo_c1;         /* Armijo constant c1                                   */
+  double theta_max;         /* cap of max_i theta_i (scales alpha)                  */
+  double accept_rtol;       /* accept when E_trial < E + accept_rtol |E| (FP64)     */
+  double accept_rtol_fp32;  /* the same allowance for FP32 fields                   */
+  double pv_floor;          /* P_V >= pv_floor |alpha_i|                            */
+  double tol_fp32_switch;   /* MIXED: FP32 phase ends when ||r|| < this             */
+  int max_iter_fp32;        /* MIXED: cap of the FP32 phase                         */
+  int trace_cap;            /* entries available in trace (0: no trace)             */
+  void* trace;              /* HOST array of egpe_trace_entry, or NULL              */
+} egpe_solve_opts;
+
+/* One attempted step of the solver (accepted or rejected). */
+typedef struct {
+  int n;                    /* iteration index (accepted steps before this one)    */
+  int kind;                 /* 0 analytic step, 1 Armijo step                       */
+  int armijo;               /* halvings k for this attempt                          */
+  int flags;                /* bit0 accepted, bit1 restart (beta = 0), bit2 residual
+                               fallback, bit3 FP32 phase                             */
+  double E, E_trial, res, beta, alpha, theta[2], Ep, Epp;
+} egpe_trace_entry;
+
+/* Result of egpe_ncg_solve, one per instance. */
+typedef struct {
+  int status;               /* EGPE_OK when converged                               */
+  int iters;                /* accepted iterations (all phases)                     */
+  int iters_fp32;           /* of which in the FP32 phase (MIXED)                   */
+  int attempts;             /* trial evaluations                                    */
+  int restarts;             /* iterations with beta = 0                             */
+  int armijo_steps;         /* rejected trials                                      */
+  int trace_len;            /* entries written to opts->trace                       */
+  int graph_launches;       /* graph replays (or attempt sequences) issued          */
+  double E;                 /* final energy                                         */
+  double mu[2];             /* final chemical potentials                            */
+  double res;               /* final ||r||                                          */
+  double seconds;           /* wall time of the call                                */
+  long long ffts;           /* complex 3D transforms executed                       */
+  long long kernels;        /* kernel launches issued (including masked ones)       */
+} egpe_report;
+
+typedef struct egpe_handle egpe_handle;
+
+/* Create a handle for n_inst instances (grids[i], params[i]) of the given
+ * precision on the current CUDA device.  cuda_stream is a cudaStream_t (NULL:
+ * the legacy default stream).  Allocates every workspace up front (about 26
+ * complex fields per instance and precision).  Errors: INVALID_ARG (bad sizes,
+ * non-symmetric couplings, L <= 0, Q out of range), OOM, CUDA. */
+egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n_inst,
+                        egpe_precision prec, void* cuda_stream, egpe_handle** out);
+
+/* Release every resource of the handle (NULL is a no-op). */
+void egpe_destroy(egpe_handle* h);
+
+/* Energy and gradient at psi (Eq. 1 and the coupled eGPE, Sec. II; mu_i of
+ * Sec. III).  psi: device (2,nz,ny,nx) complex, read only.  E, mu: host
+ * outputs (may be NULL).  grad: device output H_i psi_i, same layout, or NULL. */
+egpe_status egpe_energy_grad(egpe_handle* h, int inst, const void* psi, double* E, double mu[2],
+                             void* grad);
+
+/* As egpe_energy_grad, returning every energy term (host struct). */
+egpe_status egpe_energy_terms_eval(egpe_handle* h, int inst, const void* psi,
+                                   egpe_energy_terms* terms, void* grad);
+
+/* Coefficients of the energy along the geodesic psi_i(alpha) =
+ * cos(alpha ||p_i||) psi_i + sin(alpha ||p_i||) p_i/||p_i|| (Sec. V):
+ * coeffs[0] = E(psi), coeffs[1] = E'(0), coeffs[2] = E''(0).  p must be
+ * tangent (Re<p_i, psi_i> = 0); it is not projected.  psi, p: device. */
+egpe_status egpe_line_coeffs(egpe_handle* h, int inst, const void* psi, const void* p,
+                             double coeffs[3]);
+
+/* z = P^{-1} r at the state psi (Sec. IV.B), mode EGPE_PRECOND_*.  r == NULL
+ * uses the residual r_i = H_i psi_i - mu_i psi_i of psi.  psi, r, z: device. */
+egpe_status egpe_precondition(egpe_handle* h, int inst, int mode, const void* psi, const void* r,
+                              void* z);
+
+/* psi_out_i = (cos th_i psi_i + sin th_i p_i/||p_i||) / norm (Sec. III geodesic,
+ * explicit renormalisation of Sec. V).  theta: host[2].  Device fields. */
+egpe_status egpe_retract(egpe_handle* h, int inst, const void* psi, const void* p,
+                         const double theta[2], void* psi_out);
+
+/* Unnormalised 3D DFT (inverse: sign +, no 1/N) of nfields consecutive complex
+ * fields of the instance's grid with the library's own Stockham kernels.
+ * in and out may alias.  Device pointers.  A diagnostic of the transform that
+ * every other entry point uses. */
+egpe_status egpe_fft(egpe_handle* h, int inst, const void* in, void* out, int nfields, int inverse);
+
+/* Ground state by preconditioned NCG (Algorithm 1).  psi_inout[i] is the start
+ * and receives the result for instance i (device pointers unless
+ * opts->psi_on_host).  reports: host array of n_inst (may be NULL).
+ * Returns the status of the first instance that did not converge, else OK. */
+egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts* opts,
+                           egpe_report* reports);
+
+/* Defaults: kinetic preconditioner, HS+, K_r = 20, tol_res 1e-8, c1 1e-4,
+ * 30 halvings, theta_max = pi/2, accept_rtol 1e-13 (FP64) / 2e-6 (FP32),
+ * pv_floor 1e-2, graph replay with polls every 8 attempts. */
+void egpe_default_solve_opts(egpe_solve_opts* opts);
+
+/* Human-readable status; never NULL. */
+const char* egpe_status_string(egpe_status s);
+
+/* Message of the last CUDA error seen by this thread's calls ("" if none). */
+const char* egpe_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int egpe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EGPE_H */

@@ -465,6 +465,9 @@ def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = Solve
         E0, Ep, Epp = line_coeffs(grid, prm, psi, p, ev)
         pn = np.array([math.sqrt(inner(grid, p[i], p[i]).real) for i in range(2)])
         pmax = float(pn.max())
+        if not pmax > 0.0:
+            status = "stagnated"
+            break
         if Epp > 0.0 and np.isfinite(Epp) and np.isfinite(Ep):
             alpha0 = -Ep / Epp
             kind = "analytic"

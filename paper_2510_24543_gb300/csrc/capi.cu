@@ -1,0 +1,358 @@
+// C ABI of the eGPE hot path (declared in include/egpe.h).  Validates every
+// argument before any launch, maps CUDA failures to status codes, and drives
+// the per-precision engines.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "egpe.h"
+#include "engine.h"
+
+namespace egpe {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* what, cudaError_t e) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+}
+void set_error_msg(const std::string& msg) { g_last_error = msg; }
+
+// cast kernels for the mixed-precision hand-over (defined in engine units)
+}  // namespace egpe
+
+using egpe::Engine;
+
+struct egpe_handle {
+  int n_inst = 0;
+  egpe_precision prec = EGPE_FP64;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Engine<double>*> e64;
+  std::vector<Engine<float>*> e32;
+  std::vector<egpe_grid> grids;
+};
+
+namespace {
+
+__global__ void cast_d2f(size_t n, const double2* in, float2* out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+__global__ void cast_f2d(size_t n, const float2* in, double2* out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = in[i];
+    out[i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+bool pow2_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+
+egpe_status validate(const egpe_grid& g, const egpe_params& p) {
+  for (int a = 0; a < 3; ++a) {
+    if (!pow2_supported(g.n[a])) {
+      egpe::set_error_msg("grid size must be one of 16, 32, 64, 128, 256 on every axis");
+      return EGPE_ERR_INVALID_ARG;
+    }
+    if (!(g.L[a] > 0.0) || !std::isfinite(g.L[a])) {
+      egpe::set_error_msg("box half-lengths must be positive and finite");
+      return EGPE_ERR_INVALID_ARG;
+    }
+    if (!std::isfinite(p.trap[a])) {
+      egpe::set_error_msg("trap frequencies must be finite");
+      return EGPE_ERR_INVALID_ARG;
+    }
+  }
+  if ((size_t)g.n[0] * g.n[1] * g.n[2] > (size_t)1 << 28) {
+    egpe::set_error_msg("grid too large");
+    return EGPE_ERR_INVALID_ARG;
+  }
+  if (p.g[0][1] != p.g[1][0] || p.gdd[0][1] != p.gdd[1][0]) {
+    egpe::set_error_msg("couplings g and gdd must be symmetric");
+    return EGPE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (!std::isfinite(p.g[i][j]) || !std::isfinite(p.gdd[i][j])) {
+        egpe::set_error_msg("couplings must be finite");
+        return EGPE_ERR_INVALID_ARG;
+      }
+  if (p.lhy_nodes < 1 || p.lhy_nodes > 64 || !(p.lhy_eta_scale > 0.0) || !std::isfinite(p.lhy_kappa)) {
+    egpe::set_error_msg("lhy_nodes must be in [1,64], lhy_eta_scale > 0, lhy_kappa finite");
+    return EGPE_ERR_INVALID_ARG;
+  }
+  return EGPE_OK;
+}
+
+bool bad_inst(egpe_handle* h, int inst) { return !h || inst < 0 || inst >= h->n_inst; }
+
+egpe_status sync_and_check(egpe_handle* h) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    egpe::set_error("cudaStreamSynchronize", e);
+    return EGPE_ERR_CUDA;
+  }
+  return EGPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int egpe_version(void) { return 100; }
+
+const char* egpe_last_error(void) { return egpe::g_last_error.c_str(); }
+
+const char* egpe_status_string(egpe_status s) {
+  switch (s) {
+    case EGPE_OK: return "ok";
+    case EGPE_ERR_INVALID_ARG: return "invalid argument";
+    case EGPE_ERR_CUDA: return "CUDA error";
+    case EGPE_ERR_OOM: return "out of device memory";
+    case EGPE_ERR_NONFINITE: return "non-finite value";
+    case EGPE_ERR_NOT_CONVERGED: return "not converged";
+    case EGPE_ERR_STAGNATED: return "stagnated (no acceptable step)";
+    case EGPE_ERR_TIMEOUT: return "timeout";
+    case EGPE_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+void egpe_default_solve_opts(egpe_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precond = EGPE_PRECOND_KINETIC;
+  o->beta_rule = 0;
+  o->restart_period = 20;
+  o->max_iter = 2000;
+  o->armijo_max = 30;
+  o->poll_every = 8;
+  o->use_graph = 1;
+  o->psi_on_host = 0;
+  o->tol_res = 1e-8;
+  o->tol_dE = 0.0;
+  o->armijo_c1 = 1e-4;
+  o->theta_max = 1.5707963267948966;
+  o->accept_rtol = 1e-13;
+  o->accept_rtol_fp32 = 1e-6;
+  o->pv_floor = 1e-2;
+  o->tol_fp32_switch = 1e-4;
+  o->max_iter_fp32 = 2000;
+  o->trace_cap = 0;
+  o->trace = nullptr;
+}
+
+egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n_inst, egpe_precision prec,
+                        void* cuda_stream, egpe_handle** out) {
+  if (!out) return EGPE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!grids || !params || n_inst < 1 || n_inst > 4096 || (prec != EGPE_FP64 && prec != EGPE_FP32 && prec != EGPE_MIXED)) {
+    egpe::set_error_msg("egpe_create: bad arguments");
+    return EGPE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n_inst; ++i) {
+    egpe_status s = validate(grids[i], params[i]);
+    if (s != EGPE_OK) return s;
+  }
+  egpe_handle* h = new egpe_handle();
+  h->n_inst = n_inst;
+  h->prec = prec;
+  cudaGetDevice(&h->device);
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      egpe::set_error("cudaStreamCreateWithFlags", e);
+      delete h;
+      return EGPE_ERR_CUDA;
+    }
+    h->own_stream = true;
+  }
+  h->grids.assign(grids, grids + n_inst);
+  for (int i = 0; i < n_inst; ++i) {
+    if (prec == EGPE_FP64 || prec == EGPE_MIXED) {
+      auto* e = new Engine<double>();
+      h->e64.push_back(e);
+      egpe_status s = e->create(grids[i], params[i], h->stream);
+      if (s != EGPE_OK) {
+        egpe_destroy(h);
+        return s;
+      }
+    }
+    if (prec == EGPE_FP32 || prec == EGPE_MIXED) {
+      auto* e = new Engine<float>();
+      h->e32.push_back(e);
+      egpe_status s = e->create(grids[i], params[i], h->stream);
+      if (s != EGPE_OK) {
+        egpe_destroy(h);
+        return s;
+      }
+    }
+  }
+  egpe_status s = sync_and_check(h);
+  if (s != EGPE_OK) {
+    egpe_destroy(h);
+    return s;
+  }
+  *out = h;
+  return EGPE_OK;
+}
+
+void egpe_destroy(egpe_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto* e : h->e64) delete e;
+  for (auto* e : h->e32) delete e;
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+egpe_status egpe_energy_terms_eval(egpe_handle* h, int inst, const void* psi, egpe_energy_terms* terms, void* grad) {
+  if (bad_inst(h, inst) || !psi) return EGPE_ERR_INVALID_ARG;
+  if (h->prec == EGPE_FP32)
+    return h->e32[inst]->energy_grad((const float2*)psi, terms, (float2*)grad);
+  return h->e64[inst]->energy_grad((const double2*)psi, terms, (double2*)grad);
+}
+
+egpe_status egpe_energy_grad(egpe_handle* h, int inst, const void* psi, double* E, double mu[2], void* grad) {
+  egpe_energy_terms t;
+  egpe_status s = egpe_energy_terms_eval(h, inst, psi, &t, grad);
+  if (s != EGPE_OK) return s;
+  if (E) *E = t.E;
+  if (mu) {
+    mu[0] = t.mu[0];
+    mu[1] = t.mu[1];
+  }
+  return EGPE_OK;
+}
+
+egpe_status egpe_line_coeffs(egpe_handle* h, int inst, const void* psi, const void* p, double coeffs[3]) {
+  if (bad_inst(h, inst) || !psi || !p || !coeffs) return EGPE_ERR_INVALID_ARG;
+  if (h->prec == EGPE_FP32) return h->e32[inst]->line_coeffs((const float2*)psi, (const float2*)p, coeffs);
+  return h->e64[inst]->line_coeffs((const double2*)psi, (const double2*)p, coeffs);
+}
+
+egpe_status egpe_precondition(egpe_handle* h, int inst, int mode, const void* psi, const void* r, void* z) {
+  if (bad_inst(h, inst) || !psi || !z || mode < 0 || mode > 3) return EGPE_ERR_INVALID_ARG;
+  if (h->prec == EGPE_FP32)
+    return h->e32[inst]->precondition(mode, (const float2*)psi, (const float2*)r, (float2*)z);
+  return h->e64[inst]->precondition(mode, (const double2*)psi, (const double2*)r, (double2*)z);
+}
+
+egpe_status egpe_retract(egpe_handle* h, int inst, const void* psi, const void* p, const double theta[2],
+                         void* psi_out) {
+  if (bad_inst(h, inst) || !psi || !p || !theta || !psi_out) return EGPE_ERR_INVALID_ARG;
+  if (!std::isfinite(theta[0]) || !std::isfinite(theta[1])) return EGPE_ERR_INVALID_ARG;
+  if (h->prec == EGPE_FP32)
+    return h->e32[inst]->retract((const float2*)psi, (const float2*)p, theta, (float2*)psi_out);
+  return h->e64[inst]->retract((const double2*)psi, (const double2*)p, theta, (double2*)psi_out);
+}
+
+egpe_status egpe_fft(egpe_handle* h, int inst, const void* in, void* out, int nfields, int inverse) {
+  if (bad_inst(h, inst) || !in || !out || nfields < 1 || nfields > 64) return EGPE_ERR_INVALID_ARG;
+  if (h->prec == EGPE_FP32) return h->e32[inst]->fft((const float2*)in, (float2*)out, nfields, inverse ? 1 : 0);
+  return h->e64[inst]->fft((const double2*)in, (double2*)out, nfields, inverse ? 1 : 0);
+}
+
+egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts* opts,
+                           egpe_report* reports) {
+  if (!h || !psi_inout || !opts) return EGPE_ERR_INVALID_ARG;
+  const egpe_solve_opts& o = *opts;
+  if (o.precond < 0 || o.precond > 3 || o.beta_rule != 0 || o.max_iter < 0 || o.armijo_max < 0 ||
+      o.armijo_max > 60 || !(o.tol_res >= 0.0) || !(o.theta_max > 0.0) || !(o.pv_floor > 0.0) ||
+      o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace)) {
+    egpe::set_error_msg("egpe_ncg_solve: bad options");
+    return EGPE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < h->n_inst; ++i)
+    if (!psi_inout[i]) return EGPE_ERR_INVALID_ARG;
+  egpe_status first_bad = EGPE_OK;
+  egpe_trace_entry* trace = (egpe_trace_entry*)o.trace;
+  for (int i = 0; i < h->n_inst; ++i) {
+    const auto t0 = std::chrono::steady_clock::now();
+    egpe_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    egpe::SolveRun run{};
+    egpe_status s = EGPE_OK;
+    const cudaMemcpyKind kin = o.psi_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kout = o.psi_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    egpe_trace_entry* tr = (i == 0) ? trace : nullptr;  // trace follows the first instance
+    int tcap = (i == 0) ? o.trace_cap : 0;
+    if (h->prec == EGPE_FP64) {
+      auto* e = h->e64[i];
+      s = e->load_psi(psi_inout[i], kin);
+      if (s == EGPE_OK) s = e->solve(o, 0, o.max_iter, o.tol_res, o.accept_rtol, run, tr, tcap, 0);
+      if (s == EGPE_OK) s = e->store_psi(psi_inout[i], kout);
+    } else if (h->prec == EGPE_FP32) {
+      auto* e = h->e32[i];
+      s = e->load_psi(psi_inout[i], kin);
+      if (s == EGPE_OK) s = e->solve(o, 1, o.max_iter, o.tol_res, o.accept_rtol_fp32, run, tr, tcap, 0);
+      if (s == EGPE_OK) s = e->store_psi(psi_inout[i], kout);
+    } else {  // MIXED: FP32 phase, then FP64 polish
+      auto* e64 = h->e64[i];
+      auto* e32 = h->e32[i];
+      s = e64->load_psi(psi_inout[i], kin);
+      const size_t n2 = 2 * e64->N;
+      if (s == EGPE_OK) {
+        cast_d2f<<<256, 256, 0, h->stream>>>(n2, (const double2*)e64->psi_slot0(), e32->psi_slot0());
+        if (cudaGetLastError() != cudaSuccess) s = EGPE_ERR_CUDA;
+      }
+      egpe::SolveRun r32{};
+      if (s == EGPE_OK)
+        s = e32->solve(o, 1, o.max_iter_fp32, std::max(o.tol_res, o.tol_fp32_switch), o.accept_rtol_fp32, r32, tr,
+                       tcap, 0);
+      if (s == EGPE_OK) {
+        cast_f2d<<<256, 256, 0, h->stream>>>(n2, e32->current_psi(), e64->psi_slot0());
+        if (cudaGetLastError() != cudaSuccess) s = EGPE_ERR_CUDA;
+      }
+      if (s == EGPE_OK) s = e64->normalise_current();
+      egpe_trace_entry* tr2 = tr ? tr + r32.trace_len : nullptr;
+      const int tcap2 = tr ? std::max(0, tcap - r32.trace_len) : 0;
+      if (s == EGPE_OK)
+        s = e64->solve(o, 0, o.max_iter, o.tol_res, o.accept_rtol, run, tcap2 > 0 ? tr2 : nullptr, tcap2, 0);
+      if (s == EGPE_OK) s = e64->store_psi(psi_inout[i], kout);
+      rep.iters_fp32 = r32.n;
+      run.n += r32.n;
+      run.attempts += r32.attempts;
+      run.restarts += r32.restarts;
+      run.armijo_total += r32.armijo_total;
+      run.launches += r32.launches;
+      run.ffts += r32.ffts;
+      run.kernels += r32.kernels;
+      run.trace_len += r32.trace_len;
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    if (s != EGPE_OK) {
+      rep.status = s;
+    } else {
+      rep.status = run.status;
+    }
+    rep.iters = run.n;
+    if (h->prec == EGPE_FP32) rep.iters_fp32 = run.n;
+    rep.attempts = run.attempts;
+    rep.restarts = run.restarts;
+    rep.armijo_steps = run.armijo_total;
+    rep.trace_len = run.trace_len;
+    rep.graph_launches = run.launches;
+    rep.E = run.E;
+    rep.mu[0] = run.mu[0];
+    rep.mu[1] = run.mu[1];
+    rep.res = run.res;
+    rep.seconds = std::chrono::duration<double>(t1 - t0).count();
+    rep.ffts = run.ffts;
+    rep.kernels = run.kernels;
+    if (reports) reports[i] = rep;
+    if (s != EGPE_OK) return s;
+    if (rep.status != EGPE_OK && first_bad == EGPE_OK) first_bad = (egpe_status)rep.status;
+  }
+  return first_bad;
+}
+
+}  // extern "C"

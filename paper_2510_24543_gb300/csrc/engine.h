@@ -1,0 +1,96 @@
+// Host-side engine of one eGPE instance in one field precision: owns the
+// device workspace, the twiddle and quadrature tables, the launch shapes and
+// the captured CUDA graph of one solver attempt.  Implemented in engine_impl.cuh
+// and instantiated for double and float in their own translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <unordered_map>
+
+#include "egpe.h"
+#include "common.cuh"
+
+namespace egpe {
+
+template <class R> struct KArgs;
+
+void set_error(const char* what, cudaError_t e);
+void set_error_msg(const std::string& msg);
+
+struct SolveRun {
+  int status, n, attempts, restarts, armijo_total, trace_len, launches;
+  double E, mu[2], res;
+  long long ffts, kernels;
+};
+
+template <class R> class Engine {
+ public:
+  using C = C2<R>;
+  Engine() = default;
+  Engine(const Engine&) = delete;
+  Engine& operator=(const Engine&) = delete;
+  ~Engine() { destroy(); }
+
+  egpe_status create(const egpe_grid& g, const egpe_params& p, cudaStream_t stream);
+  void destroy();
+
+  // Standalone evaluations (synchronous; device pointers of this precision).
+  egpe_status energy_grad(const C* psi, egpe_energy_terms* out, C* grad);
+  egpe_status line_coeffs(const C* psi, const C* p, double coeffs[3]);
+  egpe_status precondition(int mode, const C* psi, const C* r, C* z);
+  egpe_status retract(const C* psi, const C* p, const double theta[2], C* out);
+  egpe_status fft(const C* in, C* out, int nf, int inverse);
+  egpe_status normalise_current();
+
+  // Solver: psi start must already be in psi buffer 0 (load_psi / cast).
+  egpe_status load_psi(const void* src, cudaMemcpyKind kind);
+  egpe_status store_psi(void* dst, cudaMemcpyKind kind);
+  egpe_status solve(const egpe_solve_opts& o, int fp32_phase, int max_iter, double tol_res, double accept_rtol,
+                    SolveRun& run, egpe_trace_entry* trace_out, int trace_cap, int trace_offset);
+  C* current_psi();  // valid after solve (device)
+  C* psi_slot0();    // psi buffer 0 (start of a solve)
+
+  size_t N = 0;
+  int nx = 0, ny = 0, nz = 0;
+  cudaStream_t stream = nullptr;
+  double dV = 0.0;
+
+ private:
+  egpe_status enq_eg(int trial, int gate, int ctrl);
+  egpe_status enq_pc(int mode, int gate, int ctrl, int rgiven);
+  egpe_status enq_lc(int gate, int ctrl, int pgiven);
+  egpe_status enq_attempt(int mode);
+  egpe_status reset_state(const egpe_solve_opts* o, int fp32_phase, int max_iter, double tol_res,
+                          double accept_rtol);
+  egpe_status read_state(DevState& hs);
+  template <class Op> egpe_status launch_x(KArgs<R> a);
+  template <class Op> egpe_status launch_col(KArgs<R> a);
+  template <template <class, int> class OpT> egpe_status dispatch_x(int L, const KArgs<R>& a);
+  template <template <class, int> class OpT> egpe_status dispatch_col(int L, const KArgs<R>& a);
+  egpe_status plain_x(int inverse, const KArgs<R>& a);
+  egpe_status plain_col(int axis, int inverse, const KArgs<R>& a);
+  int occupancy(const void* fn, int block, size_t smem);
+
+  KArgs<R>* base_ = nullptr;  // host copy of the common kernel arguments
+  egpe_grid grid_{};
+  egpe_params prm_{};
+  void* arena_ = nullptr;
+  C* twx_ = nullptr;
+  C* twy_ = nullptr;
+  C* twz_ = nullptr;
+  LhyNode<R>* nodes_ = nullptr;
+  double* partials_ = nullptr;
+  unsigned* counter_ = nullptr;
+  DevState* st_ = nullptr;
+  DevState* st_host_ = nullptr;  // pinned mirror
+  TraceDev* trace_ = nullptr;
+  int trace_alloc_ = 0;
+  int nsm_ = 0;
+  long long kernels_ = 0;
+  std::unordered_map<unsigned long long, int> occ_;
+  cudaGraphExec_t graph_[4] = {nullptr, nullptr, nullptr, nullptr};
+  int graph_max_iter_[4] = {0, 0, 0, 0};
+};
+
+}  // namespace egpe

@@ -1,0 +1,653 @@
+// Implementation of Engine<R> (see engine.h).  Included by engine_f64.cu and
+// engine_f32.cu only.
+#pragma once
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "engine.h"
+#include "kernels.cuh"
+
+namespace egpe {
+
+#define EGPE_CUDA(call)                       \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) {                  \
+      set_error(#call, e_);                   \
+      return e_ == cudaErrorMemoryAllocation ? EGPE_ERR_OOM : EGPE_ERR_CUDA; \
+    }                                         \
+  } while (0)
+
+static inline bool supported_len(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+
+// Gauss-Legendre rule on [0,1] by Newton iteration on P_Q (long double).
+static void gauss_legendre01(int Q, std::vector<long double>& u, std::vector<long double>& w) {
+  u.resize(Q);
+  w.resize(Q);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < Q; ++i) {
+    long double x = cosl(pi * (i + 0.75L) / (Q + 0.5L));
+    long double dp = 1.0L;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1.0L, p1 = x;
+      for (int k = 2; k <= Q; ++k) {
+        const long double p2 = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (Q == 1) {
+        p1 = x;
+        p0 = 1.0L;
+      }
+      dp = Q * (x * p1 - p0) / (x * x - 1.0L);
+      const long double dx = p1 / dp;
+      x -= dx;
+      if (fabsl(dx) < 1e-19L) break;
+    }
+    {
+      long double p0 = 1.0L, p1 = x;
+      for (int k = 2; k <= Q; ++k) {
+        const long double p2 = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (Q == 1) {
+        p1 = x;
+        p0 = 1.0L;
+      }
+      dp = Q * (x * p1 - p0) / (x * x - 1.0L);
+    }
+    u[i] = 0.5L * (1.0L + x);
+    w[i] = 1.0L / ((1.0L - x * x) * dp * dp);  // (2/((1-x^2) P'^2)) / 2
+  }
+}
+
+template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_params& p, cudaStream_t s) {
+  grid_ = g;
+  prm_ = p;
+  stream = s;
+  nx = g.n[0];
+  ny = g.n[1];
+  nz = g.n[2];
+  N = (size_t)nx * ny * nz;
+  int dev = 0;
+  EGPE_CUDA(cudaGetDevice(&dev));
+  EGPE_CUDA(cudaDeviceGetAttribute(&nsm_, cudaDevAttrMultiProcessorCount, dev));
+  const size_t fb = N * sizeof(C);
+  // psi[2], hp[2], ax[2], rb[2], pb[2]: 2 fields each; z: 2; W: 3  -> 25 fields
+  EGPE_CUDA(cudaMalloc(&arena_, 25 * fb));
+  EGPE_CUDA(cudaMemsetAsync(arena_, 0, 25 * fb, stream));
+  C* f = reinterpret_cast<C*>(arena_);
+  base_ = new KArgs<R>();
+  std::memset((void*)base_, 0, sizeof(KArgs<R>));
+  KArgs<R>& a = *base_;
+  for (int b = 0; b < 2; ++b) a.psi[b] = f + (0 + 2 * b) * N;
+  for (int b = 0; b < 2; ++b) a.hp[b] = f + (4 + 2 * b) * N;
+  for (int b = 0; b < 2; ++b) a.ax[b] = f + (8 + 2 * b) * N;
+  for (int b = 0; b < 2; ++b) a.rb[b] = f + (12 + 2 * b) * N;
+  for (int b = 0; b < 2; ++b) a.pb[b] = f + (16 + 2 * b) * N;
+  a.z = f + 20 * N;
+  a.W = f + 22 * N;
+  // twiddles W_L^m = exp(-2 pi i m / L), long double on the host
+  C** tws[3] = {&twx_, &twy_, &twz_};
+  for (int ax = 0; ax < 3; ++ax) {
+    const int L = g.n[ax];
+    std::vector<C> h(L);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int m = 0; m < L; ++m) {
+      const long double ang = 2.0L * pi * (long double)m / (long double)L;
+      h[m] = cmk<C>((R)cosl(ang), (R)(-sinl(ang)));
+    }
+    EGPE_CUDA(cudaMalloc(tws[ax], L * sizeof(C)));
+    EGPE_CUDA(cudaMemcpy(*tws[ax], h.data(), L * sizeof(C), cudaMemcpyHostToDevice));
+  }
+  // LHY node constants
+  {
+    const int Q = p.lhy_nodes;
+    std::vector<long double> u, w;
+    gauss_legendre01(Q, u, w);
+    std::vector<LhyNode<R>> h(Q);
+    const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
+    for (int q = 0; q < Q; ++q) {
+      const long double s = 3.0L * u[q] * u[q] - 1.0L;
+      const long double e11 = p.g[0][0] + p.gdd[0][0] * s;
+      const long double e22 = p.g[1][1] + p.gdd[1][1] * s;
+      const long double e12 = p.g[0][1] + p.gdd[0][1] * s;
+      const long double e21 = p.g[1][0] + p.gdd[1][0] * s;
+      h[q].e11 = (R)e11;
+      h[q].e22 = (R)e22;
+      h[q].e2 = (R)(2.0L * e12 * e21);
+      h[q].w = (R)(c5 * w[q]);
+    }
+    EGPE_CUDA(cudaMalloc(&nodes_, Q * sizeof(LhyNode<R>)));
+    EGPE_CUDA(cudaMemcpy(nodes_, h.data(), Q * sizeof(LhyNode<R>), cudaMemcpyHostToDevice));
+  }
+  EGPE_CUDA(cudaMalloc(&partials_, (size_t)16384 * MAX_NS * sizeof(double)));
+  EGPE_CUDA(cudaMalloc(&counter_, 64 * sizeof(unsigned)));
+  EGPE_CUDA(cudaMemset(counter_, 0, 64 * sizeof(unsigned)));
+  EGPE_CUDA(cudaMalloc(&st_, sizeof(DevState)));
+  EGPE_CUDA(cudaMallocHost(&st_host_, sizeof(DevState)));
+  const double hx = 2.0 * g.L[0] / nx, hy = 2.0 * g.L[1] / ny, hz = 2.0 * g.L[2] / nz;
+  dV = hx * hy * hz;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.N = (int)N;
+  a.hx = (R)hx;
+  a.hy = (R)hy;
+  a.hz = (R)hz;
+  a.Lx = (R)g.L[0];
+  a.Ly = (R)g.L[1];
+  a.Lz = (R)g.L[2];
+  const double pi = 3.14159265358979323846;
+  a.dkx = (R)(pi / g.L[0]);
+  a.dky = (R)(pi / g.L[1]);
+  a.dkz = (R)(pi / g.L[2]);
+  a.vx = (R)(0.5 * p.trap[0] * p.trap[0]);
+  a.vy = (R)(0.5 * p.trap[1] * p.trap[1]);
+  a.vz = (R)(0.5 * p.trap[2] * p.trap[2]);
+  a.g11 = (R)p.g[0][0];
+  a.g12 = (R)p.g[0][1];
+  a.g21 = (R)p.g[1][0];
+  a.g22 = (R)p.g[1][1];
+  a.d11 = (R)p.gdd[0][0];
+  a.d12 = (R)p.gdd[0][1];
+  a.d21 = (R)p.gdd[1][0];
+  a.d22 = (R)p.gdd[1][1];
+  a.invN = (R)(1.0 / (double)N);
+  a.Q = p.lhy_nodes;
+  a.nodes = nodes_;
+  a.twx = twx_;
+  a.twy = twy_;
+  a.twz = twz_;
+  a.partials = partials_;
+  a.counter = counter_;
+  a.st = st_;
+  a.trace = nullptr;
+  a.gate = GATE_ALWAYS;
+  return reset_state(nullptr, 0, 0, 0.0, 0.0);
+}
+
+template <class R> void Engine<R>::destroy() {
+  for (auto& gx : graph_)
+    if (gx) {
+      cudaGraphExecDestroy(gx);
+      gx = nullptr;
+    }
+  if (arena_) cudaFree(arena_);
+  if (twx_) cudaFree(twx_);
+  if (twy_) cudaFree(twy_);
+  if (twz_) cudaFree(twz_);
+  if (nodes_) cudaFree(nodes_);
+  if (partials_) cudaFree(partials_);
+  if (counter_) cudaFree(counter_);
+  if (st_) cudaFree(st_);
+  if (st_host_) cudaFreeHost(st_host_);
+  if (trace_) cudaFree(trace_);
+  delete base_;
+  arena_ = nullptr;
+  twx_ = twy_ = twz_ = nullptr;
+  nodes_ = nullptr;
+  partials_ = nullptr;
+  counter_ = nullptr;
+  st_ = nullptr;
+  st_host_ = nullptr;
+  trace_ = nullptr;
+  base_ = nullptr;
+}
+
+template <class R> int Engine<R>::occupancy(const void* fn, int block, size_t smem) {
+  const unsigned long long key = ((unsigned long long)(uintptr_t)fn) ^ ((unsigned long long)block << 48) ^
+                                 ((unsigned long long)smem << 20);
+  auto it = occ_.find(key);
+  if (it != occ_.end()) return it->second;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem) != cudaSuccess || occ < 1) occ = 1;
+  occ_[key] = occ;
+  return occ;
+}
+
+template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> a) {
+  constexpr int L = Op::L, TPL = L / 8, NF = Op::NF, NS = Op::NS;
+  constexpr int LP = row_len_padded<R, L>();
+  const size_t rowbytes = (size_t)NF * LP * sizeof(C);
+  int mx = std::max(1, 32 / TPL);
+  while ((mx * 2) * TPL <= 256 && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
+  a.MX = mx;
+  const int block = mx * TPL;
+  const size_t smem = L * sizeof(C) + (Op::USES_LHY ? (size_t)a.Q * sizeof(LhyNode<R>) : 0) + mx * rowbytes +
+                      (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const int rows = ny * nz;
+  const int groups = (rows + mx - 1) / mx;
+  const int occ = occupancy((const void*)xpass_kernel<Op>, block, smem);
+  const int grid = std::min(groups, std::min(occ * nsm_, 16384));
+  xpass_kernel<Op><<<grid, block, smem, stream>>>(a);
+  ++kernels_;
+  EGPE_CUDA(cudaGetLastError());
+  return EGPE_OK;
+}
+
+template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R> a) {
+  constexpr int L = Op::L, TPL = L / 8, NS = Op::NS;
+  int M = std::max((int)(128 / sizeof(C)), 32 / TPL);
+  M = std::min(M, nx);
+  a.M = M;
+  const int block = M * TPL;
+  const size_t smem = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const int other = (Op::AXIS == 1) ? nz : ny;
+  const int tiles = (nx / M) * other * a.nf;
+  const int occ = occupancy((const void*)colpass_kernel<Op>, block, smem);
+  const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
+  colpass_kernel<Op><<<grid, block, smem, stream>>>(a);
+  ++kernels_;
+  EGPE_CUDA(cudaGetLastError());
+  return EGPE_OK;
+}
+
+template <class R> template <template <class, int> class OpT>
+egpe_status Engine<R>::dispatch_x(int L, const KArgs<R>& a) {
+  switch (L) {
+    case 16: return launch_x<OpT<R, 16>>(a);
+    case 32: return launch_x<OpT<R, 32>>(a);
+    case 64: return launch_x<OpT<R, 64>>(a);
+    case 128: return launch_x<OpT<R, 128>>(a);
+    case 256: return launch_x<OpT<R, 256>>(a);
+  }
+  return EGPE_ERR_UNSUPPORTED;
+}
+
+template <class R> template <template <class, int> class OpT>
+egpe_status Engine<R>::dispatch_col(int L, const KArgs<R>& a) {
+  switch (L) {
+    case 16: return launch_col<OpT<R, 16>>(a);
+    case 32: return launch_col<OpT<R, 32>>(a);
+    case 64: return launch_col<OpT<R, 64>>(a);
+    case 128: return launch_col<OpT<R, 128>>(a);
+    case 256: return launch_col<OpT<R, 256>>(a);
+  }
+  return EGPE_ERR_UNSUPPORTED;
+}
+
+template <class R> egpe_status Engine<R>::plain_x(int inverse, const KArgs<R>& a) {
+#define EGPE_PX(LL) \
+  case LL: return inverse ? launch_x<XPlain<R, LL, true>>(a) : launch_x<XPlain<R, LL, false>>(a);
+  switch (nx) {
+    EGPE_PX(16) EGPE_PX(32) EGPE_PX(64) EGPE_PX(128) EGPE_PX(256)
+  }
+#undef EGPE_PX
+  return EGPE_ERR_UNSUPPORTED;
+}
+
+template <class R> egpe_status Engine<R>::plain_col(int axis, int inverse, const KArgs<R>& a) {
+  const int L = axis == 1 ? ny : nz;
+#define EGPE_PC(LL)                                                                             \
+  case LL:                                                                                      \
+    if (axis == 1) return inverse ? launch_col<ColPlain<R, LL, 1, true>>(a) : launch_col<ColPlain<R, LL, 1, false>>(a); \
+    return inverse ? launch_col<ColPlain<R, LL, 2, true>>(a) : launch_col<ColPlain<R, LL, 2, false>>(a);
+  switch (L) {
+    EGPE_PC(16) EGPE_PC(32) EGPE_PC(64) EGPE_PC(128) EGPE_PC(256)
+  }
+#undef EGPE_PC
+  return EGPE_ERR_UNSUPPORTED;
+}
+
+#define EGPE_TRY(x)                 \
+  do {                              \
+    egpe_status s_ = (x);           \
+    if (s_ != EGPE_OK) return s_;   \
+  } while (0)
+
+// Energy / gradient pipeline: 6 complex 3D transforms.
+template <class R> egpe_status Engine<R>::enq_eg(int trial, int gate, int ctrl) {
+  KArgs<R> a = *base_;
+  a.gate = gate;
+  a.flag = trial;
+  a.ctrl = 0;
+  a.nf = 3;
+  a.f0 = 0;
+  EGPE_TRY(dispatch_x<XFwdEG>(nx, a));
+  KArgs<R> y = a;
+  y.gin = a.W;
+  y.gout = a.W;
+  EGPE_TRY(plain_col(1, 0, y));
+  EGPE_TRY(dispatch_col<ZEg>(nz, a));
+  EGPE_TRY(plain_col(1, 1, y));
+  a.ctrl = ctrl;
+  return dispatch_x<XInvEG>(nx, a);
+}
+
+// Preconditioner pipeline: 4 transforms for the kinetic modes, none otherwise.
+template <class R> egpe_status Engine<R>::enq_pc(int mode, int gate, int ctrl, int rgiven) {
+  KArgs<R> a = *base_;
+  a.gate = gate;
+  a.flag = rgiven;
+  a.diag = (mode & 2) ? 1 : 0;
+  a.ctrl = 0;
+  a.nf = 2;
+  a.f0 = 0;
+  if (mode & 1) {
+    EGPE_TRY(dispatch_x<XFwdPC>(nx, a));
+    KArgs<R> y = a;
+    y.gin = a.W;
+    y.gout = a.W;
+    EGPE_TRY(plain_col(1, 0, y));
+    EGPE_TRY(dispatch_col<ZPc>(nz, a));
+    EGPE_TRY(plain_col(1, 1, y));
+    a.ctrl = ctrl;
+    return dispatch_x<XInvPC>(nx, a);
+  }
+  a.ctrl = ctrl;
+  const int occ = occupancy((const void*)pc_point_kernel<R>, 256, 0);
+  const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)std::min(occ * nsm_, 16384));
+  pc_point_kernel<R><<<grid, 256, 0, stream>>>(a);
+  ++kernels_;
+  EGPE_CUDA(cudaGetLastError());
+  return EGPE_OK;
+}
+
+// Line-search pipeline: forward transforms of p_1, p_2 and one packed pair.
+template <class R> egpe_status Engine<R>::enq_lc(int gate, int ctrl, int pgiven) {
+  KArgs<R> a = *base_;
+  a.gate = gate;
+  a.flag = pgiven;
+  a.ctrl = 0;
+  a.nf = 3;
+  a.f0 = 0;
+  EGPE_TRY(dispatch_x<XFwdLC>(nx, a));
+  KArgs<R> y = a;
+  y.gin = a.W;
+  y.gout = a.W;
+  EGPE_TRY(plain_col(1, 0, y));
+  EGPE_TRY(dispatch_col<ZLc>(nz, a));
+  y.nf = 1;
+  y.f0 = 2;
+  EGPE_TRY(plain_col(1, 1, y));
+  a.ctrl = ctrl;
+  return dispatch_x<XInvLC>(nx, a);
+}
+
+template <class R> egpe_status Engine<R>::enq_attempt(int mode) {
+  EGPE_TRY(enq_pc(mode, GATE_NEW_ITER, 1, 0));
+  EGPE_TRY(enq_lc(GATE_NEW_ITER, 1, 0));
+  return enq_eg(1, GATE_ACTIVE, 1);
+}
+
+template <class R>
+egpe_status Engine<R>::reset_state(const egpe_solve_opts* o, int fp32_phase, int max_iter, double tol_res,
+                                   double accept_rtol) {
+  DevState& h = *st_host_;
+  std::memset(&h, 0, sizeof(DevState));
+  h.phase = PH_NEW_ITER;
+  h.status = EGPE_ERR_NOT_CONVERGED;
+  h.cur = 0;
+  h.dV = dV;
+  h.invN = 1.0 / (double)N;
+  h.opt.pv_floor = 1e-2;
+  h.opt.armijo_c1 = 1e-4;
+  h.opt.theta_max = 1.5707963267948966;
+  h.opt.restart_period = 20;
+  if (o) {
+    h.opt.precond = o->precond;
+    h.opt.restart_period = o->restart_period;
+    h.opt.max_iter = max_iter;
+    h.opt.armijo_max = o->armijo_max;
+    h.opt.trace_cap = o->trace ? std::min(o->trace_cap, trace_alloc_) : 0;
+    h.opt.fp32_phase = fp32_phase;
+    h.opt.tol_res = tol_res;
+    h.opt.tol_dE = o->tol_dE;
+    h.opt.armijo_c1 = o->armijo_c1;
+    h.opt.theta_max = o->theta_max;
+    h.opt.accept_rtol = accept_rtol;
+    h.opt.pv_floor = o->pv_floor;
+  }
+  EGPE_CUDA(cudaMemcpyAsync(st_, &h, sizeof(DevState), cudaMemcpyHostToDevice, stream));
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::read_state(DevState& hs) {
+  EGPE_CUDA(cudaMemcpyAsync(st_host_, st_, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  hs = *st_host_;
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::energy_grad(const C* psi, egpe_energy_terms* out, C* grad) {
+  EGPE_TRY(reset_state(nullptr, 0, 0, 0.0, 0.0));
+  EGPE_CUDA(cudaMemcpyAsync(base_->psi[0], psi, 2 * N * sizeof(C), cudaMemcpyDeviceToDevice, stream));
+  EGPE_TRY(enq_eg(0, GATE_ALWAYS, 1));
+  if (grad) EGPE_CUDA(cudaMemcpyAsync(grad, base_->hp[0], 2 * N * sizeof(C), cudaMemcpyDeviceToDevice, stream));
+  DevState hs;
+  EGPE_TRY(read_state(hs));
+  if (out) {
+    EnergyOut o;
+    finalize_energy(hs.eg[0], hs.egz[0], hs.dV, hs.invN, o);
+    out->E = o.E;
+    for (int i = 0; i < 2; ++i) {
+      out->kin[i] = o.kin[i];
+      out->mu[i] = o.mu[i];
+      out->norm2[i] = o.norm2[i];
+      out->shift[i] = o.shift[i];
+    }
+    out->trap = o.trap;
+    out->contact = o.contact;
+    out->dipolar = o.dipolar;
+    out->lhy = o.lhy;
+  }
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::line_coeffs(const C* psi, const C* p, double coeffs[3]) {
+  egpe_energy_terms t;
+  EGPE_TRY(energy_grad(psi, &t, nullptr));
+  EGPE_CUDA(cudaMemcpyAsync(base_->pb[0], p, 2 * N * sizeof(C), cudaMemcpyDeviceToDevice, stream));
+  EGPE_TRY(enq_lc(GATE_ALWAYS, 0, 1));
+  DevState hs;
+  EGPE_TRY(read_state(hs));
+  LineOut o;
+  finalize_line(hs.lc, hs.lcz, hs.mu, hs.dV, hs.invN, o);
+  coeffs[0] = t.E;
+  coeffs[1] = o.Ep;
+  coeffs[2] = o.Epp;
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::precondition(int mode, const C* psi, const C* r, C* z) {
+  EGPE_TRY(energy_grad(psi, nullptr, nullptr));
+  if (r) EGPE_CUDA(cudaMemcpyAsync(base_->rb[0], r, 2 * N * sizeof(C), cudaMemcpyDeviceToDevice, stream));
+  EGPE_TRY(enq_pc(mode, GATE_ALWAYS, 0, r ? 1 : 0));
+  EGPE_CUDA(cudaMemcpyAsync(z, base_->z, 2 * N * sizeof(C), cudaMemcpyDeviceToDevice, stream));
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::retract(const C* psi, const C* p, const double theta[2], C* out) {
+  KArgs<R> a = *base_;
+  const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)nsm_ * 8);
+  rt_sums_kernel<R><<<grid, 256, 0, stream>>>(a, psi, p);
+  ++kernels_;
+  EGPE_CUDA(cudaGetLastError());
+  DevState hs;
+  EGPE_TRY(read_state(hs));
+  double ca[2], cb[2];
+  for (int i = 0; i < 2; ++i) {
+    const double pn = sqrt(hs.rt[RT_P1 + i] * dV);
+    const double psip = hs.rt[RT_PSIP1 + i] * dV, nps = hs.rt[RT_PSI1 + i] * dV;
+    const double c = cos(theta[i]), s = sin(theta[i]);
+    if (pn > 0.0) {
+      const double inv = 1.0 / sqrt(c * c * nps + s * s + 2.0 * c * s * psip / pn);
+      ca[i] = c * inv;
+      cb[i] = s * inv / pn;
+    } else {
+      ca[i] = 1.0 / sqrt(nps);
+      cb[i] = 0.0;
+    }
+  }
+  rt_apply_kernel<R><<<grid, 256, 0, stream>>>(N, psi, p, out, (R)ca[0], (R)cb[0], (R)ca[1], (R)cb[1]);
+  ++kernels_;
+  EGPE_CUDA(cudaGetLastError());
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::normalise_current() {
+  const double th[2] = {0.0, 0.0};
+  return retract(base_->psi[0], base_->psi[0], th, base_->psi[0]);
+}
+
+template <class R> egpe_status Engine<R>::fft(const C* in, C* out, int nf, int inverse) {
+  for (int f = 0; f < nf; ++f) {
+    KArgs<R> a = *base_;
+    a.gate = GATE_ALWAYS;
+    a.nf = 1;
+    a.f0 = 0;
+    a.gin = in + (size_t)f * N;
+    a.gout = out + (size_t)f * N;
+    EGPE_TRY(plain_x(inverse, a));
+    a.gin = out + (size_t)f * N;
+    EGPE_TRY(plain_col(1, inverse, a));
+    EGPE_TRY(plain_col(2, inverse, a));
+  }
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::load_psi(const void* src, cudaMemcpyKind kind) {
+  EGPE_CUDA(cudaMemcpyAsync(base_->psi[0], src, 2 * N * sizeof(C), kind, stream));
+  return EGPE_OK;
+}
+
+template <class R> typename Engine<R>::C* Engine<R>::current_psi() { return base_->psi[st_host_->cur]; }
+template <class R> typename Engine<R>::C* Engine<R>::psi_slot0() { return base_->psi[0]; }
+
+template <class R> egpe_status Engine<R>::store_psi(void* dst, cudaMemcpyKind kind) {
+  EGPE_CUDA(cudaMemcpyAsync(dst, current_psi(), 2 * N * sizeof(C), kind, stream));
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  return EGPE_OK;
+}
+
+template <class R>
+egpe_status Engine<R>::solve(const egpe_solve_opts& o, int fp32_phase, int max_iter, double tol_res,
+                             double accept_rtol, SolveRun& run, egpe_trace_entry* trace_out, int trace_cap,
+                             int trace_offset) {
+  const int mode = o.precond & 3;
+  if (trace_out && trace_cap > trace_alloc_) {
+    // the trace buffer is captured by the graphs: allocate once, generously
+    const int want = std::max(trace_cap, 65536);
+    for (auto& gx : graph_)
+      if (gx) {
+        cudaGraphExecDestroy(gx);
+        gx = nullptr;
+      }
+    if (trace_) cudaFree(trace_);
+    trace_ = nullptr;
+    EGPE_CUDA(cudaMalloc(&trace_, (size_t)want * sizeof(TraceDev)));
+    trace_alloc_ = want;
+    base_->trace = trace_;
+  }
+  egpe_solve_opts oo = o;
+  oo.trace_cap = trace_out ? trace_cap : 0;
+  oo.trace = trace_out;
+  EGPE_TRY(reset_state(&oo, fp32_phase, max_iter, tol_res, accept_rtol));
+  // r and p history start at zero (beta = 0 at n = 0 reads them)
+  EGPE_CUDA(cudaMemsetAsync(base_->rb[0], 0, 8 * N * sizeof(C), stream));
+  EGPE_TRY(enq_eg(0, GATE_ALWAYS, 1));
+  const long long k0 = kernels_;
+  long long per_attempt = 0;
+  if (o.use_graph) {
+    if (!graph_[mode]) {
+      cudaGraph_t g = nullptr;
+      EGPE_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+      const long long kb = kernels_;
+      egpe_status s = enq_attempt(mode);
+      cudaError_t ce = cudaStreamEndCapture(stream, &g);
+      if (s != EGPE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (ce != cudaSuccess) {
+        set_error("cudaStreamEndCapture", ce);
+        return EGPE_ERR_CUDA;
+      }
+      graph_max_iter_[mode] = (int)(kernels_ - kb);
+      cudaError_t ie = cudaGraphInstantiate(&graph_[mode], g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        set_error("cudaGraphInstantiate", ie);
+        graph_[mode] = nullptr;
+        return EGPE_ERR_CUDA;
+      }
+      kernels_ = kb;
+    }
+    per_attempt = graph_max_iter_[mode];
+  }
+  const int poll = std::max(1, o.poll_every);
+  const long long max_launch = (long long)(max_iter + 2) * (long long)(o.armijo_max + 2) + 4;
+  long long launches = 0;
+  while (launches < max_launch) {
+    for (int k = 0; k < poll; ++k) {
+      if (o.use_graph) {
+        EGPE_CUDA(cudaGraphLaunch(graph_[mode], stream));
+        kernels_ += per_attempt;
+      } else {
+        EGPE_TRY(enq_attempt(mode));
+      }
+      ++launches;
+    }
+    EGPE_CUDA(cudaMemcpyAsync(&st_host_->phase, &st_->phase, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    EGPE_CUDA(cudaStreamSynchronize(stream));
+    if (st_host_->phase == PH_DONE) break;
+  }
+  {
+    KArgs<R> a = *base_;
+    const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)nsm_ * 8);
+    resnorm_kernel<R><<<grid, 256, 0, stream>>>(a);
+    ++kernels_;
+    EGPE_CUDA(cudaGetLastError());
+  }
+  DevState hs;
+  EGPE_TRY(read_state(hs));
+  run.status = (hs.phase == PH_DONE) ? hs.status : EGPE_ERR_NOT_CONVERGED;
+  run.n = hs.n;
+  run.attempts = hs.attempts;
+  run.restarts = hs.restarts;
+  run.armijo_total = hs.armijo_total;
+  run.launches = (int)launches;
+  run.E = hs.E;
+  run.mu[0] = hs.mu[0];
+  run.mu[1] = hs.mu[1];
+  run.res = sqrt((hs.pca[0] + hs.pca[1]) * dV);
+  run.ffts = hs.ffts;
+  run.kernels = kernels_ - k0;
+  run.trace_len = 0;
+  if (trace_out && hs.trace_len > 0) {
+    const int n = std::min(hs.trace_len, trace_cap);
+    std::vector<TraceDev> tmp(n);
+    EGPE_CUDA(cudaMemcpy(tmp.data(), trace_, n * sizeof(TraceDev), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n && trace_offset + i < trace_cap; ++i) {
+      egpe_trace_entry& d = trace_out[trace_offset + i];
+      const TraceDev& s = tmp[i];
+      d.n = s.n;
+      d.kind = s.kind;
+      d.armijo = s.armijo;
+      d.flags = s.flags;
+      d.E = s.E;
+      d.E_trial = s.E_trial;
+      d.res = s.res;
+      d.beta = s.beta;
+      d.alpha = s.alpha;
+      d.theta[0] = s.theta[0];
+      d.theta[1] = s.theta[1];
+      d.Ep = s.Ep;
+      d.Epp = s.Epp;
+      ++run.trace_len;
+    }
+  }
+  return EGPE_OK;
+}
+
+}  // namespace egpe

@@ -1,0 +1,183 @@
+// Batched Stockham (self-sorting) FFT of one line per group of L/8 threads.
+//
+// Each thread owns 8 complex values of its line.  A length-L transform is a
+// sequence of radix passes (radix 8, then one radix-2 or radix-4 pass when
+// log2 L is not a multiple of 3); the inverse plan runs the radices in reverse
+// order so that the forward transform's last-pass register layout is exactly
+// the inverse transform's first-pass layout.  That is what lets the z pass
+// fuse forward FFT -> k-space multiply -> inverse FFT without touching shared
+// memory at the turn.  Between passes values go through shared memory; the
+// first-pass inputs and last-pass outputs stay in registers, so prologue and
+// epilogue code reads and writes global memory directly in natural order.
+//
+// Pass p (radix r, Ns = product of earlier radices), butterfly j, element q:
+//   input position  j + q L/r
+//   twiddle         W_{Ns r}^{q (j mod Ns)}   (table entry q (j mod Ns) L/(Ns r))
+//   output position (j div Ns) Ns r + (j mod Ns) + q Ns
+// Thread t of a line owns butterflies j = t + b L/8 (b < 8/r).
+#pragma once
+#include "common.cuh"
+
+namespace egpe {
+
+template <int L> struct Plan {
+  static constexpr int TPL = L / 8;
+  static constexpr int LOG2 = (L == 8) ? 3 : (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6
+                            : (L == 128) ? 7 : (L == 256) ? 8 : -1;
+  static_assert(LOG2 > 0, "unsupported FFT length");
+  static constexpr int P = (LOG2 + 2) / 3;
+  static constexpr int LAST = L >> (3 * (P - 1));  // radix of the forward plan's last pass
+  __host__ __device__ static constexpr int rad(bool inv, int p) {
+    return inv ? (p == 0 ? LAST : 8) : (p == P - 1 ? LAST : 8);
+  }
+  __host__ __device__ static constexpr int ns(bool inv, int p) {
+    return p == 0 ? 1 : ns(inv, p - 1) * rad(inv, p - 1);
+  }
+  // position of register e of thread t on entry to / exit from the transform
+  __device__ static __forceinline__ int entry_pos(bool inv, int t, int e) {
+    const int r = rad(inv, 0);
+    return t + (e / r) * TPL + (e % r) * (L / r);
+  }
+  __device__ static __forceinline__ int exit_pos(bool inv, int t, int e) {
+    const int r = rad(inv, P - 1);
+    return t + (e / r) * TPL + (e % r) * (L / r);
+  }
+};
+
+template <class C> __device__ __forceinline__ C mul_i(C a) { return cmk<C>(-a.y, a.x); }
+template <class C> __device__ __forceinline__ C mul_mi(C a) { return cmk<C>(a.y, -a.x); }
+
+template <bool INV, class C> __device__ __forceinline__ void dft2(C* v) {
+  C a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <bool INV, class C> __device__ __forceinline__ void dft4v(C& a0, C& a1, C& a2, C& a3) {
+  C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = csub(a1, a3);
+  t3 = INV ? mul_i(t3) : mul_mi(t3);
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <bool INV, class C> __device__ __forceinline__ void dft4(C* v) { dft4v<INV>(v[0], v[1], v[2], v[3]); }
+
+template <bool INV, class C> __device__ __forceinline__ void dft8(C* v) {
+  using R = decltype(C::x);
+  const R h = R(0.70710678118654752440084436210485);
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4v<INV>(e0, e1, e2, e3);
+  dft4v<INV>(o0, o1, o2, o3);
+  // odd outputs times W8^k (forward W8 = exp(-i pi/4); inverse its conjugate)
+  if (INV) {
+    o1 = cmk<C>((o1.x - o1.y) * h, (o1.x + o1.y) * h);
+    o2 = mul_i(o2);
+    o3 = cmk<C>((-o3.x - o3.y) * h, (o3.x - o3.y) * h);
+  } else {
+    o1 = cmk<C>((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+    o2 = mul_mi(o2);
+    o3 = cmk<C>((o3.y - o3.x) * h, -(o3.x + o3.y) * h);
+  }
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+template <int R_, bool INV, class C> __device__ __forceinline__ void dft_r(C* v) {
+  if constexpr (R_ == 8) dft8<INV>(v);
+  else if constexpr (R_ == 4) dft4<INV>(v);
+  else dft2<INV>(v);
+}
+
+// Runs passes p..P-1 of the (forward or inverse) plan on NF lines at once.
+// v[f][8]: this thread's registers for field f; sm + f*fstride: the shared
+// line buffer of field f for this thread's line; si(pos): offset of line
+// position pos inside that buffer; tw: shared table W_L^m, m < L.
+template <class C, int L, bool INV, int NF, int p, class SI>
+__device__ __forceinline__ void fft_passes(C (&v)[NF][8], C* sm, int fstride, const C* __restrict__ tw,
+                                           int t, const SI& si) {
+  using PL = Plan<L>;
+  constexpr int r = PL::rad(INV, p);
+  constexpr int Ns = PL::ns(INV, p);
+  constexpr int NB = 8 / r;
+  constexpr int TPL = PL::TPL;
+  constexpr int STW = L / (Ns * r);
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = t + b * TPL;
+    if constexpr (Ns > 1) {
+      const int k = j % Ns;
+#pragma unroll
+      for (int q = 1; q < r; ++q) {
+        const C w = tw[q * k * STW];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) v[f][b * r + q] = INV ? cmulc(v[f][b * r + q], w) : cmul(v[f][b * r + q], w);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dft_r<r, INV>(&v[f][b * r]);
+  }
+  if constexpr (p + 1 < PL::P) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = t + b * TPL;
+      const int base = (j / Ns) * Ns * r + (j % Ns);
+#pragma unroll
+      for (int q = 0; q < r; ++q) {
+        const int o = si(base + q * Ns);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) sm[f * fstride + o] = v[f][b * r + q];
+      }
+    }
+    __syncthreads();
+    constexpr int r2 = PL::rad(INV, p + 1);
+    constexpr int NB2 = 8 / r2;
+#pragma unroll
+    for (int b = 0; b < NB2; ++b) {
+      const int j = t + b * TPL;
+#pragma unroll
+      for (int q = 0; q < r2; ++q) {
+        const int o = si(j + q * (L / r2));
+#pragma unroll
+        for (int f = 0; f < NF; ++f) v[f][b * r2 + q] = sm[f * fstride + o];
+      }
+    }
+    __syncthreads();
+    fft_passes<C, L, INV, NF, p + 1, SI>(v, sm, fstride, tw, t, si);
+  }
+}
+
+template <class C, int L, bool INV, int NF, class SI>
+__device__ __forceinline__ void fft_line(C (&v)[NF][8], C* sm, int fstride, const C* __restrict__ tw, int t,
+                                         const SI& si) {
+  fft_passes<C, L, INV, NF, 0, SI>(v, sm, fstride, tw, t, si);
+}
+
+// Shared-memory index maps.  Row tiles (lines contiguous in global memory):
+// one padded line per row, one pad element per 128 bytes to break the
+// power-of-two strides of the Stockham writes.  Column tiles (lines strided
+// in global memory, M adjacent lines per tile): position-major, so each
+// quarter/half warp touches one 128-byte row of the tile.
+template <int PADSHIFT> struct RowIdx {
+  __device__ __forceinline__ int operator()(int pos) const { return pos + (pos >> PADSHIFT); }
+};
+struct ColIdx {
+  int M;
+  __device__ __forceinline__ int operator()(int pos) const { return pos * M; }
+};
+template <class R> struct PadShift;
+template <> struct PadShift<double> { static constexpr int v = 3; };  // 8 x 16 B
+template <> struct PadShift<float> { static constexpr int v = 4; };   // 16 x 8 B
+template <class R, int L> __host__ __device__ constexpr int row_len_padded() {
+  return L + (L >> PadShift<R>::v);
+}
+
+}  // namespace egpe

@@ -1,0 +1,857 @@
+// Kernels of the eGPE hot path.  Two kernel shapes carry every 3D transform:
+//
+// * xpass_kernel<Op>: lines along x (contiguous).  A block owns MX rows; each
+//   row is transformed by L/8 threads.  Op supplies the prologue (values at the
+//   transform's entry positions, read straight from global memory) and the
+//   epilogue (consumes the exit positions: stores, pointwise physics, sums).
+// * colpass_kernel<Op>: lines along y or z (strided).  A tile is M adjacent x
+//   columns times one line; lanes run along x so every global access is a
+//   full 128-byte row of the tile.
+//
+// Both are persistent (grid-stride over rows / tiles) so that the per-block
+// FP64 partial sums stay few; the last block finalises the sums in a fixed
+// order and, where a pipeline needs it, runs the controller step.
+#pragma once
+#include "common.cuh"
+#include "ctrl.cuh"
+#include "fft.cuh"
+#include "lhy.cuh"
+#include "reduce.cuh"
+
+namespace egpe {
+
+template <class R> struct KArgs {
+  using C = C2<R>;
+  int nx, ny, nz, N;
+  R hx, hy, hz, Lx, Ly, Lz;
+  R dkx, dky, dkz;           // pi / L_a
+  R vx, vy, vz;              // lambda_a^2 / 2
+  R g11, g12, g21, g22;      // contact couplings
+  R d11, d12, d21, d22;      // k-space dipolar coefficients
+  R invN;
+  int Q;
+  const LhyNode<R>* nodes;
+  const C* twx;
+  const C* twy;
+  const C* twz;
+  C* psi[2];                 // psi buffers (2 fields each)
+  C* hp[2];                  // H psi buffers
+  C* ax[2];                  // aux: field 0 = (Phi1, Phi2), field 1 = (muL1, muL2)
+  C* rb[2];                  // residual buffers (current / previous by parity of n)
+  C* pb[2];                  // direction buffers (current / previous)
+  C* z;                      // preconditioned residual
+  C* W;                      // transform workspace, 3 fields
+  const C* gin;              // generic in/out of the plain passes
+  C* gout;
+  double* partials;
+  unsigned* counter;
+  DevState* st;
+  TraceDev* trace;
+  int MX, M, nf, f0;         // launch shape: rows per block, columns per tile, fields
+  int gate;                  // Gate
+  int flag;                  // op-specific (trial / r given / p given)
+  int ctrl;                  // run the controller step in the last block
+  int diag;                  // P_V part of the preconditioner
+};
+
+template <class R> __device__ __forceinline__ bool gate_open(const KArgs<R>& a) {
+  if (a.gate == GATE_ALWAYS) return true;
+  const int ph = __ldcg(&a.st->phase);
+  return a.gate == GATE_NEW_ITER ? (ph == PH_NEW_ITER) : (ph != PH_DONE);
+}
+
+template <class R> __device__ __forceinline__ R wavenum(int j, int n, R dk) {
+  return dk * (R)(j < (n >> 1) ? j : j - n);
+}
+
+// ----------------------------------------------------------------------------
+// Row (x) pass kernel
+// ----------------------------------------------------------------------------
+template <class Op> __global__ void __launch_bounds__(256) xpass_kernel(KArgs<typename Op::R> a) {
+  using R = typename Op::R;
+  using C = C2<R>;
+  constexpr int L = Op::L, NF = Op::NF, NS = Op::NS;
+  constexpr int NSR = NS > 0 ? NS : 1;
+  constexpr int TPL = L / 8;
+  constexpr int LP = row_len_padded<R, L>();
+  if (!gate_open(a)) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tw = reinterpret_cast<C*>(smraw);
+  LhyNode<R>* nodes = reinterpret_cast<LhyNode<R>*>(tw + L);
+  C* buf = reinterpret_cast<C*>(nodes + (Op::USES_LHY ? a.Q : 0));
+  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(buf + NF * a.MX * LP);
+  const int tid = threadIdx.x;
+  const int mrow = tid / TPL, t = tid - mrow * TPL;
+  for (int i = tid; i < L; i += blockDim.x) tw[i] = a.twx[i];
+  if (Op::USES_LHY)
+    for (int i = tid; i < a.Q; i += blockDim.x) nodes[i] = a.nodes[i];
+  __syncthreads();
+  typename Op::Uni u;
+  Op::uniform(a, u);
+  double acc[NSR];
+#pragma unroll
+  for (int s = 0; s < NSR; ++s) acc[s] = 0.0;
+  const int rows = a.ny * a.nz;
+  const int ngroups = (rows + a.MX - 1) / a.MX;
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int row = grp * a.MX + mrow;
+    const bool valid = row < rows;
+    C v[NF][8];
+    Op::load(a, u, row, valid, t, v, acc);
+    fft_line<C, L, Op::INV, NF>(v, buf + mrow * LP, a.MX * LP, tw, t, RowIdx<PadShift<R>::v>{});
+    Op::store(a, u, row, valid, t, v, acc, nodes);
+  }
+  if constexpr (NS > 0) {
+    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
+      if (threadIdx.x == 0) Op::finish(a, u);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Column (y or z) pass kernel
+// ----------------------------------------------------------------------------
+template <class Op> __global__ void __launch_bounds__(512) colpass_kernel(KArgs<typename Op::R> a) {
+  using R = typename Op::R;
+  using C = C2<R>;
+  constexpr int L = Op::L, NS = Op::NS;
+  constexpr int NSR = NS > 0 ? NS : 1;
+  if (!gate_open(a)) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* tw = reinterpret_cast<C*>(smraw);
+  C* buf = tw + L;
+  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(buf + a.M * L);
+  const int tid = threadIdx.x;
+  const int m = tid % a.M, t = tid / a.M;
+  const C* twsrc = (Op::AXIS == 1) ? a.twy : a.twz;
+  for (int i = tid; i < L; i += blockDim.x) tw[i] = twsrc[i];
+  __syncthreads();
+  typename Op::Uni u;
+  Op::uniform(a, u);
+  double acc[NSR];
+#pragma unroll
+  for (int s = 0; s < NSR; ++s) acc[s] = 0.0;
+  const int xb_n = a.nx / a.M;
+  const int other_n = (Op::AXIS == 1) ? a.nz : a.ny;
+  const int tiles = xb_n * other_n * a.nf;
+  const size_t lstride = (Op::AXIS == 1) ? (size_t)a.nx : (size_t)a.nx * a.ny;
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int xb = tile % xb_n;
+    const int rest = tile / xb_n;
+    const int o = rest % other_n;
+    const int f = a.f0 + rest / other_n;
+    const int x = xb * a.M + m;
+    const size_t base = (size_t)f * a.N + (Op::AXIS == 1 ? (size_t)o * a.nx * a.ny : (size_t)o * a.nx) + x;
+    Op::run(a, u, f, x, o, base, lstride, t, buf + m, tw, ColIdx{a.M}, acc);
+  }
+  if constexpr (NS > 0) {
+    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
+      if (threadIdx.x == 0) Op::finish(a, u);
+    }
+  }
+}
+
+struct NoUni {};
+
+// ----------------------------------------------------------------------------
+// Plain transforms (diagnostic entry point and the y passes of the pipelines)
+// ----------------------------------------------------------------------------
+template <class R_, int L_, bool INV_> struct XPlain {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NF = 1, NS = 0;
+  static constexpr bool INV = INV_, USES_LHY = false;
+  using Uni = NoUni;
+  static __device__ void uniform(const KArgs<R>&, Uni&) {}
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], double*) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      v[0][e] = valid ? a.gin[(size_t)row * a.nx + Plan<L>::entry_pos(INV, t, e)] : cmk<C>(0, 0);
+  }
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], double*,
+                               const LhyNode<R>*) {
+    if (!valid) return;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a.gout[(size_t)row * a.nx + Plan<L>::exit_pos(INV, t, e)] = v[0][e];
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_, int AXIS_, bool INV_> struct ColPlain {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NS = 0, AXIS = AXIS_;
+  static constexpr bool INV = INV_;
+  using Uni = NoUni;
+  static __device__ void uniform(const KArgs<R>&, Uni&) {}
+  static __device__ void run(const KArgs<R>& a, Uni&, int, int, int, size_t base, size_t ls, int t, C* sm,
+                             const C* tw, ColIdx si, double*) {
+    C v[1][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[0][e] = a.gin[base + (size_t)Plan<L>::entry_pos(INV, t, e) * ls];
+    fft_line<C, L, INV, 1>(v, sm, 0, tw, t, si);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a.gout[base + (size_t)Plan<L>::exit_pos(INV, t, e) * ls] = v[0][e];
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+// ----------------------------------------------------------------------------
+// Energy / gradient pipeline (Eq. 1, coupled eGPE):
+//   x fwd (psi or trial psi; packed dipolar source) -> y fwd -> z fused
+//   (kinetic |k|^2/2, dipolar kernel, Parseval kinetic energy) -> y inv ->
+//   x inv + H psi, LHY, energy sums.
+// Workspace fields: 0, 1 = psi_1, psi_2; 2 = zeta = sum_j gdd_1j n_j + i sum_j gdd_2j n_j
+// (both dipolar potentials from one complex transform: the kernel is real and
+// even, so Phi_1 = Re and Phi_2 = Im of the inverse).
+// ----------------------------------------------------------------------------
+template <class R> struct EgUni {
+  int cur, slot, nsel;
+  R ca[2], cb[2];
+};
+
+template <class R_, int L_> struct XFwdEG {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NF = 3, NS = 0;
+  static constexpr bool INV = false, USES_LHY = false;
+  using Uni = EgUni<R>;
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) {
+    u.cur = __ldcg(&a.st->cur);
+    u.slot = a.flag ? (u.cur ^ 1) : u.cur;
+    u.nsel = __ldcg(&a.st->n) & 1;
+    for (int i = 0; i < 2; ++i) {
+      u.ca[i] = (R)__ldcg(&a.st->coef_a[i]);
+      u.cb[i] = (R)__ldcg(&a.st->coef_b[i]);
+    }
+  }
+  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8], double*) {
+    const C* src = a.psi[u.cur];
+    const C* pd = a.pb[u.nsel];
+    C* dst = a.psi[u.slot];
+    const size_t N = a.N;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      C p1 = cmk<C>(0, 0), p2 = cmk<C>(0, 0);
+      if (valid) {
+        const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e);
+        p1 = src[idx];
+        p2 = src[N + idx];
+        if (a.flag) {  // trial point on the geodesic (Sec. III), renormalised (Sec. V)
+          const C q1 = pd[idx], q2 = pd[N + idx];
+          p1 = cmk<C>(u.ca[0] * p1.x + u.cb[0] * q1.x, u.ca[0] * p1.y + u.cb[0] * q1.y);
+          p2 = cmk<C>(u.ca[1] * p2.x + u.cb[1] * q2.x, u.ca[1] * p2.y + u.cb[1] * q2.y);
+          dst[idx] = p1;
+          dst[N + idx] = p2;
+        }
+      }
+      const R n1 = cabs2(p1), n2 = cabs2(p2);
+      v[0][e] = p1;
+      v[1][e] = p2;
+      v[2][e] = cmk<C>(a.d11 * n1 + a.d12 * n2, a.d21 * n1 + a.d22 * n2);
+    }
+  }
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], double*,
+                               const LhyNode<R>*) {
+    if (!valid) return;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(false, t, e);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) a.W[(size_t)f * a.N + idx] = v[f][e];
+    }
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct ZEg {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NS = 2, AXIS = 2;
+  struct Uni {
+    int slot;
+  };
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) {
+    const int cur = __ldcg(&a.st->cur);
+    u.slot = a.flag ? (cur ^ 1) : cur;
+  }
+  static __device__ void run(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t, C* sm,
+                             const C* tw, ColIdx si, double* acc) {
+    C v[1][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[0][e] = a.W[base + (size_t)Plan<L>::entry_pos(false, t, e) * ls];
+    fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
+    const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
+    const R kxy2 = kx * kx + ky * ky;
+    R ekin = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const R kz = wavenum<R>(Plan<L>::exit_pos(false, t, e), a.nz, a.dkz);
+      const R k2 = kxy2 + kz * kz;
+      R mult;
+      if (f < 2) {
+        const R t2 = R(0.5) * k2;
+        ekin += t2 * cabs2(v[0][e]);
+        mult = t2 * a.invN;
+      } else {
+        mult = (k2 > R(0)) ? (R(3) * kz * kz / k2 - R(1)) * a.invN : R(0);
+      }
+      v[0][e] = cscale(v[0][e], mult);
+    }
+    if (f < 2) acc[f] += (double)ekin;
+    fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
+  }
+  static __device__ double* out(const KArgs<R>& a, Uni& u) { return a.st->egz[u.slot]; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct XInvEG {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NF = 3, NS = EG_NS;
+  static constexpr bool INV = true, USES_LHY = true;
+  using Uni = EgUni<R>;
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) { XFwdEG<R, L>::uniform(a, u); }
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], double*) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) v[f][e] = valid ? a.W[(size_t)f * a.N + idx] : cmk<C>(0, 0);
+    }
+  }
+  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8],
+                               double* acc, const LhyNode<R>* nodes) {
+    if (!valid) return;
+    const C* ps = a.psi[u.slot];
+    C* hp = a.hp[u.slot];
+    C* ax = a.ax[u.slot];
+    const size_t N = a.N;
+    const int y = row % a.ny, z = row / a.ny;
+    const R Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
+    const R vyz = a.vy * Y * Y + a.vz * Z * Z;
+    R s[EG_NS];
+#pragma unroll
+    for (int k = 0; k < EG_NS; ++k) s[k] = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int x = Plan<L>::exit_pos(true, t, e);
+      const size_t idx = (size_t)row * a.nx + x;
+      const C p1 = ps[idx], p2 = ps[N + idx];
+      const R n1 = cabs2(p1), n2 = cabs2(p2);
+      const R X = -a.Lx + (R)x * a.hx;
+      const R V = a.vx * X * X + vyz;
+      const R phi1 = v[2][e].x, phi2 = v[2][e].y;
+      R F, m1, m2;
+      lhy_point<R>(nodes, a.Q, n1, n2, F, m1, m2);
+      const R U1 = V + a.g11 * n1 + a.g12 * n2 + phi1 + m1;
+      const R U2 = V + a.g21 * n1 + a.g22 * n2 + phi2 + m2;
+      const C H1 = cmk<C>(v[0][e].x + U1 * p1.x, v[0][e].y + U1 * p1.y);
+      const C H2 = cmk<C>(v[1][e].x + U2 * p2.x, v[1][e].y + U2 * p2.y);
+      hp[idx] = H1;
+      hp[N + idx] = H2;
+      ax[idx] = cmk<C>(phi1, phi2);
+      ax[N + idx] = cmk<C>(m1, m2);
+      s[EG_TRAP] += V * (n1 + n2);
+      s[EG_CONTACT] += R(0.5) * (a.g11 * n1 * n1 + (a.g12 + a.g21) * n1 * n2 + a.g22 * n2 * n2);
+      s[EG_DIPOLAR] += R(0.5) * (n1 * phi1 + n2 * phi2);
+      s[EG_LHY] += F;
+      s[EG_MU1] += cdot(p1, H1);
+      s[EG_MU2] += cdot(p2, H2);
+      s[EG_NPHI1] += n1 * phi1;
+      s[EG_NPHI2] += n2 * phi2;
+      s[EG_NMUL1] += n1 * m1;
+      s[EG_NMUL2] += n2 * m2;
+      s[EG_NORM1] += n1;
+      s[EG_NORM2] += n2;
+    }
+#pragma unroll
+    for (int k = 0; k < EG_NS; ++k) acc[k] += (double)s[k];
+  }
+  static __device__ double* out(const KArgs<R>& a, Uni& u) { return a.st->eg[u.slot]; }
+  static __device__ void finish(const KArgs<R>& a, Uni&) {
+    if (a.ctrl) {
+      a.st->ffts += 6;
+      ctrl_after_eg(a.st, a.flag ? 1 : 0, a.trace);
+    }
+  }
+};
+
+// ----------------------------------------------------------------------------
+// Preconditioner pipeline (Sec. IV.B): r = H psi - mu psi, z = P^{-1} r with
+// P^{-1} = P_Delta^{-1} P_V^{-1}; sums for HS+ beta, projection and descent.
+// ----------------------------------------------------------------------------
+template <class R> struct PcUni {
+  int cur, nsel, rgiven;
+  R mu[2], shift[2], floor_[2];
+};
+template <class R> __device__ __forceinline__ void pc_uniform(const KArgs<R>& a, PcUni<R>& u) {
+  u.cur = __ldcg(&a.st->cur);
+  u.nsel = __ldcg(&a.st->n) & 1;
+  u.rgiven = a.flag;
+  const double fl = __ldcg(&a.st->opt.pv_floor);
+  for (int i = 0; i < 2; ++i) {
+    u.mu[i] = (R)__ldcg(&a.st->mu[i]);
+    const double sh = __ldcg(&a.st->shift[i]);
+    u.shift[i] = (R)sh;
+    u.floor_[i] = (R)(fl * sh);
+  }
+}
+
+// r_i at one point (stored unless given) and P_V^{-1} r_i when diag.
+template <class R>
+__device__ __forceinline__ void pc_point_prologue(const KArgs<R>& a, const PcUni<R>& u, size_t idx, R V, C2<R>& w1,
+                                                  C2<R>& w2) {
+  using C = C2<R>;
+  const size_t N = a.N;
+  C* rd = a.rb[u.nsel];
+  const C* ps = a.psi[u.cur];
+  C r1, r2;
+  if (u.rgiven) {
+    r1 = rd[idx];
+    r2 = rd[N + idx];
+  } else {
+    const C* hp = a.hp[u.cur];
+    const C p1 = ps[idx], p2 = ps[N + idx], h1 = hp[idx], h2 = hp[N + idx];
+    r1 = cmk<C>(h1.x - u.mu[0] * p1.x, h1.y - u.mu[0] * p1.y);
+    r2 = cmk<C>(h2.x - u.mu[1] * p2.x, h2.y - u.mu[1] * p2.y);
+    rd[idx] = r1;
+    rd[N + idx] = r2;
+  }
+  if (a.diag) {
+    const C p1 = ps[idx], p2 = ps[N + idx];
+    const R n1 = cabs2(p1), n2 = cabs2(p2);
+    const C ml = a.ax[u.cur][N + idx];
+    R P1 = u.shift[0] + V + a.g11 * n1 + a.g12 * n2 + ml.x;
+    R P2 = u.shift[1] + V + a.g21 * n1 + a.g22 * n2 + ml.y;
+    P1 = P1 > u.floor_[0] ? P1 : u.floor_[0];
+    P2 = P2 > u.floor_[1] ? P2 : u.floor_[1];
+    const R i1 = R(1) / P1, i2 = R(1) / P2;
+    w1 = cscale(r1, i1);
+    w2 = cscale(r2, i2);
+  } else {
+    w1 = r1;
+    w2 = r2;
+  }
+}
+
+// Sums of one point once z is known.
+template <class R>
+__device__ __forceinline__ void pc_point_sums(const KArgs<R>& a, const PcUni<R>& u, size_t idx, C2<R> z1, C2<R> z2,
+                                              R* s) {
+  using C = C2<R>;
+  const size_t N = a.N;
+  const C* ps = a.psi[u.cur];
+  const C* rc = a.rb[u.nsel];
+  const C* rp = a.rb[u.nsel ^ 1];
+  const C* pp = a.pb[u.nsel ^ 1];
+  const C r1 = rc[idx], r2 = rc[N + idx];
+  const C q1 = rp[idx], q2 = rp[N + idx];
+  const C d1 = pp[idx], d2 = pp[N + idx];
+  const C p1 = ps[idx], p2 = ps[N + idx];
+  const C dr1 = csub(r1, q1), dr2 = csub(r2, q2);
+  s[PC_SRZ] += cdot(dr1, z1) + cdot(dr2, z2);
+  s[PC_SRP] += cdot(dr1, d1) + cdot(dr2, d2);
+  s[PC_ZPSI1] += cdot(z1, p1);
+  s[PC_ZPSI2] += cdot(z2, p2);
+  s[PC_PPPSI1] += cdot(d1, p1);
+  s[PC_PPPSI2] += cdot(d2, p2);
+  s[PC_ZR1] += cdot(z1, r1);
+  s[PC_ZR2] += cdot(z2, r2);
+  s[PC_PPR1] += cdot(d1, r1);
+  s[PC_PPR2] += cdot(d2, r2);
+  s[PC_PSIR1] += cdot(p1, r1);
+  s[PC_PSIR2] += cdot(p2, r2);
+  s[PC_RR1] += cabs2(r1);
+  s[PC_RR2] += cabs2(r2);
+}
+
+template <class R_, int L_> struct XFwdPC {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NF = 2, NS = 0;
+  static constexpr bool INV = false, USES_LHY = false;
+  using Uni = PcUni<R>;
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) { pc_uniform(a, u); }
+  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], double*) {
+    const int y = row % a.ny, z = row / a.ny;
+    const R Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
+    const R vyz = a.vy * Y * Y + a.vz * Z * Z;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      v[0][e] = cmk<C>(0, 0);
+      v[1][e] = cmk<C>(0, 0);
+      if (valid) {
+        const int x = Plan<L>::entry_pos(false, t, e);
+        const R X = -a.Lx + (R)x * a.hx;
+        pc_point_prologue<R>(a, u, (size_t)row * a.nx + x, a.vx * X * X + vyz, v[0][e], v[1][e]);
+      }
+    }
+  }
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], double*,
+                               const LhyNode<R>*) {
+    if (!valid) return;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(false, t, e);
+      a.W[idx] = v[0][e];
+      a.W[(size_t)a.N + idx] = v[1][e];
+    }
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct ZPc {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NS = 0, AXIS = 2;
+  struct Uni {
+    R shift[2];
+  };
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) {
+    u.shift[0] = (R)__ldcg(&a.st->shift[0]);
+    u.shift[1] = (R)__ldcg(&a.st->shift[1]);
+  }
+  static __device__ void run(const KArgs<R>& a, Uni& u, int f, int x, int y, size_t base, size_t ls, int t, C* sm,
+                             const C* tw, ColIdx si, double*) {
+    C v[1][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[0][e] = a.W[base + (size_t)Plan<L>::entry_pos(false, t, e) * ls];
+    fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
+    const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
+    const R kxy2 = kx * kx + ky * ky;
+    const R sh = u.shift[f];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const R kz = wavenum<R>(Plan<L>::exit_pos(false, t, e), a.nz, a.dkz);
+      v[0][e] = cscale(v[0][e], a.invN / (sh + R(0.5) * (kxy2 + kz * kz)));
+    }
+    fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct XInvPC {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NF = 2, NS = PC_NS;
+  static constexpr bool INV = true, USES_LHY = false;
+  using Uni = PcUni<R>;
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) { pc_uniform(a, u); }
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], double*) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
+      v[0][e] = valid ? a.W[idx] : cmk<C>(0, 0);
+      v[1][e] = valid ? a.W[(size_t)a.N + idx] : cmk<C>(0, 0);
+    }
+  }
+  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], double* acc,
+                               const LhyNode<R>*) {
+    if (!valid) return;
+    R s[PC_NS];
+#pragma unroll
+    for (int k = 0; k < PC_NS; ++k) s[k] = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e);
+      a.z[idx] = v[0][e];
+      a.z[(size_t)a.N + idx] = v[1][e];
+      pc_point_sums<R>(a, u, idx, v[0][e], v[1][e], s);
+    }
+#pragma unroll
+    for (int k = 0; k < PC_NS; ++k) acc[k] += (double)s[k];
+  }
+  static __device__ double* out(const KArgs<R>& a, Uni&) { return a.st->pc; }
+  static __device__ void finish(const KArgs<R>& a, Uni&) {
+    if (a.ctrl) {
+      a.st->ffts += 4;
+      ctrl_after_pc(a.st);
+    }
+  }
+};
+
+// Pointwise preconditioner (modes none and diagonal): one pass, no transform.
+template <class R>
+__global__ void __launch_bounds__(256) pc_point_kernel(KArgs<R> a) {
+  using C = C2<R>;
+  if (!gate_open(a)) return;
+  __shared__ RedSmem<PC_NS> red;
+  PcUni<R> u;
+  pc_uniform(a, u);
+  double acc[PC_NS];
+#pragma unroll
+  for (int k = 0; k < PC_NS; ++k) acc[k] = 0.0;
+  const size_t N = a.N;
+  const size_t nxy = (size_t)a.nx * a.ny;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(idx % a.nx);
+    const int y = (int)((idx / a.nx) % a.ny);
+    const int z = (int)(idx / nxy);
+    const R X = -a.Lx + (R)x * a.hx, Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
+    const R V = a.vx * X * X + a.vy * Y * Y + a.vz * Z * Z;
+    C w1, w2;
+    pc_point_prologue<R>(a, u, idx, V, w1, w2);
+    a.z[idx] = w1;
+    a.z[N + idx] = w2;
+    R s[PC_NS];
+#pragma unroll
+    for (int k = 0; k < PC_NS; ++k) s[k] = 0;
+    pc_point_sums<R>(a, u, idx, w1, w2, s);
+#pragma unroll
+    for (int k = 0; k < PC_NS; ++k) acc[k] += (double)s[k];
+  }
+  if (reduce_blocks<PC_NS>(acc, a.partials, a.counter, a.st->pc, red)) {
+    if (threadIdx.x == 0 && a.ctrl) ctrl_after_pc(a.st);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Line-search pipeline (Sec. V): p = -z + beta p_prev - c psi (projected
+// direction), forward transforms of p (Parseval <p|T|p>), the packed dipolar
+// transform of rho = Re(psi conj p), and the pointwise second-variation sums.
+// ----------------------------------------------------------------------------
+template <class R> struct LcUni {
+  int cur, nsel, pgiven, fallback;
+  R beta, c[2];
+};
+template <class R> __device__ __forceinline__ void lc_uniform(const KArgs<R>& a, LcUni<R>& u) {
+  u.cur = __ldcg(&a.st->cur);
+  u.nsel = __ldcg(&a.st->n) & 1;
+  u.pgiven = a.flag;
+  u.fallback = __ldcg(&a.st->fallback);
+  u.beta = (R)__ldcg(&a.st->beta);
+  u.c[0] = (R)__ldcg(&a.st->c[0]);
+  u.c[1] = (R)__ldcg(&a.st->c[1]);
+}
+
+template <class R_, int L_> struct XFwdLC {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NF = 3, NS = 0;
+  static constexpr bool INV = false, USES_LHY = false;
+  using Uni = LcUni<R>;
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) { lc_uniform(a, u); }
+  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8], double*) {
+    const size_t N = a.N;
+    const C* ps = a.psi[u.cur];
+    C* pd = a.pb[u.nsel];
+    const C* pp = a.pb[u.nsel ^ 1];
+    const C* wsrc = u.fallback ? a.rb[u.nsel] : a.z;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      C q1 = cmk<C>(0, 0), q2 = cmk<C>(0, 0);
+      R rho1 = 0, rho2 = 0;
+      if (valid) {
+        const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e);
+        const C p1 = ps[idx], p2 = ps[N + idx];
+        if (u.pgiven) {
+          q1 = pd[idx];
+          q2 = pd[N + idx];
+        } else {
+          const C w1 = wsrc[idx], w2 = wsrc[N + idx];
+          q1 = cmk<C>(-w1.x - u.c[0] * p1.x, -w1.y - u.c[0] * p1.y);
+          q2 = cmk<C>(-w2.x - u.c[1] * p2.x, -w2.y - u.c[1] * p2.y);
+          if (u.beta != R(0)) {
+            const C d1 = pp[idx], d2 = pp[N + idx];
+            q1 = cmk<C>(q1.x + u.beta * d1.x, q1.y + u.beta * d1.y);
+            q2 = cmk<C>(q2.x + u.beta * d2.x, q2.y + u.beta * d2.y);
+          }
+          pd[idx] = q1;
+          pd[N + idx] = q2;
+        }
+        rho1 = cdot(p1, q1);
+        rho2 = cdot(p2, q2);
+      }
+      v[0][e] = q1;
+      v[1][e] = q2;
+      v[2][e] = cmk<C>(a.d11 * rho1 + a.d12 * rho2, a.d21 * rho1 + a.d22 * rho2);
+    }
+  }
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], double*,
+                               const LhyNode<R>*) {
+    if (!valid) return;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(false, t, e);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) a.W[(size_t)f * a.N + idx] = v[f][e];
+    }
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct ZLc {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NS = 2, AXIS = 2;
+  using Uni = NoUni;
+  static __device__ void uniform(const KArgs<R>&, Uni&) {}
+  static __device__ void run(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t, C* sm,
+                             const C* tw, ColIdx si, double* acc) {
+    C v[1][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[0][e] = a.W[base + (size_t)Plan<L>::entry_pos(false, t, e) * ls];
+    fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
+    const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
+    const R kxy2 = kx * kx + ky * ky;
+    if (f < 2) {  // <p_f | T | p_f> by Parseval: forward transform only
+      R tk = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const R kz = wavenum<R>(Plan<L>::exit_pos(false, t, e), a.nz, a.dkz);
+        tk += R(0.5) * (kxy2 + kz * kz) * cabs2(v[0][e]);
+      }
+      acc[f] += (double)tk;
+      return;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const R kz = wavenum<R>(Plan<L>::exit_pos(false, t, e), a.nz, a.dkz);
+      const R k2 = kxy2 + kz * kz;
+      const R mult = (k2 > R(0)) ? (R(3) * kz * kz / k2 - R(1)) * a.invN : R(0);
+      v[0][e] = cscale(v[0][e], mult);
+    }
+    fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
+  }
+  static __device__ double* out(const KArgs<R>& a, Uni&) { return a.st->lcz; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct XInvLC {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int L = L_, NF = 1, NS = LC_NS;
+  static constexpr bool INV = true, USES_LHY = true;
+  using Uni = LcUni<R>;
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) { lc_uniform(a, u); }
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], double*) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      v[0][e] = valid ? a.W[(size_t)2 * a.N + (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e)] : cmk<C>(0, 0);
+  }
+  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[1][8], double* acc,
+                               const LhyNode<R>* nodes) {
+    if (!valid) return;
+    const size_t N = a.N;
+    const C* ps = a.psi[u.cur];
+    const C* pd = a.pb[u.nsel];
+    const C* hp = a.hp[u.cur];
+    const C* ax = a.ax[u.cur];
+    const int y = row % a.ny, z = row / a.ny;
+    const R Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
+    const R vyz = a.vy * Y * Y + a.vz * Z * Z;
+    R s[LC_NS];
+#pragma unroll
+    for (int k = 0; k < LC_NS; ++k) s[k] = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int x = Plan<L>::exit_pos(true, t, e);
+      const size_t idx = (size_t)row * a.nx + x;
+      const C p1 = ps[idx], p2 = ps[N + idx];
+      const C q1 = pd[idx], q2 = pd[N + idx];
+      const C h1 = hp[idx], h2 = hp[N + idx];
+      const C phi = ax[idx], ml = ax[N + idx];
+      const R n1 = cabs2(p1), n2 = cabs2(p2);
+      const R a1 = cabs2(q1), a2 = cabs2(q2);
+      const R rho1 = cdot(p1, q1), rho2 = cdot(p2, q2);
+      const R X = -a.Lx + (R)x * a.hx;
+      const R V = a.vx * X * X + vyz;
+      const R U1 = V + a.g11 * n1 + a.g12 * n2 + phi.x + ml.x;
+      const R U2 = V + a.g21 * n1 + a.g22 * n2 + phi.y + ml.y;
+      s[LC_P1] += a1;
+      s[LC_P2] += a2;
+      s[LC_PSIP1] += rho1;
+      s[LC_PSIP2] += rho2;
+      s[LC_PH1] += cdot(q1, h1);
+      s[LC_PH2] += cdot(q2, h2);
+      s[LC_UPP1] += U1 * a1;
+      s[LC_UPP2] += U2 * a2;
+      s[LC_SRHO] += rho1 * (a.g11 * rho1 + a.g12 * rho2 + v[0][e].x) + rho2 * (a.g21 * rho1 + a.g22 * rho2 + v[0][e].y);
+      s[LC_HLHY] += lhy_hess<R>(nodes, a.Q, n1, n2, R(2) * rho1, R(2) * rho2);
+    }
+#pragma unroll
+    for (int k = 0; k < LC_NS; ++k) acc[k] += (double)s[k];
+  }
+  static __device__ double* out(const KArgs<R>& a, Uni&) { return a.st->lc; }
+  static __device__ void finish(const KArgs<R>& a, Uni&) {
+    if (a.ctrl) {
+      a.st->ffts += 4;
+      ctrl_after_lc(a.st);
+    }
+  }
+};
+
+// ----------------------------------------------------------------------------
+// Small pointwise kernels: retraction sums and apply, residual norm, casts.
+// ----------------------------------------------------------------------------
+// sums over (psi = gin, p = gout-as-input) for the standalone retraction
+template <class R> __global__ void __launch_bounds__(256) rt_sums_kernel(KArgs<R> a, const C2<R>* psi, const C2<R>* p) {
+  __shared__ RedSmem<RT_NS> red;
+  double acc[RT_NS];
+#pragma unroll
+  for (int k = 0; k < RT_NS; ++k) acc[k] = 0.0;
+  const size_t N = a.N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
+    for (int i = 0; i < 2; ++i) {
+      const C2<R> u = psi[i * N + idx], q = p[i * N + idx];
+      acc[RT_P1 + i] += (double)cabs2(q);
+      acc[RT_PSIP1 + i] += (double)cdot(u, q);
+      acc[RT_PSI1 + i] += (double)cabs2(u);
+    }
+  }
+  reduce_blocks<RT_NS>(acc, a.partials, a.counter, a.st->rt, red);
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) rt_apply_kernel(size_t N, const C2<R>* psi, const C2<R>* p, C2<R>* out, R a1,
+                                                        R b1, R a2, R b2) {
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
+    const C2<R> u1 = psi[idx], q1 = p[idx], u2 = psi[N + idx], q2 = p[N + idx];
+    out[idx] = cmk<C2<R>>(a1 * u1.x + b1 * q1.x, a1 * u1.y + b1 * q1.y);
+    out[N + idx] = cmk<C2<R>>(a2 * u2.x + b2 * q2.x, a2 * u2.y + b2 * q2.y);
+  }
+}
+
+// ||r_i||^2 of the current point (final report of a solve).
+template <class R> __global__ void __launch_bounds__(256) resnorm_kernel(KArgs<R> a) {
+  __shared__ RedSmem<2> red;
+  double acc[2] = {0.0, 0.0};
+  const int cur = __ldcg(&a.st->cur);
+  const R mu[2] = {(R)__ldcg(&a.st->mu[0]), (R)__ldcg(&a.st->mu[1])};
+  const size_t N = a.N;
+  const C2<R>* ps = a.psi[cur];
+  const C2<R>* hp = a.hp[cur];
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
+    for (int i = 0; i < 2; ++i) {
+      const C2<R> u = ps[i * N + idx], h = hp[i * N + idx];
+      const C2<R> r = cmk<C2<R>>(h.x - mu[i] * u.x, h.y - mu[i] * u.y);
+      acc[i] += (double)cabs2(r);
+    }
+  }
+  reduce_blocks<2>(acc, a.partials, a.counter, a.st->pca, red);
+}
+
+template <class A, class B> __global__ void cast_kernel(size_t n, const A* in, B* out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const A v = in[i];
+    B w;
+    w.x = (decltype(w.x))v.x;
+    w.y = (decltype(w.y))v.y;
+    out[i] = w;
+  }
+}
+
+}  // namespace egpe

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of libegpe.so (include/egpe.h): argument marshalling only.
+
+The functions keep the C names.  Field arguments are torch CUDA tensors of
+shape (2, nz, ny, nx) (complex128 for FP64/MIXED handles, complex64 for FP32
+handles) or raw device pointers; every step of the computation runs in the
+library's CUDA kernels.  There is no fallback: if the library cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Optional, Sequence
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libegpe.so")
+
+EGPE_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "non-finite value",
+          5: "not converged", 6: "stagnated", 7: "timeout", 8: "unsupported"}
+EGPE_FP64, EGPE_FP32, EGPE_MIXED = 0, 1, 2
+PRECOND = {"none": 0, "kinetic": 1, "diagonal": 2, "kinetic+diagonal": 3}
+
+
+class egpe_grid(ct.Structure):
+    _fields_ = [("n", ct.c_int * 3), ("L", ct.c_double * 3)]
+
+
+class egpe_params(ct.Structure):
+    _fields_ = [("g", (ct.c_double * 2) * 2), ("gdd", (ct.c_double * 2) * 2), ("lhy_kappa", ct.c_double),
+                ("lhy_eta_scale", ct.c_double), ("lhy_nodes", ct.c_int), ("trap", ct.c_double * 3)]
+
+
+class egpe_energy_terms(ct.Structure):
+    _fields_ = [("E", ct.c_double), ("kin", ct.c_double * 2), ("trap", ct.c_double), ("contact", ct.c_double),
+                ("dipolar", ct.c_double), ("lhy", ct.c_double), ("mu", ct.c_double * 2),
+                ("norm2", ct.c_double * 2), ("shift", ct.c_double * 2)]
+
+
+class egpe_solve_opts(ct.Structure):
+    _fields_ = [("precond", ct.c_int), ("beta_rule", ct.c_int), ("restart_period", ct.c_int),
+                ("max_iter", ct.c_int), ("armijo_max", ct.c_int), ("poll_every", ct.c_int),
+                ("use_graph", ct.c_int), ("psi_on_host", ct.c_int), ("tol_res", ct.c_double),
+                ("tol_dE", ct.c_double), ("armijo_c1", ct.c_double), ("theta_max", ct.c_double),
+                ("accept_rtol", ct.c_double), ("accept_rtol_fp32", ct.c_double), ("pv_floor", ct.c_double),
+                ("tol_fp32_switch", ct.c_double), ("max_iter_fp32", ct.c_int), ("trace_cap", ct.c_int),
+                ("trace", ct.c_void_p)]
+
+
+class egpe_trace_entry(ct.Structure):
+    _fields_ = [("n", ct.c_int), ("kind", ct.c_int), ("armijo", ct.c_int), ("flags", ct.c_int),
+                ("E", ct.c_double), ("E_trial", ct.c_double), ("res", ct.c_double), ("beta", ct.c_double),
+                ("alpha", ct.c_double), ("theta", ct.c_double * 2), ("Ep", ct.c_double), ("Epp", ct.c_double)]
+
+
+class egpe_report(ct.Structure):
+    _fields_ = [("status", ct.c_int), ("iters", ct.c_int), ("iters_fp32", ct.c_int), ("attempts", ct.c_int),
+                ("restarts", ct.c_int), ("armijo_steps", ct.c_int), ("trace_len", ct.c_int),
+                ("graph_launches", ct.c_int), ("E", ct.c_double), ("mu", ct.c_double * 2), ("res", ct.c_double),
+                ("seconds", ct.c_double), ("ffts", ct.c_longlong), ("kernels", ct.c_longlong)]
+
+
+_lib = None
+
+_SIGS = {
+    "egpe_create": (ct.c_int, [ct.POINTER(egpe_grid), ct.POINTER(egpe_params), ct.c_int, ct.c_int, ct.c_void_p,
+                               ct.POINTER(ct.c_void_p)]),
+    "egpe_destroy": (None, [ct.c_void_p]),
+    "egpe_energy_grad": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_double),
+                                    ct.POINTER(ct.c_double), ct.c_void_p]),
+    "egpe_energy_terms_eval": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(egpe_energy_terms),
+                                          ct.c_void_p]),
+    "egpe_line_coeffs": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_double)]),
+    "egpe_precondition": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    "egpe_retract": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_double),
+                                ct.c_void_p]),
+    "egpe_fft": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int]),
+    "egpe_ncg_solve": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(egpe_solve_opts),
+                                  ct.POINTER(egpe_report)]),
+    "egpe_default_solve_opts": (None, [ct.POINTER(egpe_solve_opts)]),
+    "egpe_status_string": (ct.c_char_p, [ct.c_int]),
+    "egpe_last_error": (ct.c_char_p, []),
+    "egpe_version": (ct.c_int, []),
+}
+
+
+def load(path: Optional[str] = None):
+    """Load libegpe.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libegpe.so not built ({p}); run paper_2510_24543_gb300.build.build()")
+    lib = ct.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class EgpeError(RuntimeError):
+    def __init__(self, where: str, status: int):
+        lib = load()
+        msg = lib.egpe_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({msg})")
+        self.status = status
+
+
+def _check(where: str, status: int):
+    if status != EGPE_OK:
+        raise EgpeError(where, status)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("field tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def make_grid(n, L) -> egpe_grid:
+    g = egpe_grid()
+    for a in range(3):
+        g.n[a] = int(n[a])
+        g.L[a] = float(L[a])
+    return g
+
+
+def make_params(g, gdd, kappa, eta_s, nodes, trap) -> egpe_params:
+    p = egpe_params()
+    for i in range(2):
+        for j in range(2):
+            p.g[i][j] = float(g[i][j])
+            p.gdd[i][j] = float(gdd[i][j])
+    p.lhy_kappa = float(kappa)
+    p.lhy_eta_scale = float(eta_s)
+    p.lhy_nodes = int(nodes)
+    for a in range(3):
+        p.trap[a] = float(trap[a])
+    return p
+
+
+def egpe_create(grids: Sequence[egpe_grid], params: Sequence[egpe_params], prec: int = EGPE_FP64,
+                stream: int = 0) -> int:
+    lib = load()
+    n = len(grids)
+    G = (egpe_grid * n)(*grids)
+    P = (egpe_params * n)(*params)
+    h = ct.c_void_p()
+    _check("egpe_create", lib.egpe_create(G, P, n, prec, ct.c_void_p(stream or None), ct.byref(h)))
+    return h.value
+
+
+def egpe_destroy(h: int):
+    if h:
+        load().egpe_destroy(ct.c_void_p(h))
+
+
+def egpe_energy_terms_eval(h: int, inst: int, psi, grad=None) -> dict:
+    t = egpe_energy_terms()
+    _check("egpe_energy_terms_eval",
+           load().egpe_energy_terms_eval(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), ct.byref(t),
+                                         ct.c_void_p(_ptr(grad))))
+    return dict(E=t.E, kin1=t.kin[0], kin2=t.kin[1], trap=t.trap, contact=t.contact, dipolar=t.dipolar,
+                lhy=t.lhy, mu=(t.mu[0], t.mu[1]), norm2=(t.norm2[0], t.norm2[1]), shift=(t.shift[0], t.shift[1]))
+
+
+def egpe_energy_grad(h: int, inst: int, psi, grad=None):
+    E = ct.c_double()
+    mu = (ct.c_double * 2)()
+    _check("egpe_energy_grad", load().egpe_energy_grad(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), ct.byref(E),
+                                                       mu, ct.c_void_p(_ptr(grad))))
+    return E.value, (mu[0], mu[1])
+
+
+def egpe_line_coeffs(h: int, inst: int, psi, p):
+    c = (ct.c_double * 3)()
+    _check("egpe_line_coeffs", load().egpe_line_coeffs(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)),
+                                                       ct.c_void_p(_ptr(p)), c))
+    return c[0], c[1], c[2]
+
+
+def egpe_precondition(h: int, inst: int, mode: int, psi, r, z):
+    _check("egpe_precondition", load().egpe_precondition(ct.c_void_p(h), inst, int(mode), ct.c_void_p(_ptr(psi)),
+                                                         ct.c_void_p(_ptr(r)), ct.c_void_p(_ptr(z))))
+
+
+def egpe_retract(h: int, inst: int, psi, p, theta, out):
+    th = (ct.c_double * 2)(float(theta[0]), float(theta[1]))
+    _check("egpe_retract", load().egpe_retract(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), ct.c_void_p(_ptr(p)),
+                                               th, ct.c_void_p(_ptr(out))))
+
+
+def egpe_fft(h: int, inst: int, x, out, nfields: int, inverse: bool = False):
+    _check("egpe_fft", load().egpe_fft(ct.c_void_p(h), inst, ct.c_void_p(_ptr(x)), ct.c_void_p(_ptr(out)),
+                                       int(nfields), 1 if inverse else 0))
+
+
+def egpe_default_solve_opts() -> egpe_solve_opts:
+    o = egpe_solve_opts()
+    load().egpe_default_solve_opts(ct.byref(o))
+    return o
+
+
+def egpe_ncg_solve(h: int, psis, opts: egpe_solve_opts, n_inst: int = 1, trace_cap: int = 0):
+    """Runs the solver in place on psis (list of tensors/pointers).  Returns
+    (status, [report dicts], [trace dicts of instance 0])."""
+    lib = load()
+    ptrs = (ct.c_void_p * n_inst)(*[ct.c_void_p(_ptr(x)) for x in psis])
+    reps = (egpe_report * n_inst)()
+    tr = None
+    if trace_cap > 0:
+        tr = (egpe_trace_entry * trace_cap)()
+        opts.trace = ct.cast(tr, ct.c_void_p)
+        opts.trace_cap = trace_cap
+    status = lib.egpe_ncg_solve(ct.c_void_p(h), ptrs, ct.byref(opts), reps)
+    if status in (1, 2, 3):
+        raise EgpeError("egpe_ncg_solve", status)
+    out = []
+    for r in reps:
+        out.append(dict(status=r.status, iters=r.iters, iters_fp32=r.iters_fp32, attempts=r.attempts,
+                        restarts=r.restarts, armijo_steps=r.armijo_steps, trace_len=r.trace_len,
+                        graph_launches=r.graph_launches, E=r.E, mu=(r.mu[0], r.mu[1]), res=r.res,
+                        seconds=r.seconds, ffts=r.ffts, kernels=r.kernels))
+    trace = []
+    if tr is not None:
+        for k in range(out[0]["trace_len"]):
+            e = tr[k]
+            trace.append(dict(n=e.n, kind=e.kind, armijo=e.armijo, flags=e.flags, E=e.E, E_trial=e.E_trial,
+                              res=e.res, beta=e.beta, alpha=e.alpha, theta=(e.theta[0], e.theta[1]), Ep=e.Ep,
+                              Epp=e.Epp))
+    return status, out, trace
+
+
+def egpe_status_string(s: int) -> str:
+    return load().egpe_status_string(int(s)).decode()
+
+
+def egpe_version() -> int:
+    return load().egpe_version()
+
+
+def params_from_workload(w) -> egpe_params:
+    """C parameter struct of a workload from paper_2510_24543_gb300.inputs."""
+    return make_params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
