@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Benchmark of the eGPE ground-state solver hot path on one GB300 per rank.
+
+Headline: NCG iterations per second on the 128^3 two-component dipolar eGPE
+(the stripe/supersolid couplings on [-16,16]^2 x [-8,8]) with FP32 fields and
+FP64 reductions/controller, the FP64 path timed beside it, time to ground
+state (mixed vs FP64, relative energy 1e-8), and the HBM roofline of the
+dominant kernel.  One "step" is one attempt of the NCG loop body (precondition,
+line-search coefficients, trial energy/gradient, controller); steps are timed
+with CUDA events on the solver's stream, in chunks that each restart from the
+seeded start so the solver never finishes inside a timed region.
+
+  python bench.py --gpus N --steps K --warmup W          (this implementation)
+  python bench.py --impl reference --steps K --warmup W  (the FP64 CPU oracle)
+
+Under torchrun every rank solves its own instance (seed + rank: independent
+problems, weak scaling, no collective on the data path); rank 0 prints one
+JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-ground-state & NCG iters/s at 128^3 (mixed vs FP64), % HBM roofline"
+UNIT = "NCG iters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3p")
+    ap.add_argument("--precond", default="kinetic+diagonal")
+    ap.add_argument("--chunk", type=int, default=25)
+    ap.add_argument("--no-tts", action="store_true", help="skip time-to-ground-state")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--fp32-switch", type=float, default=1e-4)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the GPU work runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        self.index = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel_name, workload):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, or None
+    if the summary is missing or was taken on other kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        from paper_2510_24543_gb300 import build as B
+        with open(p) as f:
+            d = json.load(f)
+        rec = d.get("kernels", {}).get(kernel_name)
+        if not rec or d.get("sources") != B._digest() or rec.get("workload") != workload:
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2510_24543_gb300 import build as B
+    from paper_2510_24543_gb300 import egpe as E
+    from paper_2510_24543_gb300 import inputs as I
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    B.build()
+    E.load()
+    w0 = I.PRESETS[args.workload]
+    w = I.Workload(w0.name, w0.n, w0.L, w0.trap, w0.g, w0.gdd, w0.lhy_c, w0.seed + rank, w0.precond, w0.lhy_nodes)
+    N = w.points
+    psi0_np = I.gaussian_start(w)
+    stream = torch.cuda.Stream()
+    grid = E.make_grid(w.n, w.L)
+    prm = E.params_from_workload(w)
+    h = E.egpe_create([grid], [prm], E.EGPE_MIXED, stream.cuda_stream)
+    psi64 = torch.from_numpy(psi0_np).to("cuda")
+    psi32 = psi64.to(torch.complex64)
+    pc = E.PRECOND[args.precond]
+    clocks = Clocks(local)
+    clocks.start()
+
+    def opts(**kw):
+        o = E.egpe_default_solve_opts()
+        o.precond = pc
+        o.tol_res = 0.0
+        o.max_iter = 1 << 30
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def timed_steps(engine, psi, K, W, chunk):
+        """K attempts of the NCG loop body timed with CUDA events on the solver
+        stream, W untimed warm-up attempts before each chunk."""
+        o = opts()
+        tot_ms, iters, launches, done = 0.0, 0, 0, 0
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        while done < K:
+            n = min(chunk, K - done)
+            E.egpe_solver_start(h, 0, engine, psi, o)
+            E.egpe_solver_step(h, 0, engine, W)
+            r0 = E.egpe_solver_read(h, 0, engine)
+            torch.cuda.synchronize()
+            barrier()
+            ev0.record(stream)
+            E.egpe_solver_step(h, 0, engine, n)
+            ev1.record(stream)
+            ev1.synchronize()
+            torch.cuda.synchronize()
+            barrier()
+            r1 = E.egpe_solver_read(h, 0, engine)
+            if r1["status"] != 5:
+                raise RuntimeError(f"solver finished inside a timed region ({r1}); lower --chunk")
+            tot_ms += ev0.elapsed_time(ev1)
+            iters += r1["iters"] - r0["iters"]
+            launches += r1["kernels"] - r0["kernels"] - 1  # minus the read's residual kernel
+            done += n
+        return tot_ms, iters, launches
+
+    # ---- headline: FP32 fields (mixed precision) iterations per second
+    ms32, it32, launch32 = timed_steps(1, psi32, args.steps, args.warmup, args.chunk)
+    ms32 = max_over_ranks(ms32)
+    it32_all = sum_over_ranks(it32)
+    value = it32_all / (ms32 * 1e-3)
+    ms_per_step = ms32 / args.steps
+
+    # ---- FP64 path beside it
+    k64 = min(args.steps, 10)
+    ms64, it64, launch64 = timed_steps(0, psi64, k64, args.warmup, args.chunk)
+    ms64 = max_over_ranks(ms64)
+    fp64 = {"iters_per_s": sum_over_ranks(it64) / (ms64 * 1e-3), "ms_per_step": ms64 / k64, "steps": k64,
+            "gpu_launches": launch64}
+
+    # ---- per-kernel device times (roofline of the dominant kernel)
+    hbm, peak_kind = peaks()
+    prof32 = E.egpe_profile_attempt(h, 0, 1, psi32, pc, reps=5)
+    prof64 = E.egpe_profile_attempt(h, 0, 0, psi64, pc, reps=3)
+    att_ms = sum(t for _, t, _ in prof32)
+    att_bytes = sum(b for _, _, b in prof32)
+    dom = max(prof32, key=lambda x: x[1])
+    ach = dom[2] / (dom[1] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom[0], "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "peak_kind": peak_kind + " (burst copy)",
+                "traffic": traffic_record(dom[0], args.workload),
+                "algorithmic_bytes": dom[2], "ms_per_launch": dom[1], "share_of_attempt": round(dom[1] / att_ms, 4),
+                "attempt": {"ms": round(att_ms, 4), "algorithmic_bytes": att_bytes,
+                            "achieved_GBs": round(att_bytes / (att_ms * 1e-3) / 1e9, 1),
+                            "frac": round(att_bytes / (att_ms * 1e-3) / 1e9 / hbm, 4)},
+                "kernels": [{"name": n, "ms": round(t, 5), "GBs": round(b / (t * 1e-3) / 1e9, 1)} for n, t, b in prof32]}
+    dom64 = max(prof64, key=lambda x: x[1])
+    fp64["dominant_kernel"] = {"name": dom64[0], "ms": dom64[1], "share": round(dom64[1] / sum(t for _, t, _ in prof64), 4),
+                               "bound": "alu (FP64)"}
+    fp64["kernels"] = [{"name": n, "ms": round(t, 4)} for n, t, _ in prof64]
+
+    # ---- end to end through the public solve call with host buffers
+    h32 = E.egpe_create([grid], [prm], E.EGPE_FP32, stream.cuda_stream)
+    host32 = torch.from_numpy(psi0_np.astype("complex64")).pin_memory()
+    calls = max(1, math.ceil(args.steps / args.chunk))
+    e2e_iters, e2e_s = 0, 0.0
+    o = opts(max_iter=args.chunk, psi_on_host=1)
+    buf = host32.clone().pin_memory()
+    E.egpe_ncg_solve(h32, [buf.data_ptr()], o, 1)  # warm-up call (graph capture)
+    for _ in range(calls):
+        buf.copy_(host32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, reps, _ = E.egpe_ncg_solve(h32, [buf.data_ptr()], o, 1)
+        e2e_s += time.perf_counter() - t0
+        e2e_iters += reps[0]["iters"]
+    e2e_s = max_over_ranks(e2e_s)
+    field_bytes = 2 * N * 8
+    e2e = {"value": sum_over_ranks(e2e_iters) / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": field_bytes / args.chunk, "d2h_bytes_per_step": field_bytes / args.chunk,
+           "call": f"egpe_ncg_solve(FP32 fields, host psi) running {args.chunk} iterations per call; "
+                   "per-call H2D psi and D2H psi+report amortised per iteration"}
+    E.egpe_destroy(h32)
+
+    # ---- time to ground state: mixed (FP32 phase + FP64 polish) vs plain FP64
+    tts = None
+    if not args.no_tts:
+        try:
+            tts = time_to_ground_state(E, h, grid, prm, psi64, pc, args.fp32_switch)
+        except Exception as ex:  # reported, not fatal for the iteration numbers
+            tts = {"error": str(ex)[:300]}
+    clk = clocks.stop()
+    E.egpe_destroy(h)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, f64 reductions/controller",
+                "data": "synthetic (seeded Gaussian + 1% noise start)",
+                "config": {"workload": w0.name + " on [-16,16]^2x[-8,8], trap (0.5,1,2), g=300/300/280, "
+                                       "g_dd=420/420/400, LHY c=100",
+                           "grid": list(w.n), "precond": args.precond, "lhy_nodes": w.lhy_nodes,
+                           "parallelism": f"replicas x{world} (one instance per GPU)",
+                           "l2": "inputs larger than L2: ~25 complex64 fields of 16.8 MB resident per instance",
+                           "step": "one NCG attempt (precondition + line coefficients + trial E/grad + controller)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launch32,
+                "clocks": clk, "fp64": fp64, "time_to_ground_state": tts}
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def time_to_ground_state(E, h, grid, prm, psi64, pc, fp32_switch):
+    """Wall time of egpe_ncg_solve from the seeded start until |E - E_ref| <=
+    1e-8 |E_ref|, mixed (FP32 phase then FP64 polish) against FP64 only.
+    E_ref: FP64 solve to ||r|| <= 1e-10.  The residual target r* is the
+    residual of the reference run at its first point within the accuracy."""
+    o = E.egpe_default_solve_opts()
+    o.precond = pc
+    o.tol_res = 1e-10
+    o.max_iter = 5000
+    ref = psi64.clone()
+    hd = E.egpe_create([grid], [prm], E.EGPE_FP64)
+    try:
+        st, reps, tr = E.egpe_ncg_solve(hd, [ref], o, 1, trace_cap=8000)
+        Eref = reps[0]["E"]
+        rstar = None
+        acc = [t for t in tr if t["flags"] & 1]
+        for k, t in enumerate(acc):
+            if abs(t["E_trial"] - Eref) <= 1e-8 * abs(Eref):
+                rstar = acc[k + 1]["res"] if k + 1 < len(acc) else reps[0]["res"]
+                break
+        if rstar is None:
+            raise RuntimeError("reference never reached the accuracy")
+        o.tol_res = rstar
+        x = psi64.clone()
+        st, r64, _ = E.egpe_ncg_solve(hd, [x], o, 1)
+        t64 = r64[0]
+        o.tol_fp32_switch = fp32_switch
+        x = psi64.clone()
+        st, rm, _ = E.egpe_ncg_solve(h, [x], o, 1)
+        tm = rm[0]
+        return {"E_ref": Eref, "ref_iters": reps[0]["iters"], "ref_status": reps[0]["status"], "res_target": rstar,
+                "fp64": {"seconds": t64["seconds"], "iters": t64["iters"], "rel_err": abs(t64["E"] - Eref) / abs(Eref)},
+                "mixed": {"seconds": tm["seconds"], "iters": tm["iters"], "iters_fp32": tm["iters_fp32"],
+                          "rel_err": abs(tm["E"] - Eref) / abs(Eref), "fp32_switch": fp32_switch},
+                "speedup": t64["seconds"] / tm["seconds"]}
+    finally:
+        E.egpe_destroy(hd)
+
+
+def cpu_baseline(w):
+    """The FP64 oracle as it stands on this host: one NCG iteration (precondition,
+    line coefficients, trial evaluation) of the same 128^3 workload."""
+    import numpy as np  # noqa: F401
+
+    import oracle as O
+    from paper_2510_24543_gb300 import inputs as I
+
+    g = O.Grid(w.n, w.L)
+    prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
+    psi = I.gaussian_start(w)
+    t0 = time.perf_counter()
+    O.evaluate(g, prm, psi)
+    t_eval = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, rep = O.ncg_solve(g, prm, psi, O.SolveOpts(precond=w.precond if w.precond in O.PRECOND_MODES else "kinetic",
+                                                   max_iter=1, tol_res=0.0))
+    t_solve = time.perf_counter() - t0
+    t_it = max(t_solve - t_eval, 1e-9)
+    return {"value": round(1.0 / t_it, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle NCG iteration on the full {w.n[0]}x{w.n[1]}x{w.n[2]} workload "
+                      f"({t_it:.1f} s; its initial evaluation, {t_eval:.1f} s, timed separately and excluded); "
+                      "NumPy FFT and pointwise code, single thread"}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """The FP64 CPU oracle timed on this host on the same workload and metric."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2510_24543_gb300 import inputs as I
+
+    w = I.PRESETS[args.workload]
+    g = O.Grid(w.n, w.L)
+    prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
+    psi = I.gaussian_start(w)
+    budget = 150.0
+    t0 = time.perf_counter()
+    ev = O.evaluate(g, prm, psi)
+    t_eval = time.perf_counter() - t0
+    # warm-up: one evaluation counts as the oracle's warm-up (no JIT, no cache to fill)
+    per_it = 2.0 * t_eval
+    k = max(1, min(args.steps, int(budget / max(per_it, 1e-3))))
+    t0 = time.perf_counter()
+    _, rep = O.ncg_solve(g, prm, psi, O.SolveOpts(precond=args.precond, max_iter=k, tol_res=0.0))
+    t_solve = time.perf_counter() - t0 - t_eval
+    done = rep["iters"]
+    value = done / t_solve
+    line = {"metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world, "steps": done,
+            "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t_solve / done, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Gaussian + 1% noise start)", "impl": "reference",
+            "config": {"workload": w.name, "grid": list(w.n), "precond": args.precond},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {done} oracle NCG iterations on the full workload (bounded to "
+                                       f"~{int(budget)} s), initial evaluation excluded"},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -19,7 +19,7 @@
  *          the caller owns them; the library never frees them.
  * Grid:    periodic box [-L_a, L_a) with n_a points per axis, h_a = 2L_a/n_a,
  *          x_a[j] = -L_a + j h_a; wavenumbers k_a[j] = (pi/L_a)(j or j - n_a).
- *          Supported n_a: 8, 16, 32, 64, 128, 256.
+ *          Supported n_a: 16, 32, 64, 128, 256.
  * Product: <a, b> = dV sum conj(a) b, dV = hx hy hz.
  * Model:   per-particle normalised couplings (N_i -> 1 in Eq. 1):
  *          E = sum_i <psi_i, T psi_i> + int V (n1+n2) + 1/2 int sum_ij g_ij n_i n_j
@@ -196,12 +196,44 @@ egpe_status egpe_retract(egpe_handle* h, int inst, const void* psi, const void* 
  * every other entry point uses. */
 egpe_status egpe_fft(egpe_handle* h, int inst, const void* in, void* out, int nfields, int inverse);
 
+/* Diagnostic: device time of every kernel of one solver attempt
+ * (precondition, line coefficients, trial evaluation: Algorithm 1 loop body),
+ * measured with a CUDA event pair around each launch over `reps` attempts
+ * started from psi (no graph).  engine: 0 the FP64 path (psi complex128), 1
+ * the FP32 path (psi complex64); an engine the handle lacks is INVALID_ARG.
+ * For each of the *count kernels (at most cap): names + 48 k holds a
+ * NUL-terminated name, ms[k] the mean time per launch and bytes[k] the
+ * algorithmic DRAM bytes per launch (fields read plus fields written).  All
+ * output arrays are host memory owned by the caller. */
+egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
+                                 int cap, char* names, double* ms, double* bytes, int* count);
+
 /* Ground state by preconditioned NCG (Algorithm 1).  psi_inout[i] is the start
  * and receives the result for instance i (device pointers unless
  * opts->psi_on_host).  reports: host array of n_inst (may be NULL).
  * Returns the status of the first instance that did not converge, else OK. */
 egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts* opts,
                            egpe_report* reports);
+
+/* Stepping interface: the phases of egpe_ncg_solve one by one, for callers
+ * that interleave their own work (event timing, checkpoints) with the solver.
+ * engine: 0 the FP64 path (psi complex128), 1 the FP32 path (psi complex64;
+ * the acceptance allowance is opts->accept_rtol_fp32); an engine the handle
+ * lacks is EGPE_ERR_INVALID_ARG.  Options as in egpe_ncg_solve (the trace and
+ * psi_on_host fields are ignored).
+ * egpe_solver_start: copies psi (device) in, evaluates it and prepares the
+ *   captured attempt; returns once the work is enqueued.
+ * egpe_solver_step: enqueues `attempts` attempts of the loop body of
+ *   Algorithm 1 (precondition, line coefficients, trial evaluation and the
+ *   on-device controller); asynchronous; attempts after the solver has
+ *   finished are no-ops on the device.
+ * egpe_solver_read: waits for the stream, fills *report (status
+ *   EGPE_ERR_NOT_CONVERGED while the solver is still running, res = ||r|| of
+ *   the current point) and copies the current psi to psi_out (device; may be
+ *   NULL). */
+egpe_status egpe_solver_start(egpe_handle* h, int inst, int engine, const void* psi, const egpe_solve_opts* opts);
+egpe_status egpe_solver_step(egpe_handle* h, int inst, int engine, int attempts);
+egpe_status egpe_solver_read(egpe_handle* h, int inst, int engine, egpe_report* report, void* psi_out);
 
 /* Defaults: kinetic preconditioner, HS+, K_r = 20, tol_res 1e-8, c1 1e-4,
  * 30 halvings, theta_max = pi/2, accept_rtol 1e-13 (FP64) / 2e-6 (FP32),

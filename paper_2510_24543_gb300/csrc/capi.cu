@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "egpe.h"
@@ -261,13 +262,100 @@ egpe_status egpe_fft(egpe_handle* h, int inst, const void* in, void* out, int nf
   return h->e64[inst]->fft((const double2*)in, (double2*)out, nfields, inverse ? 1 : 0);
 }
 
+egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
+                                 int cap, char* names, double* ms, double* bytes, int* count) {
+  if (bad_inst(h, inst) || !psi || precond < 0 || precond > 3 || reps < 1 || cap < 1 || !names || !ms || !bytes ||
+      !count)
+    return EGPE_ERR_INVALID_ARG;
+  std::vector<std::string> nm;
+  std::vector<double> t, b;
+  egpe_status s;
+  if (engine == 0 && !h->e64.empty()) {
+    s = h->e64[inst]->profile_attempt((const double2*)psi, precond, reps, nm, t, b);
+  } else if (engine == 1 && !h->e32.empty()) {
+    s = h->e32[inst]->profile_attempt((const float2*)psi, precond, reps, nm, t, b);
+  } else {
+    return EGPE_ERR_INVALID_ARG;
+  }
+  if (s != EGPE_OK) return s;
+  const int n = (int)std::min<size_t>(nm.size(), (size_t)cap);
+  for (int k = 0; k < n; ++k) {
+    std::strncpy(names + 48 * k, nm[k].c_str(), 47);
+    names[48 * k + 47] = 0;
+    ms[k] = t[k];
+    bytes[k] = b[k];
+  }
+  *count = n;
+  return EGPE_OK;
+}
+
+static bool opts_ok(const egpe_solve_opts& o) {
+  return !(o.precond < 0 || o.precond > 3 || o.beta_rule != 0 || o.max_iter < 0 || o.armijo_max < 0 ||
+           o.armijo_max > 60 || !(o.tol_res >= 0.0) || !(o.theta_max > 0.0) || !(o.pv_floor > 0.0) ||
+           o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace));
+}
+
+egpe_status egpe_solver_start(egpe_handle* h, int inst, int engine, const void* psi, const egpe_solve_opts* opts) {
+  if (bad_inst(h, inst) || !psi || !opts || !opts_ok(*opts)) return EGPE_ERR_INVALID_ARG;
+  const egpe_solve_opts& o = *opts;
+  if (engine == 0 && !h->e64.empty()) {
+    auto* e = h->e64[inst];
+    egpe_status s = e->load_psi(psi, cudaMemcpyDeviceToDevice);
+    if (s != EGPE_OK) return s;
+    return e->solve_begin(o, 0, o.max_iter, o.tol_res, o.accept_rtol, false, 0);
+  }
+  if (engine == 1 && !h->e32.empty()) {
+    auto* e = h->e32[inst];
+    egpe_status s = e->load_psi(psi, cudaMemcpyDeviceToDevice);
+    if (s != EGPE_OK) return s;
+    return e->solve_begin(o, 1, o.max_iter, o.tol_res, o.accept_rtol_fp32, false, 0);
+  }
+  return EGPE_ERR_INVALID_ARG;
+}
+
+egpe_status egpe_solver_step(egpe_handle* h, int inst, int engine, int attempts) {
+  if (bad_inst(h, inst) || attempts < 0) return EGPE_ERR_INVALID_ARG;
+  if (engine == 0 && !h->e64.empty()) return h->e64[inst]->solve_launch(attempts);
+  if (engine == 1 && !h->e32.empty()) return h->e32[inst]->solve_launch(attempts);
+  return EGPE_ERR_INVALID_ARG;
+}
+
+egpe_status egpe_solver_read(egpe_handle* h, int inst, int engine, egpe_report* report, void* psi_out) {
+  if (bad_inst(h, inst) || !report) return EGPE_ERR_INVALID_ARG;
+  egpe::SolveRun run{};
+  egpe_status s;
+  if (engine == 0 && !h->e64.empty()) {
+    s = h->e64[inst]->solve_finish(run, nullptr, 0, 0);
+    if (s == EGPE_OK && psi_out) s = h->e64[inst]->store_psi(psi_out, cudaMemcpyDeviceToDevice);
+  } else if (engine == 1 && !h->e32.empty()) {
+    s = h->e32[inst]->solve_finish(run, nullptr, 0, 0);
+    if (s == EGPE_OK && psi_out) s = h->e32[inst]->store_psi(psi_out, cudaMemcpyDeviceToDevice);
+  } else {
+    return EGPE_ERR_INVALID_ARG;
+  }
+  if (s != EGPE_OK) return s;
+  std::memset(report, 0, sizeof(*report));
+  report->status = run.status;
+  report->iters = run.n;
+  report->iters_fp32 = engine == 1 ? run.n : 0;
+  report->attempts = run.attempts;
+  report->restarts = run.restarts;
+  report->armijo_steps = run.armijo_total;
+  report->graph_launches = run.launches;
+  report->E = run.E;
+  report->mu[0] = run.mu[0];
+  report->mu[1] = run.mu[1];
+  report->res = run.res;
+  report->ffts = run.ffts;
+  report->kernels = run.kernels;
+  return EGPE_OK;
+}
+
 egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts* opts,
                            egpe_report* reports) {
   if (!h || !psi_inout || !opts) return EGPE_ERR_INVALID_ARG;
   const egpe_solve_opts& o = *opts;
-  if (o.precond < 0 || o.precond > 3 || o.beta_rule != 0 || o.max_iter < 0 || o.armijo_max < 0 ||
-      o.armijo_max > 60 || !(o.tol_res >= 0.0) || !(o.theta_max > 0.0) || !(o.pv_floor > 0.0) ||
-      o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace)) {
+  if (!opts_ok(o)) {
     egpe::set_error_msg("egpe_ncg_solve: bad options");
     return EGPE_ERR_INVALID_ARG;
   }

@@ -7,6 +7,7 @@
 
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "egpe.h"
 #include "common.cuh"
@@ -19,7 +20,7 @@ void set_error(const char* what, cudaError_t e);
 void set_error_msg(const std::string& msg);
 
 struct SolveRun {
-  int status, n, attempts, restarts, armijo_total, trace_len, launches;
+  int status, n, attempts, restarts, armijo_total, trace_len, launches, phase;
   double E, mu[2], res;
   long long ffts, kernels;
 };
@@ -48,6 +49,18 @@ template <class R> class Engine {
   egpe_status store_psi(void* dst, cudaMemcpyKind kind);
   egpe_status solve(const egpe_solve_opts& o, int fp32_phase, int max_iter, double tol_res, double accept_rtol,
                     SolveRun& run, egpe_trace_entry* trace_out, int trace_cap, int trace_offset);
+  // Per-kernel device times of `reps` solver attempts from psi (CUDA events
+  // around every launch, no graph): names, mean ms and algorithmic bytes.
+  egpe_status profile_attempt(const C* psi, int precond, int reps, std::vector<std::string>& names,
+                              std::vector<double>& ms, std::vector<double>& bytes);
+  // Stepping interface (the same phases egpe_ncg_solve runs): begin loads
+  // nothing -- psi must be in slot 0 -- evaluates the start and prepares the
+  // graph; launch enqueues attempts without waiting; finish reads the state.
+  egpe_status solve_begin(const egpe_solve_opts& o, int fp32_phase, int max_iter, double tol_res,
+                          double accept_rtol, bool want_trace, int trace_cap);
+  egpe_status solve_launch(int attempts);
+  egpe_status solve_poll(int& phase);
+  egpe_status solve_finish(SolveRun& run, egpe_trace_entry* trace_out, int trace_cap, int trace_offset);
   C* current_psi();  // valid after solve (device)
   C* psi_slot0();    // psi buffer 0 (start of a solve)
 
@@ -71,6 +84,17 @@ template <class R> class Engine {
   egpe_status plain_x(int inverse, const KArgs<R>& a);
   egpe_status plain_col(int axis, int inverse, const KArgs<R>& a);
   int occupancy(const void* fn, int block, size_t smem);
+  void t_begin(const char* name, int L, double bytes);
+  void t_end();
+
+  struct KTime {
+    std::string name;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  std::vector<KTime> tlog_;
+  bool timing_ = false;
+  size_t tpos_ = 0;
 
   KArgs<R>* base_ = nullptr;  // host copy of the common kernel arguments
   egpe_grid grid_{};
@@ -90,6 +114,8 @@ template <class R> class Engine {
   long long kernels_ = 0;
   std::unordered_map<unsigned long long, int> occ_;
   cudaGraphExec_t graph_[4] = {nullptr, nullptr, nullptr, nullptr};
+  int run_mode_ = 0, run_graph_ = 1;
+  long long run_k0_ = 0, run_launches_ = 0, per_attempt_ = 0;
   int graph_max_iter_[4] = {0, 0, 0, 0};
 };
 

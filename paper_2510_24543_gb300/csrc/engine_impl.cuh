@@ -22,6 +22,12 @@ namespace egpe {
     }                                         \
   } while (0)
 
+#define EGPE_TRY(x)                 \
+  do {                              \
+    egpe_status s_ = (x);           \
+    if (s_ != EGPE_OK) return s_;   \
+  } while (0)
+
 static inline bool supported_len(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
 
 // Gauss-Legendre rule on [0,1] by Newton iteration on P_Q (long double).
@@ -173,6 +179,11 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
 }
 
 template <class R> void Engine<R>::destroy() {
+  for (auto& k : tlog_) {
+    cudaEventDestroy(k.a);
+    cudaEventDestroy(k.b);
+  }
+  tlog_.clear();
   for (auto& gx : graph_)
     if (gx) {
       cudaGraphExecDestroy(gx);
@@ -212,6 +223,69 @@ template <class R> int Engine<R>::occupancy(const void* fn, int block, size_t sm
   return occ;
 }
 
+template <class R> void Engine<R>::t_begin(const char* name, int L, double bytes) {
+  if (tpos_ >= tlog_.size()) {
+    KTime k;
+    cudaEventCreate(&k.a);
+    cudaEventCreate(&k.b);
+    tlog_.push_back(k);
+  }
+  KTime& k = tlog_[tpos_];
+  k.name = std::string(name) + (L ? " L=" + std::to_string(L) : std::string());
+  k.bytes = bytes;
+  cudaEventRecord(k.a, stream);
+}
+
+template <class R> void Engine<R>::t_end() {
+  cudaEventRecord(tlog_[tpos_].b, stream);
+  ++tpos_;
+}
+
+template <class R>
+egpe_status Engine<R>::profile_attempt(const C* psi, int precond, int reps, std::vector<std::string>& names,
+                                       std::vector<double>& ms, std::vector<double>& bytes) {
+  egpe_solve_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.precond = precond & 3;
+  o.restart_period = 20;
+  o.armijo_max = 30;
+  o.armijo_c1 = 1e-4;
+  o.theta_max = 1.5707963267948966;
+  o.pv_floor = 1e-2;
+  EGPE_CUDA(cudaMemcpyAsync(base_->psi[0], psi, 2 * N * sizeof(C), cudaMemcpyDeviceToDevice, stream));
+  EGPE_TRY(reset_state(&o, sizeof(R) == 4, 1 << 30, 0.0, sizeof(R) == 4 ? 1e-6 : 1e-13));
+  EGPE_CUDA(cudaMemsetAsync(base_->rb[0], 0, 8 * N * sizeof(C), stream));
+  EGPE_TRY(enq_eg(0, GATE_ALWAYS, 1));
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  names.clear();
+  ms.clear();
+  bytes.clear();
+  timing_ = true;
+  for (int r = 0; r < reps; ++r) {
+    tpos_ = 0;
+    egpe_status s = enq_attempt(o.precond);
+    if (s != EGPE_OK) {
+      timing_ = false;
+      return s;
+    }
+    EGPE_CUDA(cudaStreamSynchronize(stream));
+    if (names.empty()) {
+      for (size_t k = 0; k < tpos_; ++k) {
+        names.push_back(tlog_[k].name);
+        bytes.push_back(tlog_[k].bytes);
+        ms.push_back(0.0);
+      }
+    }
+    for (size_t k = 0; k < tpos_ && k < ms.size(); ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, tlog_[k].a, tlog_[k].b);
+      ms[k] += t / reps;
+    }
+  }
+  timing_ = false;
+  return EGPE_OK;
+}
+
 template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> a) {
   constexpr int L = Op::L, TPL = L / 8, NF = Op::NF, NS = Op::NS;
   constexpr int LP = row_len_padded<R, L>();
@@ -226,7 +300,9 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   const int groups = (rows + mx - 1) / mx;
   const int occ = occupancy((const void*)xpass_kernel<Op>, block, smem);
   const int grid = std::min(groups, std::min(occ * nsm_, 16384));
+  if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
   xpass_kernel<Op><<<grid, block, smem, stream>>>(a);
+  if (timing_) t_end();
   ++kernels_;
   EGPE_CUDA(cudaGetLastError());
   return EGPE_OK;
@@ -243,7 +319,9 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   const int tiles = (nx / M) * other * a.nf;
   const int occ = occupancy((const void*)colpass_kernel<Op>, block, smem);
   const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
+  if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
   colpass_kernel<Op><<<grid, block, smem, stream>>>(a);
+  if (timing_) t_end();
   ++kernels_;
   EGPE_CUDA(cudaGetLastError());
   return EGPE_OK;
@@ -296,11 +374,6 @@ template <class R> egpe_status Engine<R>::plain_col(int axis, int inverse, const
   return EGPE_ERR_UNSUPPORTED;
 }
 
-#define EGPE_TRY(x)                 \
-  do {                              \
-    egpe_status s_ = (x);           \
-    if (s_ != EGPE_OK) return s_;   \
-  } while (0)
 
 // Energy / gradient pipeline: 6 complex 3D transforms.
 template <class R> egpe_status Engine<R>::enq_eg(int trial, int gate, int ctrl) {
@@ -344,7 +417,9 @@ template <class R> egpe_status Engine<R>::enq_pc(int mode, int gate, int ctrl, i
   a.ctrl = ctrl;
   const int occ = occupancy((const void*)pc_point_kernel<R>, 256, 0);
   const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)std::min(occ * nsm_, 16384));
+  if (timing_) t_begin("pointwise precond sums", 0, (a.diag ? 13.0 : 12.0) * N * sizeof(C));
   pc_point_kernel<R><<<grid, 256, 0, stream>>>(a);
+  if (timing_) t_end();
   ++kernels_;
   EGPE_CUDA(cudaGetLastError());
   return EGPE_OK;
@@ -531,11 +606,10 @@ template <class R> egpe_status Engine<R>::store_psi(void* dst, cudaMemcpyKind ki
 }
 
 template <class R>
-egpe_status Engine<R>::solve(const egpe_solve_opts& o, int fp32_phase, int max_iter, double tol_res,
-                             double accept_rtol, SolveRun& run, egpe_trace_entry* trace_out, int trace_cap,
-                             int trace_offset) {
+egpe_status Engine<R>::solve_begin(const egpe_solve_opts& o, int fp32_phase, int max_iter, double tol_res,
+                                   double accept_rtol, bool want_trace, int trace_cap) {
   const int mode = o.precond & 3;
-  if (trace_out && trace_cap > trace_alloc_) {
+  if (want_trace && trace_cap > trace_alloc_) {
     // the trace buffer is captured by the graphs: allocate once, generously
     const int want = std::max(trace_cap, 65536);
     for (auto& gx : graph_)
@@ -550,15 +624,18 @@ egpe_status Engine<R>::solve(const egpe_solve_opts& o, int fp32_phase, int max_i
     base_->trace = trace_;
   }
   egpe_solve_opts oo = o;
-  oo.trace_cap = trace_out ? trace_cap : 0;
-  oo.trace = trace_out;
+  oo.trace_cap = want_trace ? trace_cap : 0;
+  oo.trace = want_trace ? (void*)1 : nullptr;
   EGPE_TRY(reset_state(&oo, fp32_phase, max_iter, tol_res, accept_rtol));
   // r and p history start at zero (beta = 0 at n = 0 reads them)
   EGPE_CUDA(cudaMemsetAsync(base_->rb[0], 0, 8 * N * sizeof(C), stream));
   EGPE_TRY(enq_eg(0, GATE_ALWAYS, 1));
-  const long long k0 = kernels_;
-  long long per_attempt = 0;
-  if (o.use_graph) {
+  run_k0_ = kernels_;
+  run_mode_ = mode;
+  run_graph_ = o.use_graph ? 1 : 0;
+  run_launches_ = 0;
+  per_attempt_ = 0;
+  if (run_graph_) {
     if (!graph_[mode]) {
       cudaGraph_t g = nullptr;
       EGPE_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
@@ -583,25 +660,33 @@ egpe_status Engine<R>::solve(const egpe_solve_opts& o, int fp32_phase, int max_i
       }
       kernels_ = kb;
     }
-    per_attempt = graph_max_iter_[mode];
+    per_attempt_ = graph_max_iter_[mode];
   }
-  const int poll = std::max(1, o.poll_every);
-  const long long max_launch = (long long)(max_iter + 2) * (long long)(o.armijo_max + 2) + 4;
-  long long launches = 0;
-  while (launches < max_launch) {
-    for (int k = 0; k < poll; ++k) {
-      if (o.use_graph) {
-        EGPE_CUDA(cudaGraphLaunch(graph_[mode], stream));
-        kernels_ += per_attempt;
-      } else {
-        EGPE_TRY(enq_attempt(mode));
-      }
-      ++launches;
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::solve_launch(int attempts) {
+  for (int k = 0; k < attempts; ++k) {
+    if (run_graph_) {
+      EGPE_CUDA(cudaGraphLaunch(graph_[run_mode_], stream));
+      kernels_ += per_attempt_;
+    } else {
+      EGPE_TRY(enq_attempt(run_mode_));
     }
-    EGPE_CUDA(cudaMemcpyAsync(&st_host_->phase, &st_->phase, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    EGPE_CUDA(cudaStreamSynchronize(stream));
-    if (st_host_->phase == PH_DONE) break;
+    ++run_launches_;
   }
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::solve_poll(int& phase) {
+  EGPE_CUDA(cudaMemcpyAsync(&st_host_->phase, &st_->phase, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  phase = st_host_->phase;
+  return EGPE_OK;
+}
+
+template <class R>
+egpe_status Engine<R>::solve_finish(SolveRun& run, egpe_trace_entry* trace_out, int trace_cap, int trace_offset) {
   {
     KArgs<R> a = *base_;
     const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)nsm_ * 8);
@@ -616,14 +701,15 @@ egpe_status Engine<R>::solve(const egpe_solve_opts& o, int fp32_phase, int max_i
   run.attempts = hs.attempts;
   run.restarts = hs.restarts;
   run.armijo_total = hs.armijo_total;
-  run.launches = (int)launches;
+  run.launches = (int)run_launches_;
   run.E = hs.E;
   run.mu[0] = hs.mu[0];
   run.mu[1] = hs.mu[1];
   run.res = sqrt((hs.pca[0] + hs.pca[1]) * dV);
   run.ffts = hs.ffts;
-  run.kernels = kernels_ - k0;
+  run.kernels = kernels_ - run_k0_;
   run.trace_len = 0;
+  run.phase = hs.phase;
   if (trace_out && hs.trace_len > 0) {
     const int n = std::min(hs.trace_len, trace_cap);
     std::vector<TraceDev> tmp(n);
@@ -648,6 +734,22 @@ egpe_status Engine<R>::solve(const egpe_solve_opts& o, int fp32_phase, int max_i
     }
   }
   return EGPE_OK;
+}
+
+template <class R>
+egpe_status Engine<R>::solve(const egpe_solve_opts& o, int fp32_phase, int max_iter, double tol_res,
+                             double accept_rtol, SolveRun& run, egpe_trace_entry* trace_out, int trace_cap,
+                             int trace_offset) {
+  EGPE_TRY(solve_begin(o, fp32_phase, max_iter, tol_res, accept_rtol, trace_out != nullptr, trace_cap));
+  const int poll = std::max(1, o.poll_every);
+  const long long max_launch = (long long)(max_iter + 2) * (long long)(o.armijo_max + 2) + 4;
+  while (run_launches_ < max_launch) {
+    EGPE_TRY(solve_launch(poll));
+    int phase = 0;
+    EGPE_TRY(solve_poll(phase));
+    if (phase == PH_DONE) break;
+  }
+  return solve_finish(run, trace_out, trace_cap, trace_offset);
 }
 
 }  // namespace egpe

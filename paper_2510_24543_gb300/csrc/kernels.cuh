@@ -159,6 +159,8 @@ struct NoUni {};
 template <class R_, int L_, bool INV_> struct XPlain {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "x-plain";
+  static double alg_bytes(const KArgs<R>& a) { return 2.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 1, NS = 0;
   static constexpr bool INV = INV_, USES_LHY = false;
   using Uni = NoUni;
@@ -181,6 +183,8 @@ template <class R_, int L_, bool INV_> struct XPlain {
 template <class R_, int L_, int AXIS_, bool INV_> struct ColPlain {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = AXIS_ == 1 ? "y-pass" : "z-pass";
+  static double alg_bytes(const KArgs<R>& a) { return 2.0 * a.nf * a.N * sizeof(C); }
   static constexpr int L = L_, NS = 0, AXIS = AXIS_;
   static constexpr bool INV = INV_;
   using Uni = NoUni;
@@ -215,6 +219,8 @@ template <class R> struct EgUni {
 template <class R_, int L_> struct XFwdEG {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "x-fwd energy";
+  static double alg_bytes(const KArgs<R>& a) { return (a.flag ? 9.0 : 5.0) * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 3, NS = 0;
   static constexpr bool INV = false, USES_LHY = false;
   using Uni = EgUni<R>;
@@ -270,6 +276,8 @@ template <class R_, int L_> struct XFwdEG {
 template <class R_, int L_> struct ZEg {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "z fused energy";
+  static double alg_bytes(const KArgs<R>& a) { return 6.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NS = 2, AXIS = 2;
   struct Uni {
     int slot;
@@ -313,6 +321,8 @@ template <class R_, int L_> struct ZEg {
 template <class R_, int L_> struct XInvEG {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "x-inv energy+LHY";
+  static double alg_bytes(const KArgs<R>& a) { return 9.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 3, NS = EG_NS;
   static constexpr bool INV = true, USES_LHY = true;
   using Uni = EgUni<R>;
@@ -474,6 +484,8 @@ __device__ __forceinline__ void pc_point_sums(const KArgs<R>& a, const PcUni<R>&
 template <class R_, int L_> struct XFwdPC {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "x-fwd precond";
+  static double alg_bytes(const KArgs<R>& a) { return (a.diag ? 9.0 : 8.0) * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 2, NS = 0;
   static constexpr bool INV = false, USES_LHY = false;
   using Uni = PcUni<R>;
@@ -510,6 +522,8 @@ template <class R_, int L_> struct XFwdPC {
 template <class R_, int L_> struct ZPc {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "z fused precond";
+  static double alg_bytes(const KArgs<R>& a) { return 4.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NS = 0, AXIS = 2;
   struct Uni {
     R shift[2];
@@ -543,6 +557,8 @@ template <class R_, int L_> struct ZPc {
 template <class R_, int L_> struct XInvPC {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "x-inv precond sums";
+  static double alg_bytes(const KArgs<R>& a) { return 12.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 2, NS = PC_NS;
   static constexpr bool INV = true, USES_LHY = false;
   using Uni = PcUni<R>;
@@ -637,6 +653,8 @@ template <class R> __device__ __forceinline__ void lc_uniform(const KArgs<R>& a,
 template <class R_, int L_> struct XFwdLC {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "x-fwd line dir";
+  static double alg_bytes(const KArgs<R>& a) { return 11.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 3, NS = 0;
   static constexpr bool INV = false, USES_LHY = false;
   using Uni = LcUni<R>;
@@ -694,6 +712,8 @@ template <class R_, int L_> struct XFwdLC {
 template <class R_, int L_> struct ZLc {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "z line coeffs";
+  static double alg_bytes(const KArgs<R>& a) { return 4.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NS = 2, AXIS = 2;
   using Uni = NoUni;
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
@@ -733,6 +753,8 @@ template <class R_, int L_> struct ZLc {
 template <class R_, int L_> struct XInvLC {
   using R = R_;
   using C = C2<R>;
+  static constexpr const char* NAME = "x-inv line sums+LHY";
+  static double alg_bytes(const KArgs<R>& a) { return 9.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 1, NS = LC_NS;
   static constexpr bool INV = true, USES_LHY = true;
   using Uni = LcUni<R>;

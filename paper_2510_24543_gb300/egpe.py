@@ -77,6 +77,12 @@ _SIGS = {
     "egpe_fft": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_int]),
     "egpe_ncg_solve": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(egpe_solve_opts),
                                   ct.POINTER(egpe_report)]),
+    "egpe_profile_attempt": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int, ct.c_int,
+                                        ct.c_char_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                                        ct.POINTER(ct.c_int)]),
+    "egpe_solver_start": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.POINTER(egpe_solve_opts)]),
+    "egpe_solver_step": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int]),
+    "egpe_solver_read": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(egpe_report), ct.c_void_p]),
     "egpe_default_solve_opts": (None, [ct.POINTER(egpe_solve_opts)]),
     "egpe_status_string": (ct.c_char_p, [ct.c_int]),
     "egpe_last_error": (ct.c_char_p, []),
@@ -204,6 +210,23 @@ def egpe_fft(h: int, inst: int, x, out, nfields: int, inverse: bool = False):
                                        int(nfields), 1 if inverse else 0))
 
 
+def egpe_profile_attempt(h: int, inst: int, engine: int, psi, precond: int, reps: int = 5, cap: int = 64):
+    """[(name, mean ms, algorithmic bytes)] for every kernel of one solver attempt."""
+    names = ct.create_string_buffer(48 * cap)
+    ms = (ct.c_double * cap)()
+    by = (ct.c_double * cap)()
+    n = ct.c_int()
+    _check("egpe_profile_attempt", load().egpe_profile_attempt(ct.c_void_p(h), inst, engine, ct.c_void_p(_ptr(psi)),
+                                                               int(precond), int(reps), cap, names, ms, by,
+                                                               ct.byref(n)))
+    raw = names.raw
+    out = []
+    for k in range(n.value):
+        nm = raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
+        out.append((nm, ms[k], by[k]))
+    return out
+
+
 def egpe_default_solve_opts() -> egpe_solve_opts:
     o = egpe_solve_opts()
     load().egpe_default_solve_opts(ct.byref(o))
@@ -224,12 +247,7 @@ def egpe_ncg_solve(h: int, psis, opts: egpe_solve_opts, n_inst: int = 1, trace_c
     status = lib.egpe_ncg_solve(ct.c_void_p(h), ptrs, ct.byref(opts), reps)
     if status in (1, 2, 3):
         raise EgpeError("egpe_ncg_solve", status)
-    out = []
-    for r in reps:
-        out.append(dict(status=r.status, iters=r.iters, iters_fp32=r.iters_fp32, attempts=r.attempts,
-                        restarts=r.restarts, armijo_steps=r.armijo_steps, trace_len=r.trace_len,
-                        graph_launches=r.graph_launches, E=r.E, mu=(r.mu[0], r.mu[1]), res=r.res,
-                        seconds=r.seconds, ffts=r.ffts, kernels=r.kernels))
+    out = [_report_dict(r) for r in reps]
     trace = []
     if tr is not None:
         for k in range(out[0]["trace_len"]):
@@ -238,6 +256,28 @@ def egpe_ncg_solve(h: int, psis, opts: egpe_solve_opts, n_inst: int = 1, trace_c
                               res=e.res, beta=e.beta, alpha=e.alpha, theta=(e.theta[0], e.theta[1]), Ep=e.Ep,
                               Epp=e.Epp))
     return status, out, trace
+
+
+def _report_dict(r) -> dict:
+    return dict(status=r.status, iters=r.iters, iters_fp32=r.iters_fp32, attempts=r.attempts, restarts=r.restarts,
+                armijo_steps=r.armijo_steps, trace_len=r.trace_len, graph_launches=r.graph_launches, E=r.E,
+                mu=(r.mu[0], r.mu[1]), res=r.res, seconds=r.seconds, ffts=r.ffts, kernels=r.kernels)
+
+
+def egpe_solver_start(h: int, inst: int, engine: int, psi, opts: egpe_solve_opts):
+    _check("egpe_solver_start", load().egpe_solver_start(ct.c_void_p(h), inst, engine, ct.c_void_p(_ptr(psi)),
+                                                         ct.byref(opts)))
+
+
+def egpe_solver_step(h: int, inst: int, engine: int, attempts: int):
+    _check("egpe_solver_step", load().egpe_solver_step(ct.c_void_p(h), inst, engine, int(attempts)))
+
+
+def egpe_solver_read(h: int, inst: int, engine: int, psi_out=None) -> dict:
+    r = egpe_report()
+    _check("egpe_solver_read", load().egpe_solver_read(ct.c_void_p(h), inst, engine, ct.byref(r),
+                                                       ct.c_void_p(_ptr(psi_out))))
+    return _report_dict(r)
 
 
 def egpe_status_string(s: int) -> str:
