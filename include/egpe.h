@@ -160,6 +160,28 @@ typedef struct egpe_handle egpe_handle;
 egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n_inst,
                         egpe_precision prec, void* cuda_stream, egpe_handle** out);
 
+/* Energy and gradient without any device allocation.  The paper has no
+ * counterpart: this is a deployment variant of egpe_energy_grad for callers
+ * that cannot allocate device memory -- applications whose device memory is
+ * owned entirely by their own pool allocator (a cudaMalloc from a library
+ * would fail or eat into a budget already handed out) and latency-sensitive
+ * loops that must never enter the CUDA allocator -- and so cannot create a
+ * handle (egpe_create allocates the workspaces).  Same kernels and arithmetic
+ * as egpe_energy_grad on an EGPE_FP64 handle.  psi: complex128 device field
+ * (2,nz,ny,nx), read only; grad: complex128 device output H_i psi_i or NULL;
+ * E, mu: host outputs or NULL; cuda_stream: a cudaStream_t (NULL: the legacy
+ * default stream); the call waits for its stream before returning.
+ * Limit: 16 or 32 points per axis (at most 32^3 points); larger grids return
+ * EGPE_ERR_INVALID_ARG with the reason in egpe_last_error().
+ * Workspace: one fixed 4 MiB device array inside the library, held on every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address; make that first call before
+ * any stream capture begins.  Every call shares the array and it keeps the
+ * last call's contents (what must start at zero is cleared by each call):
+ * calls whose work overlaps on the GPU race on it and must be serialised. */
+egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egpe_params* params, const void* psi,
+                                     double* E, double mu[2], void* grad, void* cuda_stream);
+
 /* Release every resource of the handle (NULL is a no-op). */
 void egpe_destroy(egpe_handle* h);
 

@@ -83,6 +83,9 @@ _SIGS = {
     "egpe_solver_start": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.POINTER(egpe_solve_opts)]),
     "egpe_solver_step": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int]),
     "egpe_solver_read": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(egpe_report), ct.c_void_p]),
+    "egpe_energy_grad_noalloc": (ct.c_int, [ct.POINTER(egpe_grid), ct.POINTER(egpe_params), ct.c_void_p,
+                                            ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_void_p,
+                                            ct.c_void_p]),
     "egpe_default_solve_opts": (None, [ct.POINTER(egpe_solve_opts)]),
     "egpe_status_string": (ct.c_char_p, [ct.c_int]),
     "egpe_last_error": (ct.c_char_p, []),
@@ -184,6 +187,17 @@ def egpe_energy_grad(h: int, inst: int, psi, grad=None):
     mu = (ct.c_double * 2)()
     _check("egpe_energy_grad", load().egpe_energy_grad(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), ct.byref(E),
                                                        mu, ct.c_void_p(_ptr(grad))))
+    return E.value, (mu[0], mu[1])
+
+
+def egpe_energy_grad_noalloc(grid: egpe_grid, params: egpe_params, psi, grad=None, stream: int = 0):
+    """Energy and gradient with the library's fixed workspace (no device
+    allocation; at most 32 points per axis).  Returns (E, (mu1, mu2))."""
+    E = ct.c_double()
+    mu = (ct.c_double * 2)()
+    _check("egpe_energy_grad_noalloc",
+           load().egpe_energy_grad_noalloc(ct.byref(grid), ct.byref(params), ct.c_void_p(_ptr(psi)), ct.byref(E), mu,
+                                           ct.c_void_p(_ptr(grad)), ct.c_void_p(stream or None)))
     return E.value, (mu[0], mu[1])
 
 
