@@ -92,8 +92,15 @@ struct DevState {
 
 // Gauss-Legendre node constants of the LHY u-integral, in field precision.
 template <class R> struct LhyNode {
-  R e11, e22, e2;  // eta11(u), eta22(u), 2 eta12(u) eta21(u)
-  R w;             // kappa eta_s^{-5/2} w_q
+  R w;      // 3 u_q^2 - 1
+  R W;      // kappa eta_s^{-5/2} times the quadrature weight on [0,1]
+  R Ww;     // W w
+  R e12sq;  // eta12(u_q)^2 = (g12 + gdd12 w)^2
+};
+
+// Couplings entering the LHY terms (symmetric: eta12 = eta21).
+template <class R> struct LhyCoef {
+  R g11, g22, g12, d11, d22, d12;
 };
 
 }  // namespace egpe

@@ -188,10 +188,11 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
       }
       const long double u = 0.5L * (1.0L + x), w = 1.0L / ((1.0L - x * x) * dp * dp);
       const long double sdd = 3.0L * u * u - 1.0L;
-      nodes[q].e11 = (double)(p.g[0][0] + p.gdd[0][0] * sdd);
-      nodes[q].e22 = (double)(p.g[1][1] + p.gdd[1][1] * sdd);
-      nodes[q].e2 = (double)(2.0L * (p.g[0][1] + p.gdd[0][1] * sdd) * (p.g[1][0] + p.gdd[1][0] * sdd));
-      nodes[q].w = (double)(c5 * w);
+      const long double e12 = p.g[0][1] + p.gdd[0][1] * sdd;
+      nodes[q].w = (double)sdd;
+      nodes[q].W = (double)(c5 * w);
+      nodes[q].Ww = (double)(c5 * w * sdd);
+      nodes[q].e12sq = (double)(e12 * e12);
     }
   }
   double2* twd = (double2*)(base + kOffTw);

@@ -120,14 +120,11 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
     const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
     for (int q = 0; q < Q; ++q) {
       const long double s = 3.0L * u[q] * u[q] - 1.0L;
-      const long double e11 = p.g[0][0] + p.gdd[0][0] * s;
-      const long double e22 = p.g[1][1] + p.gdd[1][1] * s;
       const long double e12 = p.g[0][1] + p.gdd[0][1] * s;
-      const long double e21 = p.g[1][0] + p.gdd[1][0] * s;
-      h[q].e11 = (R)e11;
-      h[q].e22 = (R)e22;
-      h[q].e2 = (R)(2.0L * e12 * e21);
-      h[q].w = (R)(c5 * w[q]);
+      h[q].w = (R)s;
+      h[q].W = (R)(c5 * w[q]);
+      h[q].Ww = (R)(c5 * w[q] * s);
+      h[q].e12sq = (R)(e12 * e12);
     }
     EGPE_CUDA(cudaMalloc(&nodes_, Q * sizeof(LhyNode<R>)));
     EGPE_CUDA(cudaMemcpy(nodes_, h.data(), Q * sizeof(LhyNode<R>), cudaMemcpyHostToDevice));

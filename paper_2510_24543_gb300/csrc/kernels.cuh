@@ -60,6 +60,17 @@ template <class R> __device__ __forceinline__ bool gate_open(const KArgs<R>& a) 
   return a.gate == GATE_NEW_ITER ? (ph == PH_NEW_ITER) : (ph != PH_DONE);
 }
 
+template <class R> __device__ __forceinline__ LhyCoef<R> lhy_coef(const KArgs<R>& a) {
+  LhyCoef<R> c;
+  c.g11 = a.g11;
+  c.g22 = a.g22;
+  c.g12 = a.g12;
+  c.d11 = a.d11;
+  c.d22 = a.d22;
+  c.d12 = a.d12;
+  return c;
+}
+
 template <class R> __device__ __forceinline__ R wavenum(int j, int n, R dk) {
   return dk * (R)(j < (n >> 1) ? j : j - n);
 }
@@ -358,7 +369,7 @@ template <class R_, int L_> struct XInvEG {
       const R V = a.vx * X * X + vyz;
       const R phi1 = v[2][e].x, phi2 = v[2][e].y;
       R F, m1, m2;
-      lhy_point<R>(nodes, a.Q, n1, n2, F, m1, m2);
+      lhy_point<R>(nodes, a.Q, lhy_coef(a), n1, n2, F, m1, m2);
       const R U1 = V + a.g11 * n1 + a.g12 * n2 + phi1 + m1;
       const R U2 = V + a.g21 * n1 + a.g22 * n2 + phi2 + m2;
       const C H1 = cmk<C>(v[0][e].x + U1 * p1.x, v[0][e].y + U1 * p1.y);
@@ -802,7 +813,7 @@ template <class R_, int L_> struct XInvLC {
       s[LC_UPP1] += U1 * a1;
       s[LC_UPP2] += U2 * a2;
       s[LC_SRHO] += rho1 * (a.g11 * rho1 + a.g12 * rho2 + v[0][e].x) + rho2 * (a.g21 * rho1 + a.g22 * rho2 + v[0][e].y);
-      s[LC_HLHY] += lhy_hess<R>(nodes, a.Q, n1, n2, R(2) * rho1, R(2) * rho2);
+      s[LC_HLHY] += lhy_hess<R>(nodes, a.Q, lhy_coef(a), n1, n2, R(2) * rho1, R(2) * rho2);
     }
 #pragma unroll
     for (int k = 0; k < LC_NS; ++k) acc[k] += (double)s[k];

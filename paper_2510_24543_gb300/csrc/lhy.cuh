@@ -2,10 +2,14 @@
 // over a Gauss-Legendre rule on u in [0,1] (Eq. 1 LHY term, Sec. II branch
 // potentials and mu_LHY, Sec. V second variations).
 //
-// At node u: eta_ij = g_ij + gdd_ij (3u^2 - 1), delta = eta11 n1 - eta22 n2,
-// s = sqrt(delta^2 + 4 eta12 eta21 n1 n2), V_+- = eta11 n1 + eta22 n2 +- s.
-// Negative V contributes max(V,0)^{5/2}; where s = 0 every term divided by s
-// is 0 (the two branches coincide there).  One rsqrt gives both s and 1/s.
+// At node u, with w = 3u^2 - 1: eta_ij = g_ij + gdd_ij w,
+//   A = eta11 n1 + eta22 n2 = A0 + A1 w,  delta = eta11 n1 - eta22 n2 = D0 + D1 w,
+//   s = sqrt(delta^2 + 4 eta12^2 n1 n2),  V_+- = A +- s   (eta12 = eta21: the couplings
+// are symmetric).  Negative V contributes max(V,0)^{5/2}; where s = 0 every
+// term divided by s is 0 (the two branches coincide there).  Because eta is
+// linear in w, the per-point coefficients A0, A1, D0, D1 and the polynomial
+// coefficients of sigma_i(w) are formed once per point, and the node loop only
+// carries what depends on the square roots.
 #pragma once
 #include "common.cuh"
 
@@ -13,8 +17,6 @@ namespace egpe {
 
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 
 // Smallest s^2 treated as nonzero (below it the rsqrt of the field precision
 // would overflow or lose its meaning).
@@ -22,84 +24,112 @@ template <class R> __device__ __forceinline__ R s2_min();
 template <> __device__ __forceinline__ double s2_min<double>() { return 1e-300; }
 template <> __device__ __forceinline__ float s2_min<float>() { return 1e-36f; }
 
-// F = sum_q w_q sum_+- max(V,0)^{5/2};  mu_i = dF/dn_i
-//   = sum_q w_q (5/2) sum_+- max(V,0)^{3/2} (eta_ii +- sigma_i/s),
-// sigma_1 = eta11 delta + 2 eta12 eta21 n2, sigma_2 = -eta22 delta + 2 eta12 eta21 n1.
-// The weights already include kappa eta_s^{-5/2}.
+// sqrt(max(v,0)) without branches.  FP64: the library square root; FP32:
+// v * rsqrt(v) (MUFU), a few ulp, with the argument of rsqrt kept positive.
+__device__ __forceinline__ double sqrt_pos(double v) { return sqrt(fmax(v, 0.0)); }
+__device__ __forceinline__ float sqrt_pos(float v) {
+  const float c = fmaxf(v, 0.0f);
+  return c * rsqrtf(fmaxf(c, 1e-30f));
+}
+
+// 1/s (0 where s^2 is below the threshold) and s = s^2 / s.
+template <class R> __device__ __forceinline__ void inv_s(R s2, R& rs, R& s) {
+  const R r = rsqrt_(s2 > s2_min<R>() ? s2 : R(1));
+  rs = s2 > s2_min<R>() ? r : R(0);
+  s = s2 * rs;
+}
+
+// Per-point coefficients.
+template <class R> struct LhyPt {
+  R A0, A1, D0, D1, q4;  // q4 = 4 n1 n2
+};
+template <class R> __device__ __forceinline__ LhyPt<R> lhy_pt(const LhyCoef<R>& c, R n1, R n2) {
+  LhyPt<R> p;
+  p.A0 = c.g11 * n1 + c.g22 * n2;
+  p.A1 = c.d11 * n1 + c.d22 * n2;
+  p.D0 = c.g11 * n1 - c.g22 * n2;
+  p.D1 = c.d11 * n1 - c.d22 * n2;
+  p.q4 = R(4) * n1 * n2;
+  return p;
+}
+
+// F = sum_q W_q sum_+- max(V,0)^{5/2};  mu_i = dF/dn_i
+//   = sum_q W_q (5/2) sum_+- max(V,0)^{3/2} (eta_ii +- sigma_i/s),
+// sigma_1 = eta11 delta + 2 eta12^2 n2, sigma_2 = -eta22 delta + 2 eta12^2 n1
+// (the paper's mu_LHY, Sec. II).  With S_k = sum W w^k (V+^{3/2} + V-^{3/2}) and
+// T_k = sum W w^k (V+^{3/2} - V-^{3/2})/s, and sigma_i(w) quadratic in w:
+//   mu_i = 5/2 (g_ii S_0 + gdd_ii S_1 + sigma_i0 T_0 + sigma_i1 T_1 + sigma_i2 T_2).
+// W_q already includes kappa eta_s^{-5/2}.
 template <class R>
-__device__ __forceinline__ void lhy_point(const LhyNode<R>* __restrict__ nd, int Q, R n1, R n2, R& F, R& mu1,
-                                          R& mu2) {
-  R f = 0, m1 = 0, m2 = 0;
-  for (int q = 0; q < Q; ++q) {
-    const R e11 = nd[q].e11, e22 = nd[q].e22, e2 = nd[q].e2, w = nd[q].w;
-    const R a1 = e11 * n1, a2 = e22 * n2;
-    const R A = a1 + a2, d = a1 - a2;
-    const R s2 = d * d + R(2) * e2 * n1 * n2;
-    R rs = 0, s = 0;
-    if (s2 > s2_min<R>()) {
-      rs = rsqrt_(s2);
-      s = s2 * rs;
-    }
-    const R vp = A + s, vm = A - s;
-    R p32 = 0, m32 = 0, p52 = 0, m52 = 0;
-    if (vp > R(0)) {
-      const R sq = sqrt_(vp);
-      p32 = vp * sq;
-      p52 = vp * p32;
-    }
-    if (vm > R(0)) {
-      const R sq = sqrt_(vm);
-      m32 = vm * sq;
-      m52 = vm * m32;
-    }
-    f += w * (p52 + m52);
-    const R sum32 = p32 + m32, dif32 = p32 - m32;
-    const R q1 = (e11 * d + e2 * n2) * rs;
-    const R q2 = (e2 * n1 - e22 * d) * rs;
-    m1 += w * (e11 * sum32 + q1 * dif32);
-    m2 += w * (e22 * sum32 + q2 * dif32);
+__device__ __forceinline__ void lhy_point(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c, R n1, R n2,
+                                          R& F, R& mu1, R& mu2) {
+  const LhyPt<R> p = lhy_pt(c, n1, n2);
+  R f = 0, S0 = 0, S1 = 0, T0 = 0, T1 = 0, T2 = 0;
+#pragma unroll 4
+  for (int k = 0; k < Q; ++k) {
+    const LhyNode<R> e = nd[k];
+    const R A = p.A0 + p.A1 * e.w;
+    const R d = p.D0 + p.D1 * e.w;
+    const R s2 = d * d + e.e12sq * p.q4;
+    R rs, s;
+    inv_s(s2, rs, s);
+    const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
+    const R sp = sqrt_pos(vp), sm = sqrt_pos(vm);
+    const R p32 = vp * sp, m32 = vm * sm;
+    f += e.W * (vp * p32 + vm * m32);
+    const R sum32 = p32 + m32;
+    const R t = (p32 - m32) * rs;
+    S0 += e.W * sum32;
+    S1 += e.Ww * sum32;
+    T0 += e.W * t;
+    T1 += e.Ww * t;
+    T2 += e.Ww * e.w * t;
   }
+  // sigma_1(w) = (g11 + d11 w)(D0 + D1 w) + 2 n2 (g12 + d12 w)^2, sigma_2 likewise
+  const R n2x2 = R(2) * n2, n1x2 = R(2) * n1;
+  const R s10 = c.g11 * p.D0 + n2x2 * c.g12 * c.g12;
+  const R s11 = c.g11 * p.D1 + c.d11 * p.D0 + R(2) * n2x2 * c.g12 * c.d12;
+  const R s12 = c.d11 * p.D1 + n2x2 * c.d12 * c.d12;
+  const R s20 = -c.g22 * p.D0 + n1x2 * c.g12 * c.g12;
+  const R s21 = -c.g22 * p.D1 - c.d22 * p.D0 + R(2) * n1x2 * c.g12 * c.d12;
+  const R s22 = -c.d22 * p.D1 + n1x2 * c.d12 * c.d12;
   F = f;
-  mu1 = R(2.5) * m1;
-  mu2 = R(2.5) * m2;
+  mu1 = R(2.5) * (c.g11 * S0 + c.d11 * S1 + s10 * T0 + s11 * T1 + s12 * T2);
+  mu2 = R(2.5) * (c.g22 * S0 + c.d22 * S1 + s20 * T0 + s21 * T1 + s22 * T2);
 }
 
 // Second variation of F along n(alpha) with first variations n1', n2' and the
-// second variations n'' removed (they enter through mu_LHY, see the line-search
-// assembly):  sum_q w_q (5/2) sum_+- [ 2 max(V,0)^{3/2} K_+- + (3/2) max(V,0)^{1/2} (V1_+-)^2 ],
-// V1_+- = eta11 n1' + eta22 n2' +- t1,  t1 = (delta delta1 + 2 eta12 eta21 (n1 n2' + n1' n2))/s,
-// K_+- = +-(delta1^2 + 4 eta12 eta21 n1' n2' - t1^2)/(2s),  delta1 = eta11 n1' - eta22 n2'
+// second variations n'' removed (they enter through mu_LHY in the line-search
+// assembly):  sum_q W_q (5/2) sum_+- [ 2 max(V,0)^{3/2} K_+- + (3/2) max(V,0)^{1/2} (V1_+-)^2 ],
+// V1_+- = eta11 n1' + eta22 n2' +- t1,  t1 = (delta delta1 + 2 eta12^2 (n1 n2' + n1' n2))/s,
+// K_+- = +-(delta1^2 + 4 eta12^2 n1' n2' - t1^2)/(2s),  delta1 = eta11 n1' - eta22 n2'
 // (the n''-free part of the paper's V^2_+-, Sec. V auxiliaries).
 template <class R>
-__device__ __forceinline__ R lhy_hess(const LhyNode<R>* __restrict__ nd, int Q, R n1, R n2, R n1p, R n2p) {
+__device__ __forceinline__ R lhy_hess(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c, R n1, R n2,
+                                      R n1p, R n2p) {
+  const LhyPt<R> p = lhy_pt(c, n1, n2);
+  const R B0 = c.g11 * n1p + c.g22 * n2p, B1 = c.d11 * n1p + c.d22 * n2p;   // A1(w)
+  const R E0 = c.g11 * n1p - c.g22 * n2p, E1 = c.d11 * n1p - c.d22 * n2p;   // delta1(w)
+  const R m = R(2) * (n1 * n2p + n1p * n2);  // 2 eta12^2 (n1 n2' + n1' n2) = eta12^2 m
+  const R mp = R(4) * n1p * n2p;              // 4 eta12^2 n1' n2' = eta12^2 mp
   R h = 0;
-  for (int q = 0; q < Q; ++q) {
-    const R e11 = nd[q].e11, e22 = nd[q].e22, e2 = nd[q].e2, w = nd[q].w;
-    const R a1 = e11 * n1, a2 = e22 * n2;
-    const R A = a1 + a2, d = a1 - a2;
-    const R s2 = d * d + R(2) * e2 * n1 * n2;
-    R rs = 0, s = 0;
-    if (s2 > s2_min<R>()) {
-      rs = rsqrt_(s2);
-      s = s2 * rs;
-    }
-    const R d1 = e11 * n1p - e22 * n2p;
-    const R A1 = e11 * n1p + e22 * n2p;
-    const R t1 = (d * d1 + e2 * (n1 * n2p + n1p * n2)) * rs;
-    const R K = (d1 * d1 + R(2) * e2 * n1p * n2p - t1 * t1) * R(0.5) * rs;
-    const R vp = A + s, vm = A - s;
-    R acc = 0;
-    if (vp > R(0)) {
-      const R sq = sqrt_(vp);
-      const R v1 = A1 + t1;
-      acc += R(2) * vp * sq * K + R(1.5) * sq * v1 * v1;
-    }
-    if (vm > R(0)) {
-      const R sq = sqrt_(vm);
-      const R v1 = A1 - t1;
-      acc += R(-2) * vm * sq * K + R(1.5) * sq * v1 * v1;
-    }
-    h += w * acc;
+#pragma unroll 4
+  for (int k = 0; k < Q; ++k) {
+    const LhyNode<R> e = nd[k];
+    const R A = p.A0 + p.A1 * e.w;
+    const R d = p.D0 + p.D1 * e.w;
+    const R s2 = d * d + e.e12sq * p.q4;
+    R rs, s;
+    inv_s(s2, rs, s);
+    const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
+    const R sp = sqrt_pos(vp), sm = sqrt_pos(vm);
+    const R A1 = B0 + B1 * e.w;
+    const R d1 = E0 + E1 * e.w;
+    const R t1 = (d * d1 + e.e12sq * m) * rs;
+    const R K = (d1 * d1 + e.e12sq * mp - t1 * t1) * (R(0.5) * rs);
+    const R v1p = A1 + t1, v1m = A1 - t1;
+    const R acc = R(2) * K * (vp * sp - vm * sm) + R(1.5) * (sp * v1p * v1p + sm * v1m * v1m);
+    h += e.W * acc;
   }
   return R(2.5) * h;
 }
