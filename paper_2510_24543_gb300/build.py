@@ -20,6 +20,11 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libegpe.so")
 UNITS = ["capi.cu", "engine_f64.cu", "engine_f32.cu"]
+# The FP32-field engine flushes denormals and uses the approximate (MUFU)
+# divide and square root: values below 1e-38 carry no weight in any sum of that
+# path, and its fields are accurate to ~1e-7 anyway.  The FP64 engine keeps
+# IEEE division and square root.
+UNIT_FLAGS = {"engine_f32.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -39,6 +44,7 @@ def _digest() -> str:
                 with open(os.path.join(d, name), "rb") as f:
                     h.update(name.encode() + f.read())
     h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(repr(sorted(UNIT_FLAGS.items())).encode())
     return h.hexdigest()
 
 
@@ -56,7 +62,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_unit(unit):
         src = os.path.join(CSRC, unit)
         obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS + UNIT_FLAGS.get(unit, []) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {unit}:\n{r.stdout}\n{r.stderr}")

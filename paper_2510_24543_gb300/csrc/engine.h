@@ -78,6 +78,7 @@ template <class R> class Engine {
                           double accept_rtol);
   egpe_status read_state(DevState& hs);
   template <class Op> egpe_status launch_x(KArgs<R> a);
+  egpe_status launch_point(void (*kern)(KArgs<R>), const char* name, double bytes, const KArgs<R>& a);
   template <class Op> egpe_status launch_col(KArgs<R> a);
   template <template <class, int> class OpT> egpe_status dispatch_x(int L, const KArgs<R>& a);
   template <template <class, int> class OpT> egpe_status dispatch_col(int L, const KArgs<R>& a);
@@ -94,6 +95,8 @@ template <class R> class Engine {
   };
   std::vector<KTime> tlog_;
   bool timing_ = false;
+  // LHY epilogues as separate pointwise kernels (true) or fused into the last x pass
+  bool split_lhy_ = false;
   size_t tpos_ = 0;
 
   KArgs<R>* base_ = nullptr;  // host copy of the common kernel arguments

@@ -283,6 +283,18 @@ egpe_status Engine<R>::profile_attempt(const C* psi, int precond, int reps, std:
   return EGPE_OK;
 }
 
+template <class R>
+egpe_status Engine<R>::launch_point(void (*kern)(KArgs<R>), const char* name, double bytes, const KArgs<R>& a) {
+  const int occ = occupancy((const void*)kern, 256, 0);
+  const int grid = (int)std::min<size_t>((N + 511) / 512, (size_t)std::min(occ * nsm_, 16384));
+  if (timing_) t_begin(name, 0, bytes);
+  kern<<<grid, 256, 0, stream>>>(a);
+  if (timing_) t_end();
+  ++kernels_;
+  EGPE_CUDA(cudaGetLastError());
+  return EGPE_OK;
+}
+
 template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> a) {
   constexpr int L = Op::L, TPL = L / 8, NF = Op::NF, NS = Op::NS;
   constexpr int LP = row_len_padded<R, L>();
@@ -388,7 +400,11 @@ template <class R> egpe_status Engine<R>::enq_eg(int trial, int gate, int ctrl) 
   EGPE_TRY(dispatch_col<ZEg>(nz, a));
   EGPE_TRY(plain_col(1, 1, y));
   a.ctrl = ctrl;
-  return dispatch_x<XInvEG>(nx, a);
+  if (!split_lhy_) return dispatch_x<XInvEG>(nx, a);
+  a.ctrl = 0;
+  EGPE_TRY(dispatch_x<XInvW3>(nx, a));
+  a.ctrl = ctrl;
+  return launch_point(eg_point_kernel<R>, "energy+LHY pointwise", 9.0 * N * sizeof(C), a);
 }
 
 // Preconditioner pipeline: 4 transforms for the kinetic modes, none otherwise.
@@ -440,7 +456,11 @@ template <class R> egpe_status Engine<R>::enq_lc(int gate, int ctrl, int pgiven)
   y.f0 = 2;
   EGPE_TRY(plain_col(1, 1, y));
   a.ctrl = ctrl;
-  return dispatch_x<XInvLC>(nx, a);
+  if (!split_lhy_) return dispatch_x<XInvLC>(nx, a);
+  a.ctrl = 0;
+  EGPE_TRY(dispatch_x<XInvW1F2>(nx, a));
+  a.ctrl = ctrl;
+  return launch_point(lc_point_kernel<R>, "line sums+LHY pointwise", 9.0 * N * sizeof(C), a);
 }
 
 template <class R> egpe_status Engine<R>::enq_attempt(int mode) {

@@ -24,13 +24,11 @@ template <class R> __device__ __forceinline__ R s2_min();
 template <> __device__ __forceinline__ double s2_min<double>() { return 1e-300; }
 template <> __device__ __forceinline__ float s2_min<float>() { return 1e-36f; }
 
-// sqrt(max(v,0)) without branches.  FP64: the library square root; FP32:
-// v * rsqrt(v) (MUFU), a few ulp, with the argument of rsqrt kept positive.
-__device__ __forceinline__ double sqrt_pos(double v) { return sqrt(fmax(v, 0.0)); }
-__device__ __forceinline__ float sqrt_pos(float v) {
-  const float c = fmaxf(v, 0.0f);
-  return c * rsqrtf(fmaxf(c, 1e-30f));
-}
+// sqrt(v) of a clamped v >= 0 without branches.  FP64: the library square
+// root; FP32: the translation unit is built with the approximate square root
+// (MUFU, a few ulp).
+__device__ __forceinline__ double sqrt_pos(double v) { return sqrt(v); }
+__device__ __forceinline__ float sqrt_pos(float v) { return sqrtf(v); }
 
 // 1/s (0 where s^2 is below the threshold) and s = s^2 / s.
 template <class R> __device__ __forceinline__ void inv_s(R s2, R& rs, R& s) {
@@ -59,43 +57,57 @@ template <class R> __device__ __forceinline__ LhyPt<R> lhy_pt(const LhyCoef<R>& 
 // (the paper's mu_LHY, Sec. II).  With S_k = sum W w^k (V+^{3/2} + V-^{3/2}) and
 // T_k = sum W w^k (V+^{3/2} - V-^{3/2})/s, and sigma_i(w) quadratic in w:
 //   mu_i = 5/2 (g_ii S_0 + gdd_ii S_1 + sigma_i0 T_0 + sigma_i1 T_1 + sigma_i2 T_2).
-// W_q already includes kappa eta_s^{-5/2}.
-template <class R>
-__device__ __forceinline__ void lhy_point(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c, R n1, R n2,
-                                          R& F, R& mu1, R& mu2) {
-  const LhyPt<R> p = lhy_pt(c, n1, n2);
-  R f = 0, S0 = 0, S1 = 0, T0 = 0, T1 = 0, T2 = 0;
-#pragma unroll 4
+// W_q already includes kappa eta_s^{-5/2}.  NP points are evaluated together
+// (independent dependency chains per node).
+template <class R, int NP>
+__device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c,
+                                           const R (&n1)[NP], const R (&n2)[NP], R (&F)[NP], R (&mu1)[NP],
+                                           R (&mu2)[NP]) {
+  LhyPt<R> p[NP];
+  R f[NP], S0[NP], S1[NP], T0[NP], T1[NP], T2[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    p[j] = lhy_pt(c, n1[j], n2[j]);
+    f[j] = S0[j] = S1[j] = T0[j] = T1[j] = T2[j] = R(0);
+  }
+#pragma unroll 2
   for (int k = 0; k < Q; ++k) {
     const LhyNode<R> e = nd[k];
-    const R A = p.A0 + p.A1 * e.w;
-    const R d = p.D0 + p.D1 * e.w;
-    const R s2 = d * d + e.e12sq * p.q4;
-    R rs, s;
-    inv_s(s2, rs, s);
-    const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
-    const R sp = sqrt_pos(vp), sm = sqrt_pos(vm);
-    const R p32 = vp * sp, m32 = vm * sm;
-    f += e.W * (vp * p32 + vm * m32);
-    const R sum32 = p32 + m32;
-    const R t = (p32 - m32) * rs;
-    S0 += e.W * sum32;
-    S1 += e.Ww * sum32;
-    T0 += e.W * t;
-    T1 += e.Ww * t;
-    T2 += e.Ww * e.w * t;
+    const R Www = e.Ww * e.w;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const R A = p[j].A0 + p[j].A1 * e.w;
+      const R d = p[j].D0 + p[j].D1 * e.w;
+      const R s2 = d * d + e.e12sq * p[j].q4;
+      R rs, s;
+      inv_s(s2, rs, s);
+      const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
+      const R sp = sqrt_pos(vp), sm = sqrt_pos(vm);
+      const R p32 = vp * sp, m32 = vm * sm;
+      f[j] += e.W * (vp * p32 + vm * m32);
+      const R sum32 = p32 + m32;
+      const R t = (p32 - m32) * rs;
+      S0[j] += e.W * sum32;
+      S1[j] += e.Ww * sum32;
+      T0[j] += e.W * t;
+      T1[j] += e.Ww * t;
+      T2[j] += Www * t;
+    }
   }
-  // sigma_1(w) = (g11 + d11 w)(D0 + D1 w) + 2 n2 (g12 + d12 w)^2, sigma_2 likewise
-  const R n2x2 = R(2) * n2, n1x2 = R(2) * n1;
-  const R s10 = c.g11 * p.D0 + n2x2 * c.g12 * c.g12;
-  const R s11 = c.g11 * p.D1 + c.d11 * p.D0 + R(2) * n2x2 * c.g12 * c.d12;
-  const R s12 = c.d11 * p.D1 + n2x2 * c.d12 * c.d12;
-  const R s20 = -c.g22 * p.D0 + n1x2 * c.g12 * c.g12;
-  const R s21 = -c.g22 * p.D1 - c.d22 * p.D0 + R(2) * n1x2 * c.g12 * c.d12;
-  const R s22 = -c.d22 * p.D1 + n1x2 * c.d12 * c.d12;
-  F = f;
-  mu1 = R(2.5) * (c.g11 * S0 + c.d11 * S1 + s10 * T0 + s11 * T1 + s12 * T2);
-  mu2 = R(2.5) * (c.g22 * S0 + c.d22 * S1 + s20 * T0 + s21 * T1 + s22 * T2);
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    // sigma_1(w) = (g11 + d11 w)(D0 + D1 w) + 2 n2 (g12 + d12 w)^2, sigma_2 likewise
+    const R n2x2 = R(2) * n2[j], n1x2 = R(2) * n1[j];
+    const R s10 = c.g11 * p[j].D0 + n2x2 * c.g12 * c.g12;
+    const R s11 = c.g11 * p[j].D1 + c.d11 * p[j].D0 + R(2) * n2x2 * c.g12 * c.d12;
+    const R s12 = c.d11 * p[j].D1 + n2x2 * c.d12 * c.d12;
+    const R s20 = -c.g22 * p[j].D0 + n1x2 * c.g12 * c.g12;
+    const R s21 = -c.g22 * p[j].D1 - c.d22 * p[j].D0 + R(2) * n1x2 * c.g12 * c.d12;
+    const R s22 = -c.d22 * p[j].D1 + n1x2 * c.d12 * c.d12;
+    F[j] = f[j];
+    mu1[j] = R(2.5) * (c.g11 * S0[j] + c.d11 * S1[j] + s10 * T0[j] + s11 * T1[j] + s12 * T2[j]);
+    mu2[j] = R(2.5) * (c.g22 * S0[j] + c.d22 * S1[j] + s20 * T0[j] + s21 * T1[j] + s22 * T2[j]);
+  }
 }
 
 // Second variation of F along n(alpha) with first variations n1', n2' and the
@@ -103,35 +115,47 @@ __device__ __forceinline__ void lhy_point(const LhyNode<R>* __restrict__ nd, int
 // assembly):  sum_q W_q (5/2) sum_+- [ 2 max(V,0)^{3/2} K_+- + (3/2) max(V,0)^{1/2} (V1_+-)^2 ],
 // V1_+- = eta11 n1' + eta22 n2' +- t1,  t1 = (delta delta1 + 2 eta12^2 (n1 n2' + n1' n2))/s,
 // K_+- = +-(delta1^2 + 4 eta12^2 n1' n2' - t1^2)/(2s),  delta1 = eta11 n1' - eta22 n2'
-// (the n''-free part of the paper's V^2_+-, Sec. V auxiliaries).
-template <class R>
-__device__ __forceinline__ R lhy_hess(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c, R n1, R n2,
-                                      R n1p, R n2p) {
-  const LhyPt<R> p = lhy_pt(c, n1, n2);
-  const R B0 = c.g11 * n1p + c.g22 * n2p, B1 = c.d11 * n1p + c.d22 * n2p;   // A1(w)
-  const R E0 = c.g11 * n1p - c.g22 * n2p, E1 = c.d11 * n1p - c.d22 * n2p;   // delta1(w)
-  const R m = R(2) * (n1 * n2p + n1p * n2);  // 2 eta12^2 (n1 n2' + n1' n2) = eta12^2 m
-  const R mp = R(4) * n1p * n2p;              // 4 eta12^2 n1' n2' = eta12^2 mp
-  R h = 0;
-#pragma unroll 4
+// (the n''-free part of the paper's V^2_+-, Sec. V auxiliaries).  NP points together.
+template <class R, int NP>
+__device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c,
+                                         const R (&n1)[NP], const R (&n2)[NP], const R (&n1p)[NP],
+                                         const R (&n2p)[NP], R (&H)[NP]) {
+  LhyPt<R> p[NP];
+  R B0[NP], B1[NP], E0[NP], E1[NP], m[NP], mp[NP], h[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    p[j] = lhy_pt(c, n1[j], n2[j]);
+    B0[j] = c.g11 * n1p[j] + c.g22 * n2p[j];  // A1(w) = B0 + B1 w
+    B1[j] = c.d11 * n1p[j] + c.d22 * n2p[j];
+    E0[j] = c.g11 * n1p[j] - c.g22 * n2p[j];  // delta1(w) = E0 + E1 w
+    E1[j] = c.d11 * n1p[j] - c.d22 * n2p[j];
+    m[j] = R(2) * (n1[j] * n2p[j] + n1p[j] * n2[j]);  // 2 eta12^2 (n1 n2' + n1' n2) = eta12^2 m
+    mp[j] = R(4) * n1p[j] * n2p[j];                   // 4 eta12^2 n1' n2' = eta12^2 mp
+    h[j] = R(0);
+  }
+#pragma unroll 2
   for (int k = 0; k < Q; ++k) {
     const LhyNode<R> e = nd[k];
-    const R A = p.A0 + p.A1 * e.w;
-    const R d = p.D0 + p.D1 * e.w;
-    const R s2 = d * d + e.e12sq * p.q4;
-    R rs, s;
-    inv_s(s2, rs, s);
-    const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
-    const R sp = sqrt_pos(vp), sm = sqrt_pos(vm);
-    const R A1 = B0 + B1 * e.w;
-    const R d1 = E0 + E1 * e.w;
-    const R t1 = (d * d1 + e.e12sq * m) * rs;
-    const R K = (d1 * d1 + e.e12sq * mp - t1 * t1) * (R(0.5) * rs);
-    const R v1p = A1 + t1, v1m = A1 - t1;
-    const R acc = R(2) * K * (vp * sp - vm * sm) + R(1.5) * (sp * v1p * v1p + sm * v1m * v1m);
-    h += e.W * acc;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const R A = p[j].A0 + p[j].A1 * e.w;
+      const R d = p[j].D0 + p[j].D1 * e.w;
+      const R s2 = d * d + e.e12sq * p[j].q4;
+      R rs, s;
+      inv_s(s2, rs, s);
+      const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
+      const R sp = sqrt_pos(vp), sm = sqrt_pos(vm);
+      const R A1 = B0[j] + B1[j] * e.w;
+      const R d1 = E0[j] + E1[j] * e.w;
+      const R t1 = (d * d1 + e.e12sq * m[j]) * rs;
+      const R K = (d1 * d1 + e.e12sq * mp[j] - t1 * t1) * (R(0.5) * rs);
+      const R v1p = A1 + t1, v1m = A1 - t1;
+      const R acc = R(2) * K * (vp * sp - vm * sm) + R(1.5) * (sp * v1p * v1p + sm * v1m * v1m);
+      h[j] += e.W * acc;
+    }
   }
-  return R(2.5) * h;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) H[j] = R(2.5) * h[j];
 }
 
 }  // namespace egpe
