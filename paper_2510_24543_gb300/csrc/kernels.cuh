@@ -60,6 +60,13 @@ template <class R> __device__ __forceinline__ bool gate_open(const KArgs<R>& a) 
   return a.gate == GATE_NEW_ITER ? (ph == PH_NEW_ITER) : (ph != PH_DONE);
 }
 
+// Points whose global loads are issued together before any store of the chunk
+// (the buffers may alias as far as the compiler knows, so loads and stores are
+// grouped explicitly to keep several loads in flight per thread).
+template <class R> struct ChunkW;
+template <> struct ChunkW<float> { static constexpr int v = 4; };
+template <> struct ChunkW<double> { static constexpr int v = 2; };
+
 // Grid points evaluated together in the LHY node loops (independent chains).
 template <class R> struct LhyNP;
 template <> struct LhyNP<float> { static constexpr int v = 2; };
@@ -254,25 +261,37 @@ template <class R_, int L_> struct XFwdEG {
     const C* pd = a.pb[u.nsel];
     C* dst = a.psi[u.slot];
     const size_t N = a.N;
+    constexpr int CH = ChunkW<R>::v;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      C p1 = cmk<C>(0, 0), p2 = cmk<C>(0, 0);
-      if (valid) {
-        const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e);
-        p1 = src[idx];
-        p2 = src[N + idx];
-        if (a.flag) {  // trial point on the geodesic (Sec. III), renormalised (Sec. V)
-          const C q1 = pd[idx], q2 = pd[N + idx];
-          p1 = cmk<C>(u.ca[0] * p1.x + u.cb[0] * q1.x, u.ca[0] * p1.y + u.cb[0] * q1.y);
-          p2 = cmk<C>(u.ca[1] * p2.x + u.cb[1] * q2.x, u.ca[1] * p2.y + u.cb[1] * q2.y);
-          dst[idx] = p1;
-          dst[N + idx] = p2;
+    for (int e0 = 0; e0 < 8; e0 += CH) {
+      C p1[CH], p2[CH], q1[CH], q2[CH];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e0 + j);
+        p1[j] = valid ? src[idx] : cmk<C>(0, 0);
+        p2[j] = valid ? src[N + idx] : cmk<C>(0, 0);
+        if (a.flag) {
+          q1[j] = valid ? pd[idx] : cmk<C>(0, 0);
+          q2[j] = valid ? pd[N + idx] : cmk<C>(0, 0);
         }
       }
-      const R n1 = cabs2(p1), n2 = cabs2(p2);
-      v[0][e] = p1;
-      v[1][e] = p2;
-      v[2][e] = cmk<C>(a.d11 * n1 + a.d12 * n2, a.d21 * n1 + a.d22 * n2);
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const int e = e0 + j;
+        if (a.flag) {  // trial point on the geodesic (Sec. III), renormalised (Sec. V)
+          p1[j] = cmk<C>(u.ca[0] * p1[j].x + u.cb[0] * q1[j].x, u.ca[0] * p1[j].y + u.cb[0] * q1[j].y);
+          p2[j] = cmk<C>(u.ca[1] * p2[j].x + u.cb[1] * q2[j].x, u.ca[1] * p2[j].y + u.cb[1] * q2[j].y);
+          if (valid) {
+            const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e);
+            dst[idx] = p1[j];
+            dst[N + idx] = p2[j];
+          }
+        }
+        const R n1 = cabs2(p1[j]), n2 = cabs2(p2[j]);
+        v[0][e] = p1[j];
+        v[1][e] = p2[j];
+        v[2][e] = cmk<C>(a.d11 * n1 + a.d12 * n2, a.d21 * n1 + a.d22 * n2);
+      }
     }
   }
   static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], double*,
@@ -442,72 +461,88 @@ template <class R> __device__ __forceinline__ void pc_uniform(const KArgs<R>& a,
   }
 }
 
-// r_i at one point (stored unless given) and P_V^{-1} r_i when diag.
+// Inputs of the preconditioner prologue at one point.
+template <class R> struct PcIn {
+  C2<R> p1, p2, h1, h2, ml;
+};
 template <class R>
-__device__ __forceinline__ void pc_point_prologue(const KArgs<R>& a, const PcUni<R>& u, size_t idx, R V, C2<R>& w1,
-                                                  C2<R>& w2) {
-  using C = C2<R>;
+__device__ __forceinline__ void pc_load(const KArgs<R>& a, const PcUni<R>& u, size_t idx, PcIn<R>& in) {
   const size_t N = a.N;
-  C* rd = a.rb[u.nsel];
-  const C* ps = a.psi[u.cur];
+  if (u.rgiven) {
+    in.h1 = a.rb[u.nsel][idx];
+    in.h2 = a.rb[u.nsel][N + idx];
+  } else {
+    in.h1 = a.hp[u.cur][idx];
+    in.h2 = a.hp[u.cur][N + idx];
+  }
+  if (a.diag || !u.rgiven) {
+    in.p1 = a.psi[u.cur][idx];
+    in.p2 = a.psi[u.cur][N + idx];
+  }
+  if (a.diag) in.ml = a.ax[u.cur][N + idx];
+}
+// r_i = H_i psi_i - mu_i psi_i (stored unless given) and w_i = P_V^{-1} r_i when diag.
+template <class R>
+__device__ __forceinline__ void pc_apply(const KArgs<R>& a, const PcUni<R>& u, size_t idx, R V, const PcIn<R>& in,
+                                         C2<R>& w1, C2<R>& w2) {
+  using C = C2<R>;
   C r1, r2;
   if (u.rgiven) {
-    r1 = rd[idx];
-    r2 = rd[N + idx];
+    r1 = in.h1;
+    r2 = in.h2;
   } else {
-    const C* hp = a.hp[u.cur];
-    const C p1 = ps[idx], p2 = ps[N + idx], h1 = hp[idx], h2 = hp[N + idx];
-    r1 = cmk<C>(h1.x - u.mu[0] * p1.x, h1.y - u.mu[0] * p1.y);
-    r2 = cmk<C>(h2.x - u.mu[1] * p2.x, h2.y - u.mu[1] * p2.y);
-    rd[idx] = r1;
-    rd[N + idx] = r2;
+    r1 = cmk<C>(in.h1.x - u.mu[0] * in.p1.x, in.h1.y - u.mu[0] * in.p1.y);
+    r2 = cmk<C>(in.h2.x - u.mu[1] * in.p2.x, in.h2.y - u.mu[1] * in.p2.y);
+    a.rb[u.nsel][idx] = r1;
+    a.rb[u.nsel][(size_t)a.N + idx] = r2;
   }
   if (a.diag) {
-    const C p1 = ps[idx], p2 = ps[N + idx];
-    const R n1 = cabs2(p1), n2 = cabs2(p2);
-    const C ml = a.ax[u.cur][N + idx];
-    R P1 = u.shift[0] + V + a.g11 * n1 + a.g12 * n2 + ml.x;
-    R P2 = u.shift[1] + V + a.g21 * n1 + a.g22 * n2 + ml.y;
+    const R n1 = cabs2(in.p1), n2 = cabs2(in.p2);
+    R P1 = u.shift[0] + V + a.g11 * n1 + a.g12 * n2 + in.ml.x;
+    R P2 = u.shift[1] + V + a.g21 * n1 + a.g22 * n2 + in.ml.y;
     P1 = P1 > u.floor_[0] ? P1 : u.floor_[0];
     P2 = P2 > u.floor_[1] ? P2 : u.floor_[1];
-    const R i1 = R(1) / P1, i2 = R(1) / P2;
-    w1 = cscale(r1, i1);
-    w2 = cscale(r2, i2);
+    w1 = cscale(r1, R(1) / P1);
+    w2 = cscale(r2, R(1) / P2);
   } else {
     w1 = r1;
     w2 = r2;
   }
 }
 
-// Sums of one point once z is known.
+// Inputs of the preconditioner sums at one point.
+template <class R> struct PcSumIn {
+  C2<R> r1, r2, q1, q2, d1, d2, p1, p2;
+};
 template <class R>
-__device__ __forceinline__ void pc_point_sums(const KArgs<R>& a, const PcUni<R>& u, size_t idx, C2<R> z1, C2<R> z2,
-                                              R* s) {
-  using C = C2<R>;
+__device__ __forceinline__ void pc_sum_load(const KArgs<R>& a, const PcUni<R>& u, size_t idx, PcSumIn<R>& in) {
   const size_t N = a.N;
-  const C* ps = a.psi[u.cur];
-  const C* rc = a.rb[u.nsel];
-  const C* rp = a.rb[u.nsel ^ 1];
-  const C* pp = a.pb[u.nsel ^ 1];
-  const C r1 = rc[idx], r2 = rc[N + idx];
-  const C q1 = rp[idx], q2 = rp[N + idx];
-  const C d1 = pp[idx], d2 = pp[N + idx];
-  const C p1 = ps[idx], p2 = ps[N + idx];
-  const C dr1 = csub(r1, q1), dr2 = csub(r2, q2);
+  in.r1 = a.rb[u.nsel][idx];
+  in.r2 = a.rb[u.nsel][N + idx];
+  in.q1 = a.rb[u.nsel ^ 1][idx];
+  in.q2 = a.rb[u.nsel ^ 1][N + idx];
+  in.d1 = a.pb[u.nsel ^ 1][idx];
+  in.d2 = a.pb[u.nsel ^ 1][N + idx];
+  in.p1 = a.psi[u.cur][idx];
+  in.p2 = a.psi[u.cur][N + idx];
+}
+template <class R>
+__device__ __forceinline__ void pc_sum_add(const PcSumIn<R>& in, C2<R> z1, C2<R> z2, R* s) {
+  const C2<R> dr1 = csub(in.r1, in.q1), dr2 = csub(in.r2, in.q2);
   s[PC_SRZ] += cdot(dr1, z1) + cdot(dr2, z2);
-  s[PC_SRP] += cdot(dr1, d1) + cdot(dr2, d2);
-  s[PC_ZPSI1] += cdot(z1, p1);
-  s[PC_ZPSI2] += cdot(z2, p2);
-  s[PC_PPPSI1] += cdot(d1, p1);
-  s[PC_PPPSI2] += cdot(d2, p2);
-  s[PC_ZR1] += cdot(z1, r1);
-  s[PC_ZR2] += cdot(z2, r2);
-  s[PC_PPR1] += cdot(d1, r1);
-  s[PC_PPR2] += cdot(d2, r2);
-  s[PC_PSIR1] += cdot(p1, r1);
-  s[PC_PSIR2] += cdot(p2, r2);
-  s[PC_RR1] += cabs2(r1);
-  s[PC_RR2] += cabs2(r2);
+  s[PC_SRP] += cdot(dr1, in.d1) + cdot(dr2, in.d2);
+  s[PC_ZPSI1] += cdot(z1, in.p1);
+  s[PC_ZPSI2] += cdot(z2, in.p2);
+  s[PC_PPPSI1] += cdot(in.d1, in.p1);
+  s[PC_PPPSI2] += cdot(in.d2, in.p2);
+  s[PC_ZR1] += cdot(z1, in.r1);
+  s[PC_ZR2] += cdot(z2, in.r2);
+  s[PC_PPR1] += cdot(in.d1, in.r1);
+  s[PC_PPR2] += cdot(in.d2, in.r2);
+  s[PC_PSIR1] += cdot(in.p1, in.r1);
+  s[PC_PSIR2] += cdot(in.p2, in.r2);
+  s[PC_RR1] += cabs2(in.r1);
+  s[PC_RR2] += cabs2(in.r2);
 }
 
 template <class R_, int L_> struct XFwdPC {
@@ -523,14 +558,25 @@ template <class R_, int L_> struct XFwdPC {
     const int y = row % a.ny, z = row / a.ny;
     const R Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
     const R vyz = a.vy * Y * Y + a.vz * Z * Z;
+    constexpr int CH = ChunkW<R>::v;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      v[0][e] = cmk<C>(0, 0);
-      v[1][e] = cmk<C>(0, 0);
+    for (int e0 = 0; e0 < 8; e0 += CH) {
+      PcIn<R> in[CH];
       if (valid) {
-        const int x = Plan<L>::entry_pos(false, t, e);
-        const R X = -a.Lx + (R)x * a.hx;
-        pc_point_prologue<R>(a, u, (size_t)row * a.nx + x, a.vx * X * X + vyz, v[0][e], v[1][e]);
+#pragma unroll
+        for (int j = 0; j < CH; ++j)
+          pc_load<R>(a, u, (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e0 + j), in[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const int e = e0 + j;
+        v[0][e] = cmk<C>(0, 0);
+        v[1][e] = cmk<C>(0, 0);
+        if (valid) {
+          const int x = Plan<L>::entry_pos(false, t, e);
+          const R X = -a.Lx + (R)x * a.hx;
+          pc_apply<R>(a, u, (size_t)row * a.nx + x, a.vx * X * X + vyz, in[j], v[0][e], v[1][e]);
+        }
       }
     }
   }
@@ -606,12 +652,20 @@ template <class R_, int L_> struct XInvPC {
     R s[PC_NS];
 #pragma unroll
     for (int k = 0; k < PC_NS; ++k) s[k] = 0;
+    constexpr int CH = ChunkW<R>::v;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e);
-      a.z[idx] = v[0][e];
-      a.z[(size_t)a.N + idx] = v[1][e];
-      pc_point_sums<R>(a, u, idx, v[0][e], v[1][e], s);
+    for (int e0 = 0; e0 < 8; e0 += CH) {
+      PcSumIn<R> in[CH];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) pc_sum_load<R>(a, u, (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e0 + j), in[j]);
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const int e = e0 + j;
+        const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e);
+        a.z[idx] = v[0][e];
+        a.z[(size_t)a.N + idx] = v[1][e];
+        pc_sum_add<R>(in[j], v[0][e], v[1][e], s);
+      }
     }
 #pragma unroll
     for (int k = 0; k < PC_NS; ++k) acc[k] += (double)s[k];
@@ -645,13 +699,17 @@ __global__ void __launch_bounds__(256) pc_point_kernel(KArgs<R> a) {
     const R X = -a.Lx + (R)x * a.hx, Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
     const R V = a.vx * X * X + a.vy * Y * Y + a.vz * Z * Z;
     C w1, w2;
-    pc_point_prologue<R>(a, u, idx, V, w1, w2);
+    PcIn<R> in;
+    pc_load<R>(a, u, idx, in);
+    pc_apply<R>(a, u, idx, V, in, w1, w2);
     a.z[idx] = w1;
     a.z[N + idx] = w2;
     R s[PC_NS];
 #pragma unroll
     for (int k = 0; k < PC_NS; ++k) s[k] = 0;
-    pc_point_sums<R>(a, u, idx, w1, w2, s);
+    PcSumIn<R> si;
+    pc_sum_load<R>(a, u, idx, si);
+    pc_sum_add<R>(si, w1, w2, s);
 #pragma unroll
     for (int k = 0; k < PC_NS; ++k) acc[k] += (double)s[k];
   }
@@ -694,34 +752,51 @@ template <class R_, int L_> struct XFwdLC {
     C* pd = a.pb[u.nsel];
     const C* pp = a.pb[u.nsel ^ 1];
     const C* wsrc = u.fallback ? a.rb[u.nsel] : a.z;
+    const bool usepp = !u.pgiven && u.beta != R(0);
+    constexpr int CH = ChunkW<R>::v;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      C q1 = cmk<C>(0, 0), q2 = cmk<C>(0, 0);
-      R rho1 = 0, rho2 = 0;
-      if (valid) {
-        const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e);
-        const C p1 = ps[idx], p2 = ps[N + idx];
-        if (u.pgiven) {
-          q1 = pd[idx];
-          q2 = pd[N + idx];
-        } else {
-          const C w1 = wsrc[idx], w2 = wsrc[N + idx];
-          q1 = cmk<C>(-w1.x - u.c[0] * p1.x, -w1.y - u.c[0] * p1.y);
-          q2 = cmk<C>(-w2.x - u.c[1] * p2.x, -w2.y - u.c[1] * p2.y);
-          if (u.beta != R(0)) {
-            const C d1 = pp[idx], d2 = pp[N + idx];
-            q1 = cmk<C>(q1.x + u.beta * d1.x, q1.y + u.beta * d1.y);
-            q2 = cmk<C>(q2.x + u.beta * d2.x, q2.y + u.beta * d2.y);
-          }
-          pd[idx] = q1;
-          pd[N + idx] = q2;
+    for (int e0 = 0; e0 < 8; e0 += CH) {
+      C p1[CH], p2[CH], w1[CH], w2[CH], d1[CH], d2[CH];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e0 + j);
+        const size_t id = valid ? idx : 0;
+        p1[j] = ps[id];
+        p2[j] = ps[N + id];
+        w1[j] = u.pgiven ? pd[id] : wsrc[id];
+        w2[j] = u.pgiven ? pd[N + id] : wsrc[N + id];
+        if (usepp) {
+          d1[j] = pp[id];
+          d2[j] = pp[N + id];
         }
-        rho1 = cdot(p1, q1);
-        rho2 = cdot(p2, q2);
       }
-      v[0][e] = q1;
-      v[1][e] = q2;
-      v[2][e] = cmk<C>(a.d11 * rho1 + a.d12 * rho2, a.d21 * rho1 + a.d22 * rho2);
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const int e = e0 + j;
+        C q1 = cmk<C>(0, 0), q2 = cmk<C>(0, 0);
+        R rho1 = 0, rho2 = 0;
+        if (valid) {
+          if (u.pgiven) {
+            q1 = w1[j];
+            q2 = w2[j];
+          } else {
+            q1 = cmk<C>(-w1[j].x - u.c[0] * p1[j].x, -w1[j].y - u.c[0] * p1[j].y);
+            q2 = cmk<C>(-w2[j].x - u.c[1] * p2[j].x, -w2[j].y - u.c[1] * p2[j].y);
+            if (usepp) {
+              q1 = cmk<C>(q1.x + u.beta * d1[j].x, q1.y + u.beta * d1[j].y);
+              q2 = cmk<C>(q2.x + u.beta * d2[j].x, q2.y + u.beta * d2[j].y);
+            }
+            const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e);
+            pd[idx] = q1;
+            pd[N + idx] = q2;
+          }
+          rho1 = cdot(p1[j], q1);
+          rho2 = cdot(p2[j], q2);
+        }
+        v[0][e] = q1;
+        v[1][e] = q2;
+        v[2][e] = cmk<C>(a.d11 * rho1 + a.d12 * rho2, a.d21 * rho1 + a.d22 * rho2);
+      }
     }
   }
   static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], double*,
