@@ -120,6 +120,29 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# FP32 CUDA-core peak from unit counts and the maximum SM clock: 152 SMs x 128
+# FP32 lanes x 2 operations per fused multiply-add x 2070 MHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def kernel_flops(name, N, Q, L):
+    """Algorithmic FP operations per launch of the ALU-bound kernels (the LHY
+    epilogues); None for the memory-bound ones.  Counted from the formulas
+    (a sqrt, rsqrt, max or divide counts as one operation):
+      LHY node, energy and mu_LHY form (Eq. 1, Sec. II): 35 per point and node;
+      LHY node, second-variation form (Sec. V): 48 per point and node;
+      per point: 40 (setup) + 55 (potentials, H psi, 12 sums) for the energy
+      epilogue, 40 + 40 (10 sums) for the line-search epilogue;
+      Stockham x inverse: 5 log2(L) per point and transformed field (3 fields
+      in the energy epilogue, 1 in the line-search epilogue)."""
+    lg = math.log2(L)
+    if name.startswith("x-inv energy+LHY"):
+        return N * (35 * Q + 95 + 3 * 5 * lg)
+    if name.startswith("x-inv line sums+LHY"):
+        return N * (48 * Q + 80 + 5 * lg)
+    return None
+
+
 def traffic_record(kernel_name, workload):
     """DRAM bytes per launch of a kernel from the committed ncu summary, or None
     if the summary is missing or was taken on other kernel sources."""
@@ -146,6 +169,8 @@ def run_ours(args):
     from paper_2510_24543_gb300 import egpe as E
     from paper_2510_24543_gb300 import inputs as I
 
+    from paper_2510_24543_gb300 import replicas as RP
+
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dist = None
@@ -158,23 +183,15 @@ def run_ours(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return RP.combine(dist, x, 0.0, device="cuda")[0]
 
     def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return RP.combine(dist, 0.0, x, device="cuda")[1]
 
     B.build()
     E.load()
     w0 = I.PRESETS[args.workload]
-    w = I.Workload(w0.name, w0.n, w0.L, w0.trap, w0.g, w0.gdd, w0.lhy_c, w0.seed + rank, w0.precond, w0.lhy_nodes)
+    w = RP.rank_workload(w0, rank)
     N = w.points
     psi0_np = I.gaussian_start(w)
     stream = torch.cuda.Stream()
@@ -245,15 +262,26 @@ def run_ours(args):
     att_ms = sum(t for _, t, _ in prof32)
     att_bytes = sum(b for _, _, b in prof32)
     dom = max(prof32, key=lambda x: x[1])
-    ach = dom[2] / (dom[1] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom[0], "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "peak_kind": peak_kind + " (burst copy)",
-                "traffic": traffic_record(dom[0], args.workload),
-                "algorithmic_bytes": dom[2], "ms_per_launch": dom[1], "share_of_attempt": round(dom[1] / att_ms, 4),
-                "attempt": {"ms": round(att_ms, 4), "algorithmic_bytes": att_bytes,
-                            "achieved_GBs": round(att_bytes / (att_ms * 1e-3) / 1e9, 1),
-                            "frac": round(att_bytes / (att_ms * 1e-3) / 1e9 / hbm, 4)},
-                "kernels": [{"name": n, "ms": round(t, 5), "GBs": round(b / (t * 1e-3) / 1e9, 1)} for n, t, b in prof32]}
+    gbs = dom[2] / (dom[1] * 1e-3) / 1e9
+    fl = kernel_flops(dom[0], N, w.lhy_nodes, w.n[0])
+    attempt = {"ms": round(att_ms, 4), "algorithmic_bytes": att_bytes,
+               "achieved_GBs": round(att_bytes / (att_ms * 1e-3) / 1e9, 1),
+               "frac_hbm": round(att_bytes / (att_ms * 1e-3) / 1e9 / hbm, 4)}
+    common = {"kernel": dom[0], "ms_per_launch": dom[1], "share_of_attempt": round(dom[1] / att_ms, 4),
+              "traffic": traffic_record(dom[0], args.workload), "algorithmic_bytes": dom[2],
+              "hbm_view": {"achieved_GBs": round(gbs, 1), "frac": round(gbs / hbm, 4), "peak_GBs": hbm,
+                           "peak_kind": peak_kind + " (burst copy)"},
+              "attempt": attempt,
+              "kernels": [{"name": n, "ms": round(t, 5), "GBs": round(b / (t * 1e-3) / 1e9, 1)} for n, t, b in prof32]}
+    if fl is not None:
+        tf = fl / (dom[1] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                    "frac": round(tf / FP32_PEAK_TFLOPS, 4),
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                    "algorithmic_flops": fl, **common}
+    else:
+        roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(gbs / hbm, 4), "peak_kind": peak_kind + " (burst copy)", **common}
     dom64 = max(prof64, key=lambda x: x[1])
     fp64["dominant_kernel"] = {"name": dom64[0], "ms": dom64[1], "share": round(dom64[1] / sum(t for _, t, _ in prof64), 4),
                                "bound": "alu (FP64)"}
