@@ -3,6 +3,7 @@
 // the captured CUDA graph of one solver attempt.  Implemented in engine_impl.cuh
 // and instantiated for double and float in their own translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -79,11 +80,13 @@ template <class R> class Engine {
   egpe_status read_state(DevState& hs);
   template <class Op> egpe_status launch_x(KArgs<R> a);
   egpe_status launch_point(void (*kern)(KArgs<R>), const char* name, double bytes, const KArgs<R>& a);
-  template <class Op> egpe_status launch_col(KArgs<R> a);
+  template <class Op> egpe_status launch_col(KArgs<R> a, const CUtensorMap* tm);
   template <template <class, int> class OpT> egpe_status dispatch_x(int L, const KArgs<R>& a);
-  template <template <class, int> class OpT> egpe_status dispatch_col(int L, const KArgs<R>& a);
+  template <template <class, int> class OpT> egpe_status dispatch_col(int L, const KArgs<R>& a, const CUtensorMap* tm);
   egpe_status plain_x(int inverse, const KArgs<R>& a);
-  egpe_status plain_col(int axis, int inverse, const KArgs<R>& a);
+  egpe_status plain_col(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm);
+  const CUtensorMap* tmy() const { return have_maps_ ? &tmW_y_ : nullptr; }
+  const CUtensorMap* tmz() const { return have_maps_ ? &tmW_z_ : nullptr; }
   int occupancy(const void* fn, int block, size_t smem);
   void t_begin(const char* name, int L, double bytes);
   void t_end();
@@ -97,6 +100,10 @@ template <class R> class Engine {
   bool timing_ = false;
   // LHY epilogues as separate pointwise kernels (true) or fused into the last x pass
   bool split_lhy_ = false;
+  // strided passes fed by TMA (tensor maps over the workspace W)
+  bool use_tma_ = true;
+  bool have_maps_ = false;
+  CUtensorMap tmW_y_{}, tmW_z_{};
   size_t tpos_ = 0;
 
   KArgs<R>* base_ = nullptr;  // host copy of the common kernel arguments

@@ -28,6 +28,50 @@ namespace egpe {
     if (s_ != EGPE_OK) return s_;   \
   } while (0)
 
+typedef CUresult (*TmaEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+static TmaEncodeFn tma_encode_fn() {
+  static TmaEncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TmaEncodeFn>(p);
+  }
+  return fn;
+}
+
+// Columns per tile of the strided passes: 128-byte rows, at least one warp.
+template <class C> static inline int col_tile_width(int L, int nx) {
+  const int TPL = L / 8;
+  return std::min(std::max((int)(128 / sizeof(C)), 32 / TPL), nx);
+}
+
+// Tensor map of `nfields` consecutive complex fields (nx, ny, nz), box = one
+// column tile of the y (axis 1) or z (axis 2) pass.
+template <class C>
+static bool make_col_map(CUtensorMap& tm, const void* base, int nx, int ny, int nz, int nfields, int axis) {
+  TmaEncodeFn fn = tma_encode_fn();
+  if (!fn) return false;
+  const int L = axis == 1 ? ny : nz;
+  const int M = col_tile_width<C>(L, nx);
+  const cuuint64_t esz = sizeof(C) / 8;
+  cuuint64_t dims[3] = {(cuuint64_t)nx * esz, (cuuint64_t)ny, (cuuint64_t)nz * nfields};
+  cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(C), (cuuint64_t)nx * ny * sizeof(C)};
+  cuuint32_t box[3] = {(cuuint32_t)(M * esz), axis == 1 ? (cuuint32_t)L : 1u, axis == 1 ? 1u : (cuuint32_t)L};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(&tm, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static inline bool supported_len(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
 
 // Gauss-Legendre rule on [0,1] by Newton iteration on P_Q (long double).
@@ -172,6 +216,7 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   a.st = st_;
   a.trace = nullptr;
   a.gate = GATE_ALWAYS;
+  have_maps_ = make_col_map<C>(tmW_y_, a.W, nx, ny, nz, 3, 1) && make_col_map<C>(tmW_z_, a.W, nx, ny, nz, 3, 2);
   return reset_state(nullptr, 0, 0, 0.0, 0.0);
 }
 
@@ -317,20 +362,29 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   return EGPE_OK;
 }
 
-template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R> a) {
+template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R> a, const CUtensorMap* tm) {
   constexpr int L = Op::L, TPL = L / 8, NS = Op::NS;
-  int M = std::max((int)(128 / sizeof(C)), 32 / TPL);
-  M = std::min(M, nx);
+  const int M = col_tile_width<C>(L, nx);
   a.M = M;
   const int block = M * TPL;
-  const size_t smem = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const int other = (Op::AXIS == 1) ? nz : ny;
   const int tiles = (nx / M) * other * a.nf;
-  const int occ = occupancy((const void*)colpass_kernel<Op>, block, smem);
-  const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
-  if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
-  colpass_kernel<Op><<<grid, block, smem, stream>>>(a);
-  if (timing_) t_end();
+  if (tm && use_tma_) {
+    const size_t smem = 2 * (size_t)M * L * sizeof(C) + L * sizeof(C) + 2 * sizeof(uint64_t) +
+                        (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+    const int occ = occupancy((const void*)colpass_tma_kernel<Op>, block, smem);
+    const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
+    if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
+    colpass_tma_kernel<Op><<<grid, block, smem, stream>>>(*tm, a);
+    if (timing_) t_end();
+  } else {
+    const size_t smem = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+    const int occ = occupancy((const void*)colpass_kernel<Op>, block, smem);
+    const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
+    if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
+    colpass_kernel<Op><<<grid, block, smem, stream>>>(a);
+    if (timing_) t_end();
+  }
   ++kernels_;
   EGPE_CUDA(cudaGetLastError());
   return EGPE_OK;
@@ -349,13 +403,13 @@ egpe_status Engine<R>::dispatch_x(int L, const KArgs<R>& a) {
 }
 
 template <class R> template <template <class, int> class OpT>
-egpe_status Engine<R>::dispatch_col(int L, const KArgs<R>& a) {
+egpe_status Engine<R>::dispatch_col(int L, const KArgs<R>& a, const CUtensorMap* tm) {
   switch (L) {
-    case 16: return launch_col<OpT<R, 16>>(a);
-    case 32: return launch_col<OpT<R, 32>>(a);
-    case 64: return launch_col<OpT<R, 64>>(a);
-    case 128: return launch_col<OpT<R, 128>>(a);
-    case 256: return launch_col<OpT<R, 256>>(a);
+    case 16: return launch_col<OpT<R, 16>>(a, tm);
+    case 32: return launch_col<OpT<R, 32>>(a, tm);
+    case 64: return launch_col<OpT<R, 64>>(a, tm);
+    case 128: return launch_col<OpT<R, 128>>(a, tm);
+    case 256: return launch_col<OpT<R, 256>>(a, tm);
   }
   return EGPE_ERR_UNSUPPORTED;
 }
@@ -370,12 +424,14 @@ template <class R> egpe_status Engine<R>::plain_x(int inverse, const KArgs<R>& a
   return EGPE_ERR_UNSUPPORTED;
 }
 
-template <class R> egpe_status Engine<R>::plain_col(int axis, int inverse, const KArgs<R>& a) {
+template <class R>
+egpe_status Engine<R>::plain_col(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm) {
   const int L = axis == 1 ? ny : nz;
 #define EGPE_PC(LL)                                                                             \
   case LL:                                                                                      \
-    if (axis == 1) return inverse ? launch_col<ColPlain<R, LL, 1, true>>(a) : launch_col<ColPlain<R, LL, 1, false>>(a); \
-    return inverse ? launch_col<ColPlain<R, LL, 2, true>>(a) : launch_col<ColPlain<R, LL, 2, false>>(a);
+    if (axis == 1)                                                                              \
+      return inverse ? launch_col<ColPlain<R, LL, 1, true>>(a, tm) : launch_col<ColPlain<R, LL, 1, false>>(a, tm); \
+    return inverse ? launch_col<ColPlain<R, LL, 2, true>>(a, tm) : launch_col<ColPlain<R, LL, 2, false>>(a, tm);
   switch (L) {
     EGPE_PC(16) EGPE_PC(32) EGPE_PC(64) EGPE_PC(128) EGPE_PC(256)
   }
@@ -396,9 +452,9 @@ template <class R> egpe_status Engine<R>::enq_eg(int trial, int gate, int ctrl) 
   KArgs<R> y = a;
   y.gin = a.W;
   y.gout = a.W;
-  EGPE_TRY(plain_col(1, 0, y));
-  EGPE_TRY(dispatch_col<ZEg>(nz, a));
-  EGPE_TRY(plain_col(1, 1, y));
+  EGPE_TRY(plain_col(1, 0, y, tmy()));
+  EGPE_TRY(dispatch_col<ZEg>(nz, a, tmz()));
+  EGPE_TRY(plain_col(1, 1, y, tmy()));
   a.ctrl = ctrl;
   if (!split_lhy_) return dispatch_x<XInvEG>(nx, a);
   a.ctrl = 0;
@@ -421,9 +477,9 @@ template <class R> egpe_status Engine<R>::enq_pc(int mode, int gate, int ctrl, i
     KArgs<R> y = a;
     y.gin = a.W;
     y.gout = a.W;
-    EGPE_TRY(plain_col(1, 0, y));
-    EGPE_TRY(dispatch_col<ZPc>(nz, a));
-    EGPE_TRY(plain_col(1, 1, y));
+    EGPE_TRY(plain_col(1, 0, y, tmy()));
+    EGPE_TRY(dispatch_col<ZPc>(nz, a, tmz()));
+    EGPE_TRY(plain_col(1, 1, y, tmy()));
     a.ctrl = ctrl;
     return dispatch_x<XInvPC>(nx, a);
   }
@@ -450,11 +506,11 @@ template <class R> egpe_status Engine<R>::enq_lc(int gate, int ctrl, int pgiven)
   KArgs<R> y = a;
   y.gin = a.W;
   y.gout = a.W;
-  EGPE_TRY(plain_col(1, 0, y));
-  EGPE_TRY(dispatch_col<ZLc>(nz, a));
+  EGPE_TRY(plain_col(1, 0, y, tmy()));
+  EGPE_TRY(dispatch_col<ZLc>(nz, a, tmz()));
   y.nf = 1;
   y.f0 = 2;
-  EGPE_TRY(plain_col(1, 1, y));
+  EGPE_TRY(plain_col(1, 1, y, tmy()));
   a.ctrl = ctrl;
   if (!split_lhy_) return dispatch_x<XInvLC>(nx, a);
   a.ctrl = 0;
@@ -601,8 +657,11 @@ template <class R> egpe_status Engine<R>::fft(const C* in, C* out, int nf, int i
     a.gout = out + (size_t)f * N;
     EGPE_TRY(plain_x(inverse, a));
     a.gin = out + (size_t)f * N;
-    EGPE_TRY(plain_col(1, inverse, a));
-    EGPE_TRY(plain_col(2, inverse, a));
+    CUtensorMap my, mz;
+    const bool ok = use_tma_ && make_col_map<C>(my, out + (size_t)f * N, nx, ny, nz, 1, 1) &&
+                    make_col_map<C>(mz, out + (size_t)f * N, nx, ny, nz, 1, 2);
+    EGPE_TRY(plain_col(1, inverse, a, ok ? &my : nullptr));
+    EGPE_TRY(plain_col(2, inverse, a, ok ? &mz : nullptr));
   }
   EGPE_CUDA(cudaStreamSynchronize(stream));
   return EGPE_OK;

@@ -17,6 +17,7 @@
 #include "fft.cuh"
 #include "lhy.cuh"
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace egpe {
 
@@ -165,7 +166,108 @@ template <class Op> __global__ void __launch_bounds__(512) colpass_kernel(KArgs<
     const int f = a.f0 + rest / other_n;
     const int x = xb * a.M + m;
     const size_t base = (size_t)f * a.N + (Op::AXIS == 1 ? (size_t)o * a.nx * a.ny : (size_t)o * a.nx) + x;
-    Op::run(a, u, f, x, o, base, lstride, t, buf + m, tw, ColIdx{a.M}, acc);
+    const C* src = Op::src(a);
+    C v[1][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[0][e] = src[base + (size_t)Plan<L>::entry_pos(Op::FIRST_INV, t, e) * lstride];
+    Op::process(a, u, f, x, o, base, lstride, t, v, buf + m, tw, ColIdx{a.M}, acc);
+  }
+  if constexpr (NS > 0) {
+    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
+      if (threadIdx.x == 0) Op::finish(a, u);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Column (y or z) pass fed by TMA.  The tensor map describes the workspace as
+// a 3D array (x in 8-byte elements, y, z x fields); one box is one tile, M
+// columns by the whole line, landing in shared memory position-major exactly
+// as the FFT's column layout expects.  While tile i is transformed, tile i+1
+// is already loading into the other buffer.  Results go straight to global
+// memory from registers.
+// ----------------------------------------------------------------------------
+template <class Op>
+__global__ void __launch_bounds__(512)
+    colpass_tma_kernel(const __grid_constant__ CUtensorMap tm, KArgs<typename Op::R> a) {
+  using R = typename Op::R;
+  using C = C2<R>;
+  constexpr int L = Op::L, NS = Op::NS;
+  constexpr int NSR = NS > 0 ? NS : 1;
+  if (!gate_open(a)) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int tileC = a.M * L;
+  C* tiles = reinterpret_cast<C*>(smraw);  // two tiles
+  C* tw = tiles + 2 * tileC;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
+  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(bar + 2);
+  const int tid = threadIdx.x;
+  const int m = tid % a.M, t = tid / a.M;
+  const C* twsrc = (Op::AXIS == 1) ? a.twy : a.twz;
+  for (int i = tid; i < L; i += blockDim.x) tw[i] = twsrc[i];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  typename Op::Uni u;
+  Op::uniform(a, u);
+  double acc[NSR];
+#pragma unroll
+  for (int s = 0; s < NSR; ++s) acc[s] = 0.0;
+  const int xb_n = a.nx / a.M;
+  const int other_n = (Op::AXIS == 1) ? a.nz : a.ny;
+  const int tiles_n = xb_n * other_n * a.nf;
+  const size_t lstride = (Op::AXIS == 1) ? (size_t)a.nx : (size_t)a.nx * a.ny;
+  const uint32_t bytes = (uint32_t)(tileC * sizeof(C));
+  constexpr int ESZ = (int)(sizeof(C) / 8);  // 8-byte TMA elements per complex value
+  auto issue = [&](int tile, int b) {
+    const int xb = tile % xb_n;
+    const int rest = tile / xb_n;
+    const int o = rest % other_n;
+    const int f = a.f0 + rest / other_n;
+    const int c0 = xb * a.M * ESZ;
+    const int c1 = (Op::AXIS == 1) ? 0 : o;
+    const int c2 = (Op::AXIS == 1) ? f * a.nz + o : f * a.nz;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[b], bytes);
+    tma_load_3d(tiles + b * tileC, &tm, c0, c1, c2, &bar[b]);
+  };
+  if (tid == 0 && (int)blockIdx.x < tiles_n) issue(blockIdx.x, 0);
+  bool timed_out = false, next_pending = false;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < tiles_n; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    const int next = tile + gridDim.x;
+    next_pending = next < tiles_n;
+    if (tid == 0 && next_pending) issue(next, b ^ 1);
+    const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitPolls);
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    C* tb = tiles + b * tileC;
+    C v[1][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[0][e] = tb[Plan<L>::entry_pos(Op::FIRST_INV, t, e) * a.M + m];
+    __syncthreads();  // the tile buffer becomes the FFT's exchange buffer
+    const int xb = tile % xb_n;
+    const int rest = tile / xb_n;
+    const int o = rest % other_n;
+    const int f = a.f0 + rest / other_n;
+    const int x = xb * a.M + m;
+    const size_t base = (size_t)f * a.N + (Op::AXIS == 1 ? (size_t)o * a.nx * a.ny : (size_t)o * a.nx) + x;
+    Op::process(a, u, f, x, o, base, lstride, t, v, tb + m, tw, ColIdx{a.M}, acc);
+    __syncthreads();  // buffer b may be refilled from the next iteration on
+  }
+  if (timed_out) {
+    // let the copy already issued for the next tile land (bounded) before exiting
+    if (next_pending) mbar_wait(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kTmaWaitPolls);
+    if (tid == 0) {
+      a.st->status = 7;  // EGPE_ERR_TIMEOUT
+      a.st->phase = PH_DONE;
+    }
   }
   if constexpr (NS > 0) {
     if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
@@ -212,11 +314,10 @@ template <class R_, int L_, int AXIS_, bool INV_> struct ColPlain {
   static constexpr bool INV = INV_;
   using Uni = NoUni;
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
-  static __device__ void run(const KArgs<R>& a, Uni&, int, int, int, size_t base, size_t ls, int t, C* sm,
-                             const C* tw, ColIdx si, double*) {
-    C v[1][8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[0][e] = a.gin[base + (size_t)Plan<L>::entry_pos(INV, t, e) * ls];
+  static constexpr bool FIRST_INV = INV_;
+  static __device__ const C* src(const KArgs<R>& a) { return a.gin; }
+  static __device__ void process(const KArgs<R>& a, Uni&, int, int, int, size_t base, size_t ls, int t,
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, double*) {
     fft_line<C, L, INV, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.gout[base + (size_t)Plan<L>::exit_pos(INV, t, e) * ls] = v[0][e];
@@ -321,11 +422,10 @@ template <class R_, int L_> struct ZEg {
     const int cur = __ldcg(&a.st->cur);
     u.slot = a.flag ? (cur ^ 1) : cur;
   }
-  static __device__ void run(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t, C* sm,
-                             const C* tw, ColIdx si, double* acc) {
-    C v[1][8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[0][e] = a.W[base + (size_t)Plan<L>::entry_pos(false, t, e) * ls];
+  static constexpr bool FIRST_INV = false;
+  static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  static __device__ void process(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t,
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, double* acc) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -607,15 +707,14 @@ template <class R_, int L_> struct ZPc {
     u.shift[0] = (R)__ldcg(&a.st->shift[0]);
     u.shift[1] = (R)__ldcg(&a.st->shift[1]);
   }
-  static __device__ void run(const KArgs<R>& a, Uni& u, int f, int x, int y, size_t base, size_t ls, int t, C* sm,
-                             const C* tw, ColIdx si, double*) {
-    C v[1][8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[0][e] = a.W[base + (size_t)Plan<L>::entry_pos(false, t, e) * ls];
+  static constexpr bool FIRST_INV = false;
+  static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  static __device__ void process(const KArgs<R>& a, Uni& u, int f, int x, int y, size_t base, size_t ls, int t,
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, double*) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
-    const R sh = u.shift[f];
+    const R sh = f == 0 ? u.shift[0] : u.shift[1];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const R kz = wavenum<R>(Plan<L>::exit_pos(false, t, e), a.nz, a.dkz);
@@ -821,11 +920,10 @@ template <class R_, int L_> struct ZLc {
   static constexpr int L = L_, NS = 2, AXIS = 2;
   using Uni = NoUni;
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
-  static __device__ void run(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t, C* sm,
-                             const C* tw, ColIdx si, double* acc) {
-    C v[1][8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[0][e] = a.W[base + (size_t)Plan<L>::entry_pos(false, t, e) * ls];
+  static constexpr bool FIRST_INV = false;
+  static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  static __device__ void process(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t,
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, double* acc) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
