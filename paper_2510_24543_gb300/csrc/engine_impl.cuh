@@ -345,7 +345,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   constexpr int LP = row_len_padded<R, L>();
   const size_t rowbytes = (size_t)NF * LP * sizeof(C);
   int mx = std::max(1, 32 / TPL);
-  while ((mx * 2) * TPL <= 256 && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
+  while ((mx * 2) * TPL <= MaxThreads<Op>::v && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
   a.MX = mx;
   const int block = mx * TPL;
   const size_t smem = L * sizeof(C) + (Op::USES_LHY ? (size_t)a.Q * sizeof(LhyNode<R>) : 0) + mx * rowbytes +

@@ -12,6 +12,7 @@
 // FP64 partial sums stay few; the last block finalises the sums in a fixed
 // order and, where a pipeline needs it, runs the controller step.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 #include "ctrl.cuh"
 #include "fft.cuh"
@@ -112,9 +113,7 @@ template <class Op> __global__ void __launch_bounds__(256) xpass_kernel(KArgs<ty
   __syncthreads();
   typename Op::Uni u;
   Op::uniform(a, u);
-  double acc[NSR];
-#pragma unroll
-  for (int s = 0; s < NSR; ++s) acc[s] = 0.0;
+  PAcc<R> acc[NSR];
   const int rows = a.ny * a.nz;
   const int ngroups = (rows + a.MX - 1) / a.MX;
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
@@ -126,7 +125,10 @@ template <class Op> __global__ void __launch_bounds__(256) xpass_kernel(KArgs<ty
     Op::store(a, u, row, valid, t, v, acc, nodes);
   }
   if constexpr (NS > 0) {
-    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
+    double dacc[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dacc[s] = acc[s].get();
+    if (reduce_blocks<NS>(dacc, a.partials, a.counter, Op::out(a, u), *red)) {
       if (threadIdx.x == 0) Op::finish(a, u);
     }
   }
@@ -152,9 +154,7 @@ template <class Op> __global__ void __launch_bounds__(512) colpass_kernel(KArgs<
   __syncthreads();
   typename Op::Uni u;
   Op::uniform(a, u);
-  double acc[NSR];
-#pragma unroll
-  for (int s = 0; s < NSR; ++s) acc[s] = 0.0;
+  PAcc<R> acc[NSR];
   const int xb_n = a.nx / a.M;
   const int other_n = (Op::AXIS == 1) ? a.nz : a.ny;
   const int tiles = xb_n * other_n * a.nf;
@@ -173,7 +173,10 @@ template <class Op> __global__ void __launch_bounds__(512) colpass_kernel(KArgs<
     Op::process(a, u, f, x, o, base, lstride, t, v, buf + m, tw, ColIdx{a.M}, acc);
   }
   if constexpr (NS > 0) {
-    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
+    double dacc[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dacc[s] = acc[s].get();
+    if (reduce_blocks<NS>(dacc, a.partials, a.counter, Op::out(a, u), *red)) {
       if (threadIdx.x == 0) Op::finish(a, u);
     }
   }
@@ -213,9 +216,7 @@ __global__ void __launch_bounds__(512)
   __syncthreads();
   typename Op::Uni u;
   Op::uniform(a, u);
-  double acc[NSR];
-#pragma unroll
-  for (int s = 0; s < NSR; ++s) acc[s] = 0.0;
+  PAcc<R> acc[NSR];
   const int xb_n = a.nx / a.M;
   const int other_n = (Op::AXIS == 1) ? a.nz : a.ny;
   const int tiles_n = xb_n * other_n * a.nf;
@@ -270,13 +271,24 @@ __global__ void __launch_bounds__(512)
     }
   }
   if constexpr (NS > 0) {
-    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
+    double dacc[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) dacc[s] = acc[s].get();
+    if (reduce_blocks<NS>(dacc, a.partials, a.counter, Op::out(a, u), *red)) {
       if (threadIdx.x == 0) Op::finish(a, u);
     }
   }
 }
 
 struct NoUni {};
+
+// Threads per block of a row pass: 256 unless the op asks for fewer.
+template <class Op, class = void> struct MaxThreads {
+  static constexpr int v = 256;
+};
+template <class Op> struct MaxThreads<Op, std::void_t<decltype(Op::MAXT)>> {
+  static constexpr int v = Op::MAXT;
+};
 
 // ----------------------------------------------------------------------------
 // Plain transforms (diagnostic entry point and the y passes of the pipelines)
@@ -290,12 +302,12 @@ template <class R_, int L_, bool INV_> struct XPlain {
   static constexpr bool INV = INV_, USES_LHY = false;
   using Uni = NoUni;
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
-  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], double*) {
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*) {
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       v[0][e] = valid ? a.gin[(size_t)row * a.nx + Plan<L>::entry_pos(INV, t, e)] : cmk<C>(0, 0);
   }
-  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], double*,
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*,
                                const LhyNode<R>*) {
     if (!valid) return;
 #pragma unroll
@@ -317,7 +329,7 @@ template <class R_, int L_, int AXIS_, bool INV_> struct ColPlain {
   static constexpr bool FIRST_INV = INV_;
   static __device__ const C* src(const KArgs<R>& a) { return a.gin; }
   static __device__ void process(const KArgs<R>& a, Uni&, int, int, int, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, double*) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
     fft_line<C, L, INV, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.gout[base + (size_t)Plan<L>::exit_pos(INV, t, e) * ls] = v[0][e];
@@ -357,7 +369,7 @@ template <class R_, int L_> struct XFwdEG {
       u.cb[i] = (R)__ldcg(&a.st->coef_b[i]);
     }
   }
-  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8], double*) {
+  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*) {
     const C* src = a.psi[u.cur];
     const C* pd = a.pb[u.nsel];
     C* dst = a.psi[u.slot];
@@ -395,7 +407,7 @@ template <class R_, int L_> struct XFwdEG {
       }
     }
   }
-  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], double*,
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*,
                                const LhyNode<R>*) {
     if (!valid) return;
 #pragma unroll
@@ -425,7 +437,7 @@ template <class R_, int L_> struct ZEg {
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
   static __device__ void process(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, double* acc) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>* acc) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -444,7 +456,7 @@ template <class R_, int L_> struct ZEg {
       }
       v[0][e] = cscale(v[0][e], mult);
     }
-    if (f < 2) acc[f] += (double)ekin;
+    if (f < 2) acc[f].add(ekin);
     fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
@@ -462,7 +474,7 @@ template <class R_, int L_> struct XInvEG {
   static constexpr bool INV = true, USES_LHY = true;
   using Uni = EgUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { XFwdEG<R, L>::uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], double*) {
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*) {
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
@@ -472,7 +484,7 @@ template <class R_, int L_> struct XInvEG {
   }
   static constexpr int NP = LhyNP<R>::v;
   static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8],
-                               double* acc, const LhyNode<R>* nodes) {
+                               PAcc<R>* acc, const LhyNode<R>* nodes) {
     if (!valid) return;
     const C* ps = a.psi[u.slot];
     C* hp = a.hp[u.slot];
@@ -529,7 +541,7 @@ template <class R_, int L_> struct XInvEG {
       }
     }
 #pragma unroll
-    for (int k = 0; k < EG_NS; ++k) acc[k] += (double)s[k];
+    for (int k = 0; k < EG_NS; ++k) acc[k].add(s[k]);
   }
   static __device__ double* out(const KArgs<R>& a, Uni& u) { return a.st->eg[u.slot]; }
   static __device__ void finish(const KArgs<R>& a, Uni&) {
@@ -654,7 +666,7 @@ template <class R_, int L_> struct XFwdPC {
   static constexpr bool INV = false, USES_LHY = false;
   using Uni = PcUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { pc_uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], double*) {
+  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*) {
     const int y = row % a.ny, z = row / a.ny;
     const R Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
     const R vyz = a.vy * Y * Y + a.vz * Z * Z;
@@ -680,7 +692,7 @@ template <class R_, int L_> struct XFwdPC {
       }
     }
   }
-  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], double*,
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*,
                                const LhyNode<R>*) {
     if (!valid) return;
 #pragma unroll
@@ -710,7 +722,7 @@ template <class R_, int L_> struct ZPc {
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
   static __device__ void process(const KArgs<R>& a, Uni& u, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, double*) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -731,13 +743,14 @@ template <class R_, int L_> struct ZPc {
 template <class R_, int L_> struct XInvPC {
   using R = R_;
   using C = C2<R>;
+  static constexpr int MAXT = 128;  // heavy epilogue: smaller blocks, more of them per SM
   static constexpr const char* NAME = "x-inv precond sums";
   static double alg_bytes(const KArgs<R>& a) { return 12.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 2, NS = PC_NS;
   static constexpr bool INV = true, USES_LHY = false;
   using Uni = PcUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { pc_uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], double*) {
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*) {
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
@@ -745,7 +758,7 @@ template <class R_, int L_> struct XInvPC {
       v[1][e] = valid ? a.W[(size_t)a.N + idx] : cmk<C>(0, 0);
     }
   }
-  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], double* acc,
+  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], PAcc<R>* acc,
                                const LhyNode<R>*) {
     if (!valid) return;
     R s[PC_NS];
@@ -767,7 +780,7 @@ template <class R_, int L_> struct XInvPC {
       }
     }
 #pragma unroll
-    for (int k = 0; k < PC_NS; ++k) acc[k] += (double)s[k];
+    for (int k = 0; k < PC_NS; ++k) acc[k].add(s[k]);
   }
   static __device__ double* out(const KArgs<R>& a, Uni&) { return a.st->pc; }
   static __device__ void finish(const KArgs<R>& a, Uni&) {
@@ -786,9 +799,7 @@ __global__ void __launch_bounds__(256) pc_point_kernel(KArgs<R> a) {
   __shared__ RedSmem<PC_NS> red;
   PcUni<R> u;
   pc_uniform(a, u);
-  double acc[PC_NS];
-#pragma unroll
-  for (int k = 0; k < PC_NS; ++k) acc[k] = 0.0;
+  PAcc<R> acc[PC_NS];
   const size_t N = a.N;
   const size_t nxy = (size_t)a.nx * a.ny;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
@@ -810,9 +821,12 @@ __global__ void __launch_bounds__(256) pc_point_kernel(KArgs<R> a) {
     pc_sum_load<R>(a, u, idx, si);
     pc_sum_add<R>(si, w1, w2, s);
 #pragma unroll
-    for (int k = 0; k < PC_NS; ++k) acc[k] += (double)s[k];
+    for (int k = 0; k < PC_NS; ++k) acc[k].add(s[k]);
   }
-  if (reduce_blocks<PC_NS>(acc, a.partials, a.counter, a.st->pc, red)) {
+  double dacc[PC_NS];
+#pragma unroll
+  for (int k = 0; k < PC_NS; ++k) dacc[k] = acc[k].get();
+  if (reduce_blocks<PC_NS>(dacc, a.partials, a.counter, a.st->pc, red)) {
     if (threadIdx.x == 0 && a.ctrl) ctrl_after_pc(a.st);
   }
 }
@@ -845,7 +859,7 @@ template <class R_, int L_> struct XFwdLC {
   static constexpr bool INV = false, USES_LHY = false;
   using Uni = LcUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { lc_uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8], double*) {
+  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*) {
     const size_t N = a.N;
     const C* ps = a.psi[u.cur];
     C* pd = a.pb[u.nsel];
@@ -898,7 +912,7 @@ template <class R_, int L_> struct XFwdLC {
       }
     }
   }
-  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], double*,
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*,
                                const LhyNode<R>*) {
     if (!valid) return;
 #pragma unroll
@@ -923,7 +937,7 @@ template <class R_, int L_> struct ZLc {
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
   static __device__ void process(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, double* acc) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>* acc) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -934,7 +948,7 @@ template <class R_, int L_> struct ZLc {
         const R kz = wavenum<R>(Plan<L>::exit_pos(false, t, e), a.nz, a.dkz);
         tk += R(0.5) * (kxy2 + kz * kz) * cabs2(v[0][e]);
       }
-      acc[f] += (double)tk;
+      acc[f].add(tk);
       return;
     }
 #pragma unroll
@@ -961,13 +975,13 @@ template <class R_, int L_> struct XInvLC {
   static constexpr bool INV = true, USES_LHY = true;
   using Uni = LcUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { lc_uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], double*) {
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*) {
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       v[0][e] = valid ? a.W[(size_t)2 * a.N + (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e)] : cmk<C>(0, 0);
   }
   static constexpr int NP = LhyNP<R>::v;
-  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[1][8], double* acc,
+  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[1][8], PAcc<R>* acc,
                                const LhyNode<R>* nodes) {
     if (!valid) return;
     const size_t N = a.N;
@@ -1019,7 +1033,7 @@ template <class R_, int L_> struct XInvLC {
       for (int j = 0; j < NP; ++j) s[LC_HLHY] += Hh[j];
     }
 #pragma unroll
-    for (int k = 0; k < LC_NS; ++k) acc[k] += (double)s[k];
+    for (int k = 0; k < LC_NS; ++k) acc[k].add(s[k]);
   }
   static __device__ double* out(const KArgs<R>& a, Uni&) { return a.st->lc; }
   static __device__ void finish(const KArgs<R>& a, Uni&) {
@@ -1046,7 +1060,7 @@ template <class R_, int L_, int NF_, int F0_> struct XInvW {
   static double alg_bytes(const KArgs<R>& a) { return 2.0 * NF * a.N * sizeof(C); }
   using Uni = NoUni;
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
-  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[NF][8], double*) {
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[NF][8], PAcc<R>*) {
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
@@ -1054,7 +1068,7 @@ template <class R_, int L_, int NF_, int F0_> struct XInvW {
       for (int f = 0; f < NF; ++f) v[f][e] = valid ? a.W[(size_t)(F0_ + f) * a.N + idx] : cmk<C>(0, 0);
     }
   }
-  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[NF][8], double*,
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[NF][8], PAcc<R>*,
                                const LhyNode<R>*) {
     if (!valid) return;
 #pragma unroll

@@ -7,6 +7,26 @@
 
 namespace egpe {
 
+// Per-thread partial sum.  FP64 fields accumulate in FP64; FP32 fields
+// accumulate in FP32 with Kahan compensation (GB300's FP64 pipe is narrow, so
+// one conversion per thread instead of one FP64 add per tile), which keeps the
+// per-thread partial as accurate as an FP64 accumulation of the same terms.
+template <class R> struct PAcc {
+  R v = R(0);
+  __device__ __forceinline__ void add(R x) { v += x; }
+  __device__ __forceinline__ double get() const { return (double)v; }
+};
+template <> struct PAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - lo;
+    const float t = hi + y;
+    lo = (t - hi) - y;
+    hi = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)hi - (double)lo; }
+};
+
 // Shared scratch for NS values per warp (32 warps max).
 template <int NS> struct RedSmem {
   double w[32][NS];
