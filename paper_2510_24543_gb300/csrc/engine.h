@@ -121,6 +121,7 @@ template <class R> class Engine {
   TraceDev* trace_ = nullptr;
   int trace_alloc_ = 0;
   int nsm_ = 0;
+  int Qm_ = 0;  // LHY nodes with det eta > 0 (stored first)
   long long kernels_ = 0;
   std::unordered_map<unsigned long long, int> occ_;
   cudaGraphExec_t graph_[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -158,7 +158,8 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
       const long double ang = 2.0L * pi * (long double)m / (long double)g.n[ax];
       tw[ax][m] = make_double2((double)cosl(ang), (double)(-sinl(ang)));
     }
-  LhyNode<double> nodes[64];
+  LhyNode<double> nodes[64], nneg[64];
+  int qm = 0, qn = 0;
   {
     const int Q = p.lhy_nodes;
     const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
@@ -189,11 +190,19 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
       const long double u = 0.5L * (1.0L + x), w = 1.0L / ((1.0L - x * x) * dp * dp);
       const long double sdd = 3.0L * u * u - 1.0L;
       const long double e12 = p.g[0][1] + p.gdd[0][1] * sdd;
-      nodes[q].w = (double)sdd;
-      nodes[q].W = (double)(c5 * w);
-      nodes[q].Ww = (double)(c5 * w * sdd);
-      nodes[q].e12sq = (double)(e12 * e12);
+      const long double det = (p.g[0][0] + p.gdd[0][0] * sdd) * (p.g[1][1] + p.gdd[1][1] * sdd) - e12 * e12;
+      LhyNode<double> nd;
+      nd.w = (double)sdd;
+      nd.W = (double)(c5 * w);
+      nd.Ww = (double)(c5 * w * sdd);
+      nd.e12sq = (double)(e12 * e12);
+      if (det > 0.0L) {
+        nodes[qm++] = nd;
+      } else {
+        nneg[qn++] = nd;
+      }
     }
+    for (int q = 0; q < qn; ++q) nodes[qm + q] = nneg[q];
   }
   double2* twd = (double2*)(base + kOffTw);
   for (int ax = 0; ax < 3; ++ax) {
@@ -241,6 +250,7 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
   a.d22 = p.gdd[1][1];
   a.invN = 1.0 / (double)N;
   a.Q = p.lhy_nodes;
+  a.Qm = qm;
   a.nodes = (const LhyNode<double>*)(base + kOffNodes);
   a.twx = twd;
   a.twy = twd + kNoAllocMaxN;

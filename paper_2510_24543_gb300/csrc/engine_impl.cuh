@@ -160,16 +160,22 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
     const int Q = p.lhy_nodes;
     std::vector<long double> u, w;
     gauss_legendre01(Q, u, w);
-    std::vector<LhyNode<R>> h(Q);
+    std::vector<LhyNode<R>> h;
+    std::vector<LhyNode<R>> hneg;
     const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
     for (int q = 0; q < Q; ++q) {
       const long double s = 3.0L * u[q] * u[q] - 1.0L;
       const long double e12 = p.g[0][1] + p.gdd[0][1] * s;
-      h[q].w = (R)s;
-      h[q].W = (R)(c5 * w[q]);
-      h[q].Ww = (R)(c5 * w[q] * s);
-      h[q].e12sq = (R)(e12 * e12);
+      const long double det = (p.g[0][0] + p.gdd[0][0] * s) * (p.g[1][1] + p.gdd[1][1] * s) - e12 * e12;
+      LhyNode<R> nd;
+      nd.w = (R)s;
+      nd.W = (R)(c5 * w[q]);
+      nd.Ww = (R)(c5 * w[q] * s);
+      nd.e12sq = (R)(e12 * e12);
+      (det > 0.0L ? h : hneg).push_back(nd);
     }
+    Qm_ = (int)h.size();
+    h.insert(h.end(), hneg.begin(), hneg.end());
     EGPE_CUDA(cudaMalloc(&nodes_, Q * sizeof(LhyNode<R>)));
     EGPE_CUDA(cudaMemcpy(nodes_, h.data(), Q * sizeof(LhyNode<R>), cudaMemcpyHostToDevice));
   }
@@ -207,6 +213,7 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   a.d22 = (R)p.gdd[1][1];
   a.invN = (R)(1.0 / (double)N);
   a.Q = p.lhy_nodes;
+  a.Qm = Qm_;
   a.nodes = nodes_;
   a.twx = twx_;
   a.twy = twy_;
@@ -352,10 +359,13 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
                       (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const int rows = ny * nz;
   const int groups = (rows + mx - 1) / mx;
-  const int occ = occupancy((const void*)xpass_kernel<Op>, block, smem);
+  void (*kern)(KArgs<R>);
+  if constexpr (MinBlocks<Op>::v > 1) kern = xpass_kernel_mb<Op>;
+  else kern = xpass_kernel<Op>;
+  const int occ = occupancy((const void*)kern, block, smem);
   const int grid = std::min(groups, std::min(occ * nsm_, 16384));
   if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
-  xpass_kernel<Op><<<grid, block, smem, stream>>>(a);
+  kern<<<grid, block, smem, stream>>>(a);
   if (timing_) t_end();
   ++kernels_;
   EGPE_CUDA(cudaGetLastError());

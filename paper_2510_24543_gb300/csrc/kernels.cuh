@@ -20,6 +20,13 @@
 #include "reduce.cuh"
 #include "tma.cuh"
 
+#ifndef EGPE_EG_MINB
+#define EGPE_EG_MINB 1
+#endif
+#ifndef EGPE_LC_MINB
+#define EGPE_LC_MINB 1
+#endif
+
 namespace egpe {
 
 template <class R> struct KArgs {
@@ -31,7 +38,7 @@ template <class R> struct KArgs {
   R g11, g12, g21, g22;      // contact couplings
   R d11, d12, d21, d22;      // k-space dipolar coefficients
   R invN;
-  int Q;
+  int Q, Qm;  // Gauss-Legendre nodes; the first Qm have det eta > 0
   const LhyNode<R>* nodes;
   const C* twx;
   const C* twy;
@@ -89,10 +96,35 @@ template <class R> __device__ __forceinline__ R wavenum(int j, int n, R dk) {
   return dk * (R)(j < (n >> 1) ? j : j - n);
 }
 
+// Row-pass ops that read their transform outputs back from shared memory.
+template <class Op, class = void> struct StageOut {
+  static constexpr bool v = false;
+};
+template <class Op> struct StageOut<Op, std::void_t<decltype(Op::STAGE_OUT)>> {
+  static constexpr bool v = Op::STAGE_OUT;
+};
+
+// Minimum resident blocks per SM a row-pass op asks the compiler to allow for
+// (caps its registers); 1 unless the op says otherwise.
+template <class Op, class = void> struct MinBlocks {
+  static constexpr int v = 1;
+};
+template <class Op> struct MinBlocks<Op, std::void_t<decltype(Op::MINB)>> {
+  static constexpr int v = Op::MINB;
+};
+
+// Threads per block of a row pass: 256 unless the op asks for fewer.
+template <class Op, class = void> struct MaxThreads {
+  static constexpr int v = 256;
+};
+template <class Op> struct MaxThreads<Op, std::void_t<decltype(Op::MAXT)>> {
+  static constexpr int v = Op::MAXT;
+};
+
 // ----------------------------------------------------------------------------
 // Row (x) pass kernel
 // ----------------------------------------------------------------------------
-template <class Op> __global__ void __launch_bounds__(256) xpass_kernel(KArgs<typename Op::R> a) {
+template <class Op> __device__ __forceinline__ void xpass_body(const KArgs<typename Op::R>& a) {
   using R = typename Op::R;
   using C = C2<R>;
   constexpr int L = Op::L, NF = Op::NF, NS = Op::NS;
@@ -122,7 +154,20 @@ template <class Op> __global__ void __launch_bounds__(256) xpass_kernel(KArgs<ty
     C v[NF][8];
     Op::load(a, u, row, valid, t, v, acc);
     fft_line<C, L, Op::INV, NF>(v, buf + mrow * LP, a.MX * LP, tw, t, RowIdx<PadShift<R>::v>{});
-    Op::store(a, u, row, valid, t, v, acc, nodes);
+    if constexpr (StageOut<Op>::v) {
+      // park the transform outputs in the (idle) exchange buffer: the FFT
+      // registers are dead during the epilogue, which frees them for it
+      C* sm = buf + mrow * LP;
+      const RowIdx<PadShift<R>::v> si{};
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sm[f * a.MX * LP + si(Plan<L>::exit_pos(Op::INV, t, e))] = v[f][e];
+      Op::store_staged(a, u, row, valid, t, sm, a.MX * LP, acc, nodes);
+      __syncthreads();  // the next row group's exchanges reuse the buffer
+    } else {
+      Op::store(a, u, row, valid, t, v, acc, nodes);
+    }
   }
   if constexpr (NS > 0) {
     double dacc[NS];
@@ -132,6 +177,17 @@ template <class Op> __global__ void __launch_bounds__(256) xpass_kernel(KArgs<ty
       if (threadIdx.x == 0) Op::finish(a, u);
     }
   }
+}
+
+// Row-pass entry points.  A min-blocks bound is given only when the op asks for
+// more than one resident block: an explicit 1 lets the compiler take far more
+// registers than the default heuristic does.
+template <class Op> __global__ void __launch_bounds__(MaxThreads<Op>::v) xpass_kernel(KArgs<typename Op::R> a) {
+  xpass_body<Op>(a);
+}
+template <class Op>
+__global__ void __launch_bounds__(MaxThreads<Op>::v, MinBlocks<Op>::v) xpass_kernel_mb(KArgs<typename Op::R> a) {
+  xpass_body<Op>(a);
 }
 
 // ----------------------------------------------------------------------------
@@ -281,14 +337,6 @@ __global__ void __launch_bounds__(512)
 }
 
 struct NoUni {};
-
-// Threads per block of a row pass: 256 unless the op asks for fewer.
-template <class Op, class = void> struct MaxThreads {
-  static constexpr int v = 256;
-};
-template <class Op> struct MaxThreads<Op, std::void_t<decltype(Op::MAXT)>> {
-  static constexpr int v = Op::MAXT;
-};
 
 // ----------------------------------------------------------------------------
 // Plain transforms (diagnostic entry point and the y passes of the pipelines)
@@ -468,6 +516,8 @@ template <class R_, int L_> struct ZEg {
 template <class R_, int L_> struct XInvEG {
   using R = R_;
   using C = C2<R>;
+  static constexpr int MAXT = 128;
+  static constexpr int MINB = sizeof(R_) == 4 ? EGPE_EG_MINB : 1;
   static constexpr const char* NAME = "x-inv energy+LHY";
   static double alg_bytes(const KArgs<R>& a) { return 9.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 3, NS = EG_NS;
@@ -483,8 +533,10 @@ template <class R_, int L_> struct XInvEG {
     }
   }
   static constexpr int NP = LhyNP<R>::v;
-  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8],
-                               PAcc<R>* acc, const LhyNode<R>* nodes) {
+  static constexpr bool STAGE_OUT = true;
+  static __device__ void store_staged(const KArgs<R>& a, Uni& u, int row, bool valid, int t, const C* sm, int fs,
+                                      PAcc<R>* acc, const LhyNode<R>* nodes) {
+    const RowIdx<PadShift<R>::v> si{};
     if (!valid) return;
     const C* ps = a.psi[u.slot];
     C* hp = a.hp[u.slot];
@@ -509,7 +561,7 @@ template <class R_, int L_> struct XInvEG {
         n1[j] = cabs2(p1[j]);
         n2[j] = cabs2(p2[j]);
       }
-      lhy_points<R, NP>(nodes, a.Q, cf, n1, n2, F, m1, m2);
+      lhy_points<R, NP>(nodes, a.Q, a.Qm, cf, n1, n2, F, m1, m2);
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
         const int e = e0 + j;
@@ -517,11 +569,13 @@ template <class R_, int L_> struct XInvEG {
         const size_t idx = (size_t)row * a.nx + x;
         const R X = -a.Lx + (R)x * a.hx;
         const R V = a.vx * X * X + vyz;
-        const R phi1 = v[2][e].x, phi2 = v[2][e].y;
+        const int o = si(x);
+        const C T1 = sm[o], T2 = sm[fs + o], PH = sm[2 * fs + o];
+        const R phi1 = PH.x, phi2 = PH.y;
         const R U1 = V + a.g11 * n1[j] + a.g12 * n2[j] + phi1 + m1[j];
         const R U2 = V + a.g21 * n1[j] + a.g22 * n2[j] + phi2 + m2[j];
-        const C H1 = cmk<C>(v[0][e].x + U1 * p1[j].x, v[0][e].y + U1 * p1[j].y);
-        const C H2 = cmk<C>(v[1][e].x + U2 * p2[j].x, v[1][e].y + U2 * p2[j].y);
+        const C H1 = cmk<C>(T1.x + U1 * p1[j].x, T1.y + U1 * p1[j].y);
+        const C H2 = cmk<C>(T2.x + U2 * p2[j].x, T2.y + U2 * p2[j].y);
         hp[idx] = H1;
         hp[N + idx] = H2;
         ax[idx] = cmk<C>(phi1, phi2);
@@ -969,6 +1023,7 @@ template <class R_, int L_> struct ZLc {
 template <class R_, int L_> struct XInvLC {
   using R = R_;
   using C = C2<R>;
+  static constexpr int MINB = sizeof(R_) == 4 ? EGPE_LC_MINB : 1;
   static constexpr const char* NAME = "x-inv line sums+LHY";
   static double alg_bytes(const KArgs<R>& a) { return 9.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 1, NS = LC_NS;
@@ -1028,7 +1083,7 @@ template <class R_, int L_> struct XInvLC {
         s[LC_UPP2] += U2 * a2;
         s[LC_SRHO] += rho1 * (a.g11 * rho1 + a.g12 * rho2 + v[0][e].x) + rho2 * (a.g21 * rho1 + a.g22 * rho2 + v[0][e].y);
       }
-      lhy_hess<R, NP>(nodes, a.Q, cf, n1, n2, n1p, n2p, Hh);
+      lhy_hess<R, NP>(nodes, a.Q, a.Qm, cf, n1, n2, n1p, n2p, Hh);
 #pragma unroll
       for (int j = 0; j < NP; ++j) s[LC_HLHY] += Hh[j];
     }
@@ -1128,7 +1183,7 @@ template <class R> __global__ void __launch_bounds__(256) eg_point_kernel(KArgs<
       n1[j] = ok[j] ? cabs2(p1[j]) : R(0);
       n2[j] = ok[j] ? cabs2(p2[j]) : R(0);
     }
-    lhy_points<R, NP>(nodes, a.Q, cf, n1, n2, F, m1, m2);
+    lhy_points<R, NP>(nodes, a.Q, a.Qm, cf, n1, n2, F, m1, m2);
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       if (!ok[j]) continue;
@@ -1220,7 +1275,7 @@ template <class R> __global__ void __launch_bounds__(256) lc_point_kernel(KArgs<
       s[LC_UPP2] += U2 * a2;
       s[LC_SRHO] += rho1 * (a.g11 * rho1 + a.g12 * rho2 + phr.x) + rho2 * (a.g21 * rho1 + a.g22 * rho2 + phr.y);
     }
-    lhy_hess<R, NP>(nodes, a.Q, cf, n1, n2, n1p, n2p, Hh);
+    lhy_hess<R, NP>(nodes, a.Q, a.Qm, cf, n1, n2, n1p, n2p, Hh);
 #pragma unroll
     for (int j = 0; j < NP; ++j) s[LC_HLHY] += Hh[j];
   }

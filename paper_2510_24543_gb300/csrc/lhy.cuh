@@ -11,6 +11,8 @@
 // coefficients of sigma_i(w) are formed once per point, and the node loop only
 // carries what depends on the square roots.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace egpe {
@@ -37,6 +39,12 @@ template <class R> __device__ __forceinline__ void inv_s(R s2, R& rs, R& s) {
   s = s2 * rs;
 }
 
+// 1/s with a tiny offset instead of a branch: where s^2 is 0 the quantities
+// multiplied by it, (V+^{3/2} - V-^{3/2}), vanish with it.
+template <class R> __device__ __forceinline__ R s2_eps();
+template <> __device__ __forceinline__ double s2_eps<double>() { return 1e-300; }
+template <> __device__ __forceinline__ float s2_eps<float>() { return 1e-30f; }
+
 // Per-point coefficients.
 template <class R> struct LhyPt {
   R A0, A1, D0, D1, q4;  // q4 = 4 n1 n2
@@ -60,7 +68,7 @@ template <class R> __device__ __forceinline__ LhyPt<R> lhy_pt(const LhyCoef<R>& 
 // W_q already includes kappa eta_s^{-5/2}.  NP points are evaluated together
 // (independent dependency chains per node).
 template <class R, int NP>
-__device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c,
+__device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, int Q, int Qm, const LhyCoef<R>& c,
                                            const R (&n1)[NP], const R (&n2)[NP], R (&F)[NP], R (&mu1)[NP],
                                            R (&mu2)[NP]) {
   LhyPt<R> p[NP];
@@ -70,21 +78,26 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
     p[j] = lhy_pt(c, n1[j], n2[j]);
     f[j] = S0[j] = S1[j] = T0[j] = T1[j] = T2[j] = R(0);
   }
-#pragma unroll 2
-  for (int k = 0; k < Q; ++k) {
-    const LhyNode<R> e = nd[k];
+  // nodes [0, Qm): det eta > 0, both branches; [Qm, Q): det eta <= 0, where
+  // V+ V- = 4 n1 n2 det(eta) <= 0 makes max(V-, 0) = 0 at every point
+  auto node = [&](const LhyNode<R>& e, auto minus) {
     const R Www = e.Ww * e.w;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       const R A = p[j].A0 + p[j].A1 * e.w;
       const R d = p[j].D0 + p[j].D1 * e.w;
       const R s2 = d * d + e.e12sq * p[j].q4;
-      R rs, s;
-      inv_s(s2, rs, s);
-      const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
-      const R sp = sqrt_pos(vp), sm = sqrt_pos(vm);
-      const R p32 = vp * sp, m32 = vm * sm;
-      f[j] += e.W * (vp * p32 + vm * m32);
+      const R rs = rsqrt_(s2 + s2_eps<R>());
+      const R s = s2 * rs;
+      const R vp = fmax(A + s, R(0));
+      const R p32 = vp * sqrt_pos(vp);
+      R m32 = R(0), m52 = R(0);
+      if constexpr (decltype(minus)::value) {
+        const R vm = fmax(A - s, R(0));
+        m32 = vm * sqrt_pos(vm);
+        m52 = vm * m32;
+      }
+      f[j] += e.W * (vp * p32 + m52);
       const R sum32 = p32 + m32;
       const R t = (p32 - m32) * rs;
       S0[j] += e.W * sum32;
@@ -93,6 +106,16 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
       T1[j] += e.Ww * t;
       T2[j] += Www * t;
     }
+  };
+  if constexpr (std::is_same<R, float>::value) {
+    // FP32: one loop (the skipped branch is cheap there, registers are not)
+#pragma unroll 2
+    for (int k = 0; k < Q; ++k) node(nd[k], std::true_type{});
+  } else {
+#pragma unroll 2
+    for (int k = 0; k < Qm; ++k) node(nd[k], std::true_type{});
+#pragma unroll 2
+    for (int k = Qm; k < Q; ++k) node(nd[k], std::false_type{});
   }
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
@@ -117,7 +140,7 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
 // K_+- = +-(delta1^2 + 4 eta12^2 n1' n2' - t1^2)/(2s),  delta1 = eta11 n1' - eta22 n2'
 // (the n''-free part of the paper's V^2_+-, Sec. V auxiliaries).  NP points together.
 template <class R, int NP>
-__device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c,
+__device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int Q, int Qm, const LhyCoef<R>& c,
                                          const R (&n1)[NP], const R (&n2)[NP], const R (&n1p)[NP],
                                          const R (&n2p)[NP], R (&H)[NP]) {
   LhyPt<R> p[NP];
@@ -133,9 +156,7 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
     mp[j] = R(4) * n1p[j] * n2p[j];                   // 4 eta12^2 n1' n2' = eta12^2 mp
     h[j] = R(0);
   }
-#pragma unroll 2
-  for (int k = 0; k < Q; ++k) {
-    const LhyNode<R> e = nd[k];
+  auto node = [&](const LhyNode<R>& e, auto minus) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       const R A = p[j].A0 + p[j].A1 * e.w;
@@ -143,16 +164,32 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
       const R s2 = d * d + e.e12sq * p[j].q4;
       R rs, s;
       inv_s(s2, rs, s);
-      const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
-      const R sp = sqrt_pos(vp), sm = sqrt_pos(vm);
+      const R vp = fmax(A + s, R(0));
+      const R sp = sqrt_pos(vp);
       const R A1 = B0[j] + B1[j] * e.w;
       const R d1 = E0[j] + E1[j] * e.w;
       const R t1 = (d * d1 + e.e12sq * m[j]) * rs;
       const R K = (d1 * d1 + e.e12sq * mp[j] - t1 * t1) * (R(0.5) * rs);
-      const R v1p = A1 + t1, v1m = A1 - t1;
-      const R acc = R(2) * K * (vp * sp - vm * sm) + R(1.5) * (sp * v1p * v1p + sm * v1m * v1m);
+      const R v1p = A1 + t1;
+      R acc = R(2) * K * (vp * sp) + R(1.5) * (sp * v1p * v1p);
+      if constexpr (decltype(minus)::value) {
+        const R vm = fmax(A - s, R(0));
+        const R sm = sqrt_pos(vm);
+        const R v1m = A1 - t1;
+        acc += R(-2) * K * (vm * sm) + R(1.5) * (sm * v1m * v1m);
+      }
       h[j] += e.W * acc;
     }
+  };
+  if constexpr (std::is_same<R, float>::value) {
+    // FP32: one loop (the skipped branch is cheap there, registers are not)
+#pragma unroll 2
+    for (int k = 0; k < Q; ++k) node(nd[k], std::true_type{});
+  } else {
+#pragma unroll 2
+    for (int k = 0; k < Qm; ++k) node(nd[k], std::true_type{});
+#pragma unroll 2
+    for (int k = Qm; k < Q; ++k) node(nd[k], std::false_type{});
   }
 #pragma unroll
   for (int j = 0; j < NP; ++j) H[j] = R(2.5) * h[j];
