@@ -102,7 +102,7 @@ typedef struct {
 /* Options of egpe_ncg_solve (Algorithm 1 with the readings named below). */
 typedef struct {
   int precond;              /* EGPE_PRECOND_*                                        */
-  int beta_rule;            /* 0: Hestenes-Stiefel+ (Sec. IV.C); others reserved    */
+  int beta_rule;            /* 0: Hestenes-Stiefel+, 1: Polak-Ribiere+ (Sec. IV.C)   */
   int restart_period;       /* K_r: beta = 0 when n mod K_r == 0                     */
   int max_iter;             /* accepted iterations                                   */
   int armijo_max;           /* halvings after a rejected step (Sec. V, last para.)  */

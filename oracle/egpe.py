@@ -391,6 +391,7 @@ class SolveOpts:
     theta_max: float = 0.5 * math.pi
     accept_rtol: float = 1e-13     # round-off allowance: accept if E_t < E + accept_rtol |E|
     pv_floor: float = 1e-2
+    beta_rule: str = "HS"          # "HS" (Hestenes-Stiefel+) or "PR" (Polak-Ribiere+)
 
 
 def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = SolveOpts(),
@@ -400,7 +401,8 @@ def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = Solve
     Per iteration n (Algorithm 1 order):
       r_i = H_i psi_i - mu_i psi_i                         (Sec. III / IV.A)
       z = P^{-1} r                                          (Sec. IV.B)
-      beta = max(beta_HS, 0), HS denominator on p^{n-1}     (Sec. IV.C; reading: the
+      beta = max(beta_HS, 0) (or max(beta_PR, 0) with beta_rule "PR"), HS denominator on
+             p^{n-1}                                        (Sec. IV.C; reading: the
              printed p^{(n)} is the previous direction); beta = 0 when n mod K_r == 0,
              when the denominator is zero or non-finite, and when the resulting
              direction has Re<r, p> >= 0 (restart rule of Sec. IV.C)
@@ -419,6 +421,7 @@ def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = Solve
     ev = evaluate(grid, prm, psi)
     r_prev = None
     p_prev = None
+    rz_prev = None
     alpha_prev = None
     n_it = 0
     restarts = 0
@@ -441,9 +444,15 @@ def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = Solve
         z = precondition(grid, prm, ev, psi, r, opts.precond, opts.pv_floor)
         restart = (n_it % opts.restart_period == 0) or p_prev is None
         beta = 0.0
+        rz = sum(inner(grid, r[i], z[i]).real for i in range(2))
         if not restart:
             num = sum(inner(grid, r[i] - r_prev[i], z[i]).real for i in range(2))
-            den = sum(inner(grid, r[i] - r_prev[i], p_prev[i]).real for i in range(2))
+            if opts.beta_rule == "PR":
+                # PR+: Re<r^n - r^{n-1}, P^{-1} r^n> / Re<r^{n-1}, P^{-1} r^{n-1}> (Sec. IV.C);
+                # reading: the denominator uses the preconditioner of iteration n-1
+                den = rz_prev
+            else:
+                den = sum(inner(grid, r[i] - r_prev[i], p_prev[i]).real for i in range(2))
             if den == 0.0 or not np.isfinite(den) or not np.isfinite(num):
                 restart = True
             else:
@@ -503,7 +512,7 @@ def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = Solve
             status = "stagnated"
             break
         dE = ev_t.E - ev.E
-        r_prev, p_prev = r, p
+        r_prev, p_prev, rz_prev = r, p, rz
         psi, ev = psi_t, ev_t
         alpha_prev = alpha
         n_it += 1

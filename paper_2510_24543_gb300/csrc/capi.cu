@@ -290,7 +290,7 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
 }
 
 static bool opts_ok(const egpe_solve_opts& o) {
-  return !(o.precond < 0 || o.precond > 3 || o.beta_rule != 0 || o.max_iter < 0 || o.armijo_max < 0 ||
+  return !(o.precond < 0 || o.precond > 3 || o.beta_rule < 0 || o.beta_rule > 1 || o.max_iter < 0 || o.armijo_max < 0 ||
            o.armijo_max > 60 || !(o.tol_res >= 0.0) || !(o.theta_max > 0.0) || !(o.pv_floor > 0.0) ||
            o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace));
 }

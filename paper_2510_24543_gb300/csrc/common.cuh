@@ -57,7 +57,7 @@ enum Phase { PH_NEW_ITER = 0, PH_TRIAL = 1, PH_DONE = 2 };
 enum Gate { GATE_ALWAYS = 0, GATE_NEW_ITER = 1, GATE_ACTIVE = 2 };
 
 struct SolveOptsDev {
-  int precond, restart_period, max_iter, armijo_max, trace_cap, fp32_phase;
+  int precond, restart_period, max_iter, armijo_max, trace_cap, fp32_phase, beta_rule, pad;
   double tol_res, tol_dE, armijo_c1, theta_max, accept_rtol, pv_floor;
 };
 
@@ -86,6 +86,7 @@ struct DevState {
   // iteration scalars
   double res, beta, c[2], alpha0, alpha, alpha_prev, theta[2], pnorm2[2];
   double Ep, Epp, coef_a[2], coef_b[2], E_trial, dE_last, psip[2];
+  double rz, rz_prev;  // Re<r, P^{-1} r> of this and of the previous iteration (PR+ beta)
   double dV, invN;
   long long ffts;
 };

@@ -3,7 +3,8 @@
 // whole iteration stays on the device and can be replayed as a CUDA graph.
 //
 // Readings (where the paper is silent or garbled):
-// * HS+ beta with the previous projected direction p^{n-1} in the denominator,
+// * HS+ beta with the previous projected direction p^{n-1} in the denominator
+//   (or PR+ with Re<r^{n-1}, P^{-1} r^{n-1}> of the previous iteration),
 //   restart (beta = 0) when n mod K_r == 0, on a zero/non-finite denominator,
 //   and when Re<r, p> >= 0 for the resulting direction (Sec. IV.C); if even the
 //   restarted direction is not a descent direction the residual itself is used.
@@ -148,6 +149,7 @@ __device__ inline void ctrl_after_eg(DevState* st, int mode, TraceDev* trace) {
   }
   if (ok) {
     const double Eold = st->E;
+    st->rz_prev = st->rz;
     st->cur = slot;
     load_point(st, slot);
     st->dE_last = st->E - Eold;
@@ -196,8 +198,11 @@ __device__ inline void ctrl_after_pc(DevState* st) {
   }
   bool restart = (op.restart_period <= 0) ? (st->n == 0) : (st->n % op.restart_period == 0);
   double beta = 0.0;
+  st->rz = (pc[PC_ZR1] + pc[PC_ZR2]) * dV;
   if (!restart) {
-    const double num = pc[PC_SRZ], den = pc[PC_SRP];
+    // HS+: Re<r - r_prev, z> / Re<r - r_prev, p_prev>;  PR+: Re<r - r_prev, z> / Re<r_prev, z_prev>
+    const double num = pc[PC_SRZ] * dV;
+    const double den = op.beta_rule == 1 ? st->rz_prev : pc[PC_SRP] * dV;
     if (den == 0.0 || !finite_(den) || !finite_(num)) restart = true;
     else beta = fmax(num / den, 0.0);
   }

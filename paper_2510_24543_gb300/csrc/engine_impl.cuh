@@ -551,6 +551,7 @@ egpe_status Engine<R>::reset_state(const egpe_solve_opts* o, int fp32_phase, int
   h.opt.restart_period = 20;
   if (o) {
     h.opt.precond = o->precond;
+    h.opt.beta_rule = o->beta_rule;
     h.opt.restart_period = o->restart_period;
     h.opt.max_iter = max_iter;
     h.opt.armijo_max = o->armijo_max;

@@ -214,14 +214,17 @@ def _solve_gpu(E, w, psi0, precond, tol, prec=0, trace_cap=0, max_iter=2000, **k
         H.close()
 
 
-def test_ncg_lockstep_first_iterations(E):
+@pytest.mark.parametrize("beta_rule", ["HS", "PR"])
+def test_ncg_lockstep_first_iterations(E, beta_rule):
     """Per-iteration (E, ||r||, beta, alpha) of the first iterations against the oracle."""
     w = I.PRESETS["c1"]
     psi0 = I.gaussian_start(w)
     g, prm = oracle_case(w)
     otr = []
-    O.ncg_solve(g, prm, psi0, O.SolveOpts(precond="kinetic", tol_res=1e-8, max_iter=12), trace=otr)
-    st, rep, tr, _ = _solve_gpu(E, w, psi0, "kinetic", 1e-8, trace_cap=64, max_iter=12)
+    O.ncg_solve(g, prm, psi0, O.SolveOpts(precond="kinetic", tol_res=1e-8, max_iter=12, beta_rule=beta_rule),
+                trace=otr)
+    st, rep, tr, _ = _solve_gpu(E, w, psi0, "kinetic", 1e-8, trace_cap=64, max_iter=12,
+                                beta_rule=1 if beta_rule == "PR" else 0)
     acc = [t for t in tr if t["flags"] & 1]
     assert len(acc) >= 10
     oacc = [t for t in otr if t["accepted"]]

@@ -356,6 +356,20 @@ def test_ncg_all_preconditioners_same_minimum(c1_small):
     assert max(Es) - min(Es) < 1e-11 * abs(Es[0])
 
 
+def test_pr_plus_reaches_the_same_minimum(c1_small):
+    """Polak-Ribiere+ beta (Sec. IV.C) converges to the HS+ minimum, descending monotonically."""
+    g, prm, psi0 = c1_small
+    _, rep_hs = O.ncg_solve(g, prm, psi0, O.SolveOpts(precond="kinetic+diagonal", tol_res=1e-9))
+    tr = []
+    opts = O.SolveOpts(precond="kinetic+diagonal", tol_res=1e-9, beta_rule="PR")
+    _, rep_pr = O.ncg_solve(g, prm, psi0, opts, trace=tr)
+    assert rep_pr["status"] == "converged"
+    assert abs(rep_pr["E"] - rep_hs["E"]) < 1e-11 * abs(rep_hs["E"])
+    assert any(t["beta"] > 0 for t in tr)
+    tau = opts.accept_rtol * abs(tr[0]["E"])
+    assert all(t["E_new"] <= t["E"] + tau for t in tr)
+
+
 def test_symmetric_mixture_keeps_components_equal():
     """Symmetric couplings and psi1 = psi2 at the start give psi1 = psi2 throughout;
     swapping the components leaves E unchanged."""
