@@ -237,6 +237,37 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
 egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts* opts,
                            egpe_report* reports);
 
+/* Options of egpe_ite_solve. */
+typedef struct {
+  double dtau;              /* imaginary-time step (> 0)                             */
+  double tol_dE;            /* stop once |E^{k+1} - E^k| < tol_dE (> 0)              */
+  int max_steps;            /* step limit (> 0); reaching it is NOT_CONVERGED        */
+  int poll_every;           /* steps enqueued between host checks of the stop flag   */
+  int use_graph;            /* replay one captured step (1) or launch kernel by kernel */
+  int psi_on_host;          /* psi_inout are host pointers                          */
+} egpe_ite_opts;
+
+/* Ground state by imaginary-time evolution, the baseline the paper compares
+ * the NCG solver with (Sec. I; step counts and times in Sec. VI.B, stopping
+ * rule |E^{k+1} - E^k| < tol of Sec. VI.A).  The paper does not state its ITE
+ * scheme; this one is the Strang splitting
+ *   psi <- e^{-dtau T/2} e^{-dtau U[psi']} e^{-dtau T/2} psi,  psi_i <- psi_i/||psi_i||,
+ * with U_i = V + sum_j g_ij n_j + Phi_i + mu_LHY^(i) evaluated at the density
+ * of psi' = e^{-dtau T/2} psi.  Runs in the handle's kernels (FP64 handles and
+ * MIXED on the FP64 path, FP32 handles on the FP32 path); psi_inout[i] is the
+ * start and receives the result (device pointers unless opts->psi_on_host).
+ * reports (host, n_inst, may be NULL): iters = steps taken, E / mu / res of
+ * the final state, ffts = 20 per step (two kinetic half steps of 4 transforms,
+ * two evaluations of 6).  Errors: INVALID_ARG (dtau, tol_dE or max_steps not
+ * positive), CUDA; per-instance NOT_CONVERGED / NONFINITE in the reports and
+ * as the return value (first instance that failed). */
+egpe_status egpe_ite_solve(egpe_handle* h, void* const* psi_inout, const egpe_ite_opts* opts,
+                           egpe_report* reports);
+
+/* Defaults: dtau 1e-3, tol_dE 1e-10, 100000 steps, poll every 32, graph on,
+ * device pointers. */
+void egpe_default_ite_opts(egpe_ite_opts* o);
+
 /* Stepping interface: the phases of egpe_ncg_solve one by one, for callers
  * that interleave their own work (event timing, checkpoints) with the solver.
  * engine: 0 the FP64 path (psi complex128), 1 the FP32 path (psi complex64;

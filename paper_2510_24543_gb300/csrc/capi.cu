@@ -443,4 +443,64 @@ egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_so
   return first_bad;
 }
 
+void egpe_default_ite_opts(egpe_ite_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->dtau = 1e-3;
+  o->tol_dE = 1e-10;
+  o->max_steps = 100000;
+  o->poll_every = 32;
+  o->use_graph = 1;
+  o->psi_on_host = 0;
+}
+
+egpe_status egpe_ite_solve(egpe_handle* h, void* const* psi_inout, const egpe_ite_opts* opts,
+                           egpe_report* reports) {
+  if (!h || !psi_inout || !opts) return EGPE_ERR_INVALID_ARG;
+  const egpe_ite_opts& o = *opts;
+  if (!(o.dtau > 0.0) || !std::isfinite(o.dtau) || !(o.tol_dE > 0.0) || o.max_steps <= 0 || o.poll_every < 0) {
+    egpe::set_error_msg("egpe_ite_solve: dtau and tol_dE must be positive and finite, max_steps > 0");
+    return EGPE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < h->n_inst; ++i)
+    if (!psi_inout[i]) return EGPE_ERR_INVALID_ARG;
+  egpe_status first_bad = EGPE_OK;
+  const cudaMemcpyKind kin = o.psi_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind kout = o.psi_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  for (int i = 0; i < h->n_inst; ++i) {
+    const auto t0 = std::chrono::steady_clock::now();
+    egpe::SolveRun run{};
+    egpe_status s;
+    if (h->prec == EGPE_FP32) {
+      auto* e = h->e32[i];
+      s = e->load_psi(psi_inout[i], kin);
+      if (s == EGPE_OK) s = e->ite(o.dtau, o.tol_dE, o.max_steps, o.poll_every, o.use_graph != 0, run);
+      if (s == EGPE_OK) s = e->store_psi(psi_inout[i], kout);
+    } else {
+      auto* e = h->e64[i];
+      s = e->load_psi(psi_inout[i], kin);
+      if (s == EGPE_OK) s = e->ite(o.dtau, o.tol_dE, o.max_steps, o.poll_every, o.use_graph != 0, run);
+      if (s == EGPE_OK) s = e->store_psi(psi_inout[i], kout);
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    egpe_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    rep.status = (s != EGPE_OK) ? s : run.status;
+    rep.iters = run.n;
+    if (h->prec == EGPE_FP32) rep.iters_fp32 = run.n;
+    rep.graph_launches = run.launches;
+    rep.E = run.E;
+    rep.mu[0] = run.mu[0];
+    rep.mu[1] = run.mu[1];
+    rep.res = run.res;
+    rep.seconds = std::chrono::duration<double>(t1 - t0).count();
+    rep.ffts = run.ffts;
+    rep.kernels = run.kernels;
+    if (reports) reports[i] = rep;
+    if (s != EGPE_OK) return s;
+    if (rep.status != EGPE_OK && first_bad == EGPE_OK) first_bad = (egpe_status)rep.status;
+  }
+  return first_bad;
+}
+
 }  // extern "C"

@@ -174,6 +174,25 @@ __device__ inline void ctrl_after_eg(DevState* st, int mode, TraceDev* trace) {
   }
 }
 
+// End of one imaginary-time step: the energy of the renormalised state, the
+// |E^{k+1} - E^k| < tol_dE stopping rule of the ITE comparison (Sec. VI.A).
+__device__ inline void ctrl_after_ite(DevState* st) {
+  const double Eold = st->E;
+  load_point(st, st->cur);
+  st->dE_last = st->E - Eold;
+  st->n += 1;
+  if (!finite_(st->E)) {
+    st->status = 4;
+    st->phase = PH_DONE;
+  } else if (fabs(st->dE_last) < st->opt.tol_dE) {
+    st->status = 0;
+    st->phase = PH_DONE;
+  } else if (st->n >= st->opt.max_iter) {
+    st->status = 5;
+    st->phase = PH_DONE;
+  }
+}
+
 // After the preconditioned residual and its sums: convergence test, beta,
 // projection coefficients, restart rules.
 __device__ inline void ctrl_after_pc(DevState* st) {

@@ -62,6 +62,11 @@ template <class R> class Engine {
   egpe_status solve_launch(int attempts);
   egpe_status solve_poll(int& phase);
   egpe_status solve_finish(SolveRun& run, egpe_trace_entry* trace_out, int trace_cap, int trace_offset);
+  // Imaginary-time evolution (the baseline of the paper's comparison): Strang
+  // steps of size dtau from the state in slot 0 until |E^{k+1} - E^k| < tol_dE
+  // or max_steps; the same begin / launch / poll / finish phases as the solver.
+  egpe_status ite_begin(double dtau, double tol_dE, int max_steps, bool use_graph);
+  egpe_status ite(double dtau, double tol_dE, int max_steps, int poll_every, bool use_graph, SolveRun& run);
   C* current_psi();  // valid after solve (device)
   C* psi_slot0();    // psi buffer 0 (start of a solve)
 
@@ -75,6 +80,8 @@ template <class R> class Engine {
   egpe_status enq_pc(int mode, int gate, int ctrl, int rgiven);
   egpe_status enq_lc(int gate, int ctrl, int pgiven);
   egpe_status enq_attempt(int mode);
+  egpe_status enq_kin(int potential, int gate);
+  egpe_status enq_ite_step(int gate);
   egpe_status reset_state(const egpe_solve_opts* o, int fp32_phase, int max_iter, double tol_res,
                           double accept_rtol);
   egpe_status read_state(DevState& hs);
@@ -128,6 +135,11 @@ template <class R> class Engine {
   int run_mode_ = 0, run_graph_ = 1;
   long long run_k0_ = 0, run_launches_ = 0, per_attempt_ = 0;
   int graph_max_iter_[4] = {0, 0, 0, 0};
+  R* kin_tab_ = nullptr;            // ITE kinetic half-step factors and dtau
+  std::vector<R> kin_host_;
+  cudaGraphExec_t graph_ite_ = nullptr;
+  int ite_per_step_ = 0;
+  bool run_ite_ = false;
 };
 
 }  // namespace egpe

@@ -184,6 +184,8 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   EGPE_CUDA(cudaMemset(counter_, 0, 64 * sizeof(unsigned)));
   EGPE_CUDA(cudaMalloc(&st_, sizeof(DevState)));
   EGPE_CUDA(cudaMallocHost(&st_host_, sizeof(DevState)));
+  EGPE_CUDA(cudaMalloc(&kin_tab_, (size_t)(nx + ny + nz + 1) * sizeof(R)));
+  EGPE_CUDA(cudaMemsetAsync(kin_tab_, 0, (size_t)(nx + ny + nz + 1) * sizeof(R), stream));
   const double hx = 2.0 * g.L[0] / nx, hy = 2.0 * g.L[1] / ny, hz = 2.0 * g.L[2] / nz;
   dV = hx * hy * hz;
   a.nx = nx;
@@ -222,6 +224,7 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   a.counter = counter_;
   a.st = st_;
   a.trace = nullptr;
+  a.kin_tab = kin_tab_;
   a.gate = GATE_ALWAYS;
   have_maps_ = make_col_map<C>(tmW_y_, a.W, nx, ny, nz, 3, 1) && make_col_map<C>(tmW_z_, a.W, nx, ny, nz, 3, 2);
   return reset_state(nullptr, 0, 0, 0.0, 0.0);
@@ -238,6 +241,10 @@ template <class R> void Engine<R>::destroy() {
       cudaGraphExecDestroy(gx);
       gx = nullptr;
     }
+  if (graph_ite_) cudaGraphExecDestroy(graph_ite_);
+  graph_ite_ = nullptr;
+  if (kin_tab_) cudaFree(kin_tab_);
+  kin_tab_ = nullptr;
   if (arena_) cudaFree(arena_);
   if (twx_) cudaFree(twx_);
   if (twy_) cudaFree(twy_);
@@ -718,6 +725,7 @@ egpe_status Engine<R>::solve_begin(const egpe_solve_opts& o, int fp32_phase, int
   EGPE_CUDA(cudaMemsetAsync(base_->rb[0], 0, 8 * N * sizeof(C), stream));
   EGPE_TRY(enq_eg(0, GATE_ALWAYS, 1));
   run_k0_ = kernels_;
+  run_ite_ = false;
   run_mode_ = mode;
   run_graph_ = o.use_graph ? 1 : 0;
   run_launches_ = 0;
@@ -752,9 +760,122 @@ egpe_status Engine<R>::solve_begin(const egpe_solve_opts& o, int fp32_phase, int
   return EGPE_OK;
 }
 
+// Kinetic half step e^{-dtau T/2} of both components (4 transforms), with the
+// potential step e^{-dtau U} in the prologue when `potential` is set (U from
+// the aux fields of the last evaluation).  Leaves the norms in st->rt[0..1].
+template <class R> egpe_status Engine<R>::enq_kin(int potential, int gate) {
+  KArgs<R> a = *base_;
+  a.gate = gate;
+  a.flag = potential;
+  a.ctrl = 0;
+  a.nf = 2;
+  a.f0 = 0;
+  EGPE_TRY(dispatch_x<XFwdKin>(nx, a));
+  KArgs<R> y = a;
+  y.gin = a.W;
+  y.gout = a.W;
+  EGPE_TRY(plain_col(1, 0, y, tmy()));
+  EGPE_TRY(dispatch_col<ZKin>(nz, a, tmz()));
+  EGPE_TRY(plain_col(1, 1, y, tmy()));
+  return dispatch_x<XInvKin>(nx, a);
+}
+
+// One Strang step: kinetic half step, evaluation at the half-stepped state
+// (dipolar and LHY potentials), potential step fused into the second kinetic
+// half step, renormalisation, evaluation of the new state + controller.
+template <class R> egpe_status Engine<R>::enq_ite_step(int gate) {
+  EGPE_TRY(enq_kin(0, gate));
+  EGPE_TRY(enq_eg(0, gate, 0));
+  EGPE_TRY(enq_kin(1, gate));
+  {
+    KArgs<R> a = *base_;
+    a.gate = gate;
+    const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)nsm_ * 8);
+    if (timing_) t_begin("ITE renormalise", 0, 4.0 * N * sizeof(C));
+    ite_scale_kernel<R><<<grid, 256, 0, stream>>>(a);
+    if (timing_) t_end();
+    ++kernels_;
+    EGPE_CUDA(cudaGetLastError());
+  }
+  return enq_eg(0, gate, 2);
+}
+
+template <class R> egpe_status Engine<R>::ite_begin(double dtau, double tol_dE, int max_steps, bool use_graph) {
+  const double pi = 3.14159265358979323846;
+  kin_host_.assign((size_t)(nx + ny + nz + 1), R(0));
+  const int n3[3] = {nx, ny, nz};
+  int off = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const double dk = pi / grid_.L[ax];
+    for (int j = 0; j < n3[ax]; ++j) {
+      const double k = dk * (double)(j < n3[ax] / 2 ? j : j - n3[ax]);
+      kin_host_[off + j] = (R)exp(-0.25 * dtau * k * k);
+    }
+    off += n3[ax];
+  }
+  kin_host_[off] = (R)dtau;
+  EGPE_CUDA(cudaMemcpyAsync(kin_tab_, kin_host_.data(), kin_host_.size() * sizeof(R), cudaMemcpyHostToDevice,
+                            stream));
+  egpe_solve_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.tol_dE = tol_dE;
+  EGPE_TRY(reset_state(&o, sizeof(R) == 4, max_steps, 0.0, 0.0));
+  EGPE_TRY(enq_eg(0, GATE_ALWAYS, 1));
+  run_k0_ = kernels_;
+  run_ite_ = true;
+  run_graph_ = use_graph ? 1 : 0;
+  run_launches_ = 0;
+  per_attempt_ = 0;
+  if (run_graph_ && !graph_ite_) {
+    cudaGraph_t g = nullptr;
+    EGPE_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    const long long kb = kernels_;
+    egpe_status s = enq_ite_step(GATE_ACTIVE);
+    cudaError_t ce = cudaStreamEndCapture(stream, &g);
+    if (s != EGPE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (ce != cudaSuccess) {
+      set_error("cudaStreamEndCapture", ce);
+      return EGPE_ERR_CUDA;
+    }
+    ite_per_step_ = (int)(kernels_ - kb);
+    cudaError_t ie = cudaGraphInstantiate(&graph_ite_, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      set_error("cudaGraphInstantiate", ie);
+      graph_ite_ = nullptr;
+      return EGPE_ERR_CUDA;
+    }
+    kernels_ = kb;
+  }
+  return EGPE_OK;
+}
+
+template <class R>
+egpe_status Engine<R>::ite(double dtau, double tol_dE, int max_steps, int poll_every, bool use_graph, SolveRun& run) {
+  EGPE_TRY(ite_begin(dtau, tol_dE, max_steps, use_graph));
+  const int poll = std::max(1, poll_every);
+  while (run_launches_ < (long long)max_steps) {
+    EGPE_TRY(solve_launch((int)std::min<long long>(poll, (long long)max_steps - run_launches_)));
+    int phase = 0;
+    EGPE_TRY(solve_poll(phase));
+    if (phase == PH_DONE) break;
+  }
+  return solve_finish(run, nullptr, 0, 0);
+}
+
 template <class R> egpe_status Engine<R>::solve_launch(int attempts) {
   for (int k = 0; k < attempts; ++k) {
-    if (run_graph_) {
+    if (run_ite_) {
+      if (run_graph_) {
+        EGPE_CUDA(cudaGraphLaunch(graph_ite_, stream));
+        kernels_ += ite_per_step_;
+      } else {
+        EGPE_TRY(enq_ite_step(GATE_ACTIVE));
+      }
+    } else if (run_graph_) {
       EGPE_CUDA(cudaGraphLaunch(graph_[run_mode_], stream));
       kernels_ += per_attempt_;
     } else {

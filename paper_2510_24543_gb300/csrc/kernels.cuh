@@ -56,6 +56,7 @@ template <class R> struct KArgs {
   unsigned* counter;
   DevState* st;
   TraceDev* trace;
+  const R* kin_tab;          // ITE: e^{-dtau k_a^2/4} per index ([nx] x, [ny] y, [nz] z), then dtau
   int MX, M, nf, f0;         // launch shape: rows per block, columns per tile, fields
   int gate;                  // Gate
   int flag;                  // op-specific (trial / r given / p given)
@@ -400,6 +401,18 @@ template <class R> struct EgUni {
   R ca[2], cb[2];
 };
 
+// Controller step after an energy/gradient evaluation (last block, one thread):
+// ctrl 1 = NCG (start point or trial), ctrl 2 = end of an imaginary-time step.
+template <class R> __device__ __forceinline__ void eg_ctrl(const KArgs<R>& a) {
+  if (a.ctrl == 2) {
+    a.st->ffts += 20;  // two kinetic half steps (8) and two evaluations (12)
+    ctrl_after_ite(a.st);
+  } else if (a.ctrl) {
+    a.st->ffts += 6;
+    ctrl_after_eg(a.st, a.flag ? 1 : 0, a.trace);
+  }
+}
+
 template <class R_, int L_> struct XFwdEG {
   using R = R_;
   using C = C2<R>;
@@ -598,12 +611,7 @@ template <class R_, int L_> struct XInvEG {
     for (int k = 0; k < EG_NS; ++k) acc[k].add(s[k]);
   }
   static __device__ double* out(const KArgs<R>& a, Uni& u) { return a.st->eg[u.slot]; }
-  static __device__ void finish(const KArgs<R>& a, Uni&) {
-    if (a.ctrl) {
-      a.st->ffts += 6;
-      ctrl_after_eg(a.st, a.flag ? 1 : 0, a.trace);
-    }
-  }
+  static __device__ void finish(const KArgs<R>& a, Uni&) { eg_ctrl(a); }
 };
 
 // ----------------------------------------------------------------------------
@@ -1100,6 +1108,166 @@ template <class R_, int L_> struct XInvLC {
 };
 
 // ----------------------------------------------------------------------------
+// Imaginary-time evolution, the paper's baseline (Sec. I, Sec. VI.B): Strang
+// steps psi <- e^{-dtau T/2} e^{-dtau U[psi_half]} e^{-dtau T/2} psi with per-
+// component renormalisation.  A kinetic half step is an FFT pair with the
+// separable multiplier e^{-dtau |k|^2/4} = ex(kx) ey(ky) ez(kz); the potential
+// step is fused into the prologue of the second half step, with U_i = V +
+// sum_j g_ij n_j + Phi_i + mu_LHY^(i) read from the aux fields that the
+// energy/gradient pipeline wrote for the half-stepped state.
+// ----------------------------------------------------------------------------
+template <class R_, int L_> struct XFwdKin {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr const char* NAME = "x-fwd ITE half step";
+  static double alg_bytes(const KArgs<R>& a) { return (a.flag ? 6.0 : 4.0) * a.N * sizeof(C); }
+  static constexpr int L = L_, NF = 2, NS = 0;
+  static constexpr bool INV = false, USES_LHY = false;
+  struct Uni {
+    int cur;
+    R dtau;
+  };
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) {
+    u.cur = __ldcg(&a.st->cur);
+    u.dtau = a.kin_tab[a.nx + a.ny + a.nz];
+  }
+  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*) {
+    const C* ps = a.psi[u.cur];
+    const C* ax = a.ax[u.cur];
+    const size_t N = a.N;
+    const int y = row % a.ny, z = row / a.ny;
+    const R Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
+    const R vyz = a.vy * Y * Y + a.vz * Z * Z;
+    constexpr int CH = ChunkW<R>::v;
+#pragma unroll
+    for (int e0 = 0; e0 < 8; e0 += CH) {
+      C p1[CH], p2[CH], f0[CH], f1[CH];
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e0 + j);
+        const size_t id = valid ? idx : 0;
+        p1[j] = ps[id];
+        p2[j] = ps[N + id];
+        if (a.flag) {
+          f0[j] = ax[id];
+          f1[j] = ax[N + id];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const int e = e0 + j;
+        C q1 = valid ? p1[j] : cmk<C>(0, 0), q2 = valid ? p2[j] : cmk<C>(0, 0);
+        if (a.flag && valid) {
+          const int x = Plan<L>::entry_pos(false, t, e);
+          const R X = -a.Lx + (R)x * a.hx;
+          const R V = a.vx * X * X + vyz;
+          const R n1 = cabs2(q1), n2 = cabs2(q2);
+          const R U1 = V + a.g11 * n1 + a.g12 * n2 + f0[j].x + f1[j].x;
+          const R U2 = V + a.g21 * n1 + a.g22 * n2 + f0[j].y + f1[j].y;
+          q1 = cscale(q1, exp(-u.dtau * U1));
+          q2 = cscale(q2, exp(-u.dtau * U2));
+        }
+        v[0][e] = q1;
+        v[1][e] = q2;
+      }
+    }
+  }
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*,
+                               const LhyNode<R>*) {
+    if (!valid) return;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(false, t, e);
+      a.W[idx] = v[0][e];
+      a.W[(size_t)a.N + idx] = v[1][e];
+    }
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct ZKin {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr const char* NAME = "z fused ITE half step";
+  static double alg_bytes(const KArgs<R>& a) { return 4.0 * a.N * sizeof(C); }
+  static constexpr int L = L_, NS = 0, AXIS = 2;
+  using Uni = NoUni;
+  static __device__ void uniform(const KArgs<R>&, Uni&) {}
+  static constexpr bool FIRST_INV = false;
+  static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  static __device__ void process(const KArgs<R>& a, Uni&, int, int x, int y, size_t base, size_t ls, int t,
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
+    fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
+    const R exy = a.kin_tab[x] * a.kin_tab[a.nx + y] * a.invN;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int kz = Plan<L>::exit_pos(false, t, e);
+      v[0][e] = cscale(v[0][e], exy * a.kin_tab[a.nx + a.ny + kz]);
+    }
+    fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct XInvKin {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr const char* NAME = "x-inv ITE half step";
+  static double alg_bytes(const KArgs<R>& a) { return 4.0 * a.N * sizeof(C); }
+  static constexpr int L = L_, NF = 2, NS = 2;
+  static constexpr bool INV = true, USES_LHY = false;
+  struct Uni {
+    int cur;
+  };
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) { u.cur = __ldcg(&a.st->cur); }
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
+      v[0][e] = valid ? a.W[idx] : cmk<C>(0, 0);
+      v[1][e] = valid ? a.W[(size_t)a.N + idx] : cmk<C>(0, 0);
+    }
+  }
+  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], PAcc<R>* acc,
+                               const LhyNode<R>*) {
+    if (!valid) return;
+    C* ps = a.psi[u.cur];
+    R s0 = 0, s1 = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e);
+      ps[idx] = v[0][e];
+      ps[(size_t)a.N + idx] = v[1][e];
+      s0 += cabs2(v[0][e]);
+      s1 += cabs2(v[1][e]);
+    }
+    acc[0].add(s0);
+    acc[1].add(s1);
+  }
+  static __device__ double* out(const KArgs<R>& a, Uni&) { return a.st->rt; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+// psi_i <- psi_i / ||psi_i|| with the norms the last half step reduced.
+template <class R> __global__ void __launch_bounds__(256) ite_scale_kernel(KArgs<R> a) {
+  if (!gate_open(a)) return;
+  const int cur = __ldcg(&a.st->cur);
+  const double dV = __ldcg(&a.st->dV);
+  const R s1 = (R)(1.0 / sqrt(__ldcg(&a.st->rt[0]) * dV));
+  const R s2 = (R)(1.0 / sqrt(__ldcg(&a.st->rt[1]) * dV));
+  C2<R>* ps = a.psi[cur];
+  const size_t N = a.N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
+    ps[idx] = cscale(ps[idx], s1);
+    ps[N + idx] = cscale(ps[N + idx], s2);
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Split epilogues: the last x pass only inverts the workspace in place, and a
 // pointwise kernel with high occupancy evaluates the LHY quadrature, H psi and
 // the sums.  (Same arithmetic as the fused XInvEG / XInvLC epilogues; the LHY
@@ -1215,10 +1383,7 @@ template <class R> __global__ void __launch_bounds__(256) eg_point_kernel(KArgs<
 #pragma unroll
   for (int k = 0; k < EG_NS; ++k) acc[k] = (double)s[k];
   if (reduce_blocks<EG_NS>(acc, a.partials, a.counter, a.st->eg[u.slot], red)) {
-    if (threadIdx.x == 0 && a.ctrl) {
-      a.st->ffts += 6;
-      ctrl_after_eg(a.st, a.flag ? 1 : 0, a.trace);
-    }
+    if (threadIdx.x == 0) eg_ctrl(a);
   }
 }
 

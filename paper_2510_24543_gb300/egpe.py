@@ -53,6 +53,11 @@ class egpe_trace_entry(ct.Structure):
                 ("alpha", ct.c_double), ("theta", ct.c_double * 2), ("Ep", ct.c_double), ("Epp", ct.c_double)]
 
 
+class egpe_ite_opts(ct.Structure):
+    _fields_ = [("dtau", ct.c_double), ("tol_dE", ct.c_double), ("max_steps", ct.c_int), ("poll_every", ct.c_int),
+                ("use_graph", ct.c_int), ("psi_on_host", ct.c_int)]
+
+
 class egpe_report(ct.Structure):
     _fields_ = [("status", ct.c_int), ("iters", ct.c_int), ("iters_fp32", ct.c_int), ("attempts", ct.c_int),
                 ("restarts", ct.c_int), ("armijo_steps", ct.c_int), ("trace_len", ct.c_int),
@@ -86,6 +91,9 @@ _SIGS = {
     "egpe_energy_grad_noalloc": (ct.c_int, [ct.POINTER(egpe_grid), ct.POINTER(egpe_params), ct.c_void_p,
                                             ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_void_p,
                                             ct.c_void_p]),
+    "egpe_ite_solve": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(egpe_ite_opts),
+                                  ct.POINTER(egpe_report)]),
+    "egpe_default_ite_opts": (None, [ct.POINTER(egpe_ite_opts)]),
     "egpe_default_solve_opts": (None, [ct.POINTER(egpe_solve_opts)]),
     "egpe_status_string": (ct.c_char_p, [ct.c_int]),
     "egpe_last_error": (ct.c_char_p, []),
@@ -270,6 +278,23 @@ def egpe_ncg_solve(h: int, psis, opts: egpe_solve_opts, n_inst: int = 1, trace_c
                               res=e.res, beta=e.beta, alpha=e.alpha, theta=(e.theta[0], e.theta[1]), Ep=e.Ep,
                               Epp=e.Epp))
     return status, out, trace
+
+
+def egpe_default_ite_opts() -> egpe_ite_opts:
+    o = egpe_ite_opts()
+    load().egpe_default_ite_opts(ct.byref(o))
+    return o
+
+
+def egpe_ite_solve(h: int, psis, opts: egpe_ite_opts, n_inst: int = 1):
+    """Imaginary-time evolution in place on psis.  Returns (status, [report dicts])."""
+    lib = load()
+    ptrs = (ct.c_void_p * n_inst)(*[ct.c_void_p(_ptr(x)) for x in psis])
+    reps = (egpe_report * n_inst)()
+    status = lib.egpe_ite_solve(ct.c_void_p(h), ptrs, ct.byref(opts), reps)
+    if status in (1, 2, 3):
+        raise EgpeError("egpe_ite_solve", status)
+    return status, [_report_dict(r) for r in reps]
 
 
 def _report_dict(r) -> dict:
