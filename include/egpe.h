@@ -19,7 +19,7 @@
  *          the caller owns them; the library never frees them.
  * Grid:    periodic box [-L_a, L_a) with n_a points per axis, h_a = 2L_a/n_a,
  *          x_a[j] = -L_a + j h_a; wavenumbers k_a[j] = (pi/L_a)(j or j - n_a).
- *          Supported n_a: 16, 32, 64, 128, 256.
+ *          Supported n_a: 16, 32, 48, 64, 80, 96, 128, 256.
  * Product: <a, b> = dV sum conj(a) b, dV = hx hy hz.
  * Model:   per-particle normalised couplings (N_i -> 1 in Eq. 1):
  *          E = sum_i <psi_i, T psi_i> + int V (n1+n2) + 1/2 int sum_ij g_ij n_i n_j

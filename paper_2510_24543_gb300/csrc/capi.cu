@@ -53,12 +53,14 @@ __global__ void cast_f2d(size_t n, const float2* in, double2* out) {
   }
 }
 
-bool pow2_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+bool len_supported(int n) {
+  return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 48 || n == 80 || n == 96;
+}
 
 egpe_status validate(const egpe_grid& g, const egpe_params& p) {
   for (int a = 0; a < 3; ++a) {
-    if (!pow2_supported(g.n[a])) {
-      egpe::set_error_msg("grid size must be one of 16, 32, 64, 128, 256 on every axis");
+    if (!len_supported(g.n[a])) {
+      egpe::set_error_msg("grid size must be one of 16, 32, 48, 64, 80, 96, 128, 256 on every axis");
       return EGPE_ERR_INVALID_ARG;
     }
     if (!(g.L[a] > 0.0) || !std::isfinite(g.L[a])) {

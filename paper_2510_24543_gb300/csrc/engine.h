@@ -92,6 +92,13 @@ template <class R> class Engine {
   template <template <class, int> class OpT> egpe_status dispatch_col(int L, const KArgs<R>& a, const CUtensorMap* tm);
   egpe_status plain_x(int inverse, const KArgs<R>& a);
   egpe_status plain_col(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm);
+  // Lengths 48, 80, 96 (mixed radix): defined in engine_mr.cuh, instantiated
+  // in their own translation units to keep compile times apart.
+  template <template <class, int> class OpT> egpe_status dispatch_x_mr(int L, const KArgs<R>& a);
+  template <template <class, int> class OpT>
+  egpe_status dispatch_col_mr(int L, const KArgs<R>& a, const CUtensorMap* tm);
+  egpe_status plain_x_mr(int inverse, const KArgs<R>& a);
+  egpe_status plain_col_mr(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm);
   const CUtensorMap* tmy() const { return have_maps_ ? &tmW_y_ : nullptr; }
   const CUtensorMap* tmz() const { return have_maps_ ? &tmW_z_ : nullptr; }
   int occupancy(const void* fn, int block, size_t smem);

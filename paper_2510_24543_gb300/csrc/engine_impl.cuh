@@ -72,7 +72,9 @@ static bool make_col_map(CUtensorMap& tm, const void* base, int nx, int ny, int 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-static inline bool supported_len(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+static inline bool supported_len(int n) {
+  return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 48 || n == 80 || n == 96;
+}
 
 // Gauss-Legendre rule on [0,1] by Newton iteration on P_Q (long double).
 static void gauss_legendre01(int Q, std::vector<long double>& u, std::vector<long double>& w) {
@@ -416,7 +418,7 @@ egpe_status Engine<R>::dispatch_x(int L, const KArgs<R>& a) {
     case 128: return launch_x<OpT<R, 128>>(a);
     case 256: return launch_x<OpT<R, 256>>(a);
   }
-  return EGPE_ERR_UNSUPPORTED;
+  return dispatch_x_mr<OpT>(L, a);
 }
 
 template <class R> template <template <class, int> class OpT>
@@ -428,7 +430,7 @@ egpe_status Engine<R>::dispatch_col(int L, const KArgs<R>& a, const CUtensorMap*
     case 128: return launch_col<OpT<R, 128>>(a, tm);
     case 256: return launch_col<OpT<R, 256>>(a, tm);
   }
-  return EGPE_ERR_UNSUPPORTED;
+  return dispatch_col_mr<OpT>(L, a, tm);
 }
 
 template <class R> egpe_status Engine<R>::plain_x(int inverse, const KArgs<R>& a) {
@@ -438,7 +440,7 @@ template <class R> egpe_status Engine<R>::plain_x(int inverse, const KArgs<R>& a
     EGPE_PX(16) EGPE_PX(32) EGPE_PX(64) EGPE_PX(128) EGPE_PX(256)
   }
 #undef EGPE_PX
-  return EGPE_ERR_UNSUPPORTED;
+  return plain_x_mr(inverse, a);
 }
 
 template <class R>
@@ -453,7 +455,7 @@ egpe_status Engine<R>::plain_col(int axis, int inverse, const KArgs<R>& a, const
     EGPE_PC(16) EGPE_PC(32) EGPE_PC(64) EGPE_PC(128) EGPE_PC(256)
   }
 #undef EGPE_PC
-  return EGPE_ERR_UNSUPPORTED;
+  return plain_col_mr(axis, inverse, a, tm);
 }
 
 

@@ -15,12 +15,38 @@
 //   twiddle         W_{Ns r}^{q (j mod Ns)}   (table entry q (j mod Ns) L/(Ns r))
 //   output position (j div Ns) Ns r + (j mod Ns) + q Ns
 // Thread t of a line owns butterflies j = t + b L/8 (b < 8/r).
+//
+// Lengths 48, 80 and 96 (a power of two times 3 or 5) use the same register
+// interface with a mixed-radix plan (radix 8, then 3/5 and 2/4 passes in
+// shared memory) and natural entry/exit layouts; see fft_mixed.
 #pragma once
 #include "common.cuh"
 
 namespace egpe {
 
-template <int L> struct Plan {
+template <int L> struct IsPow2 {
+  static constexpr bool v = L > 0 && (L & (L - 1)) == 0;
+};
+
+// Radix sequence of the mixed-radix lengths (a multiple of 8 times 3 or 5):
+// radix 8 first, then the remaining factors.
+template <int L> struct MixedPlan {
+  static constexpr int TPL = L / 8;
+  static constexpr int P = (L == 48) ? 3 : (L == 80) ? 3 : (L == 96) ? 3 : -1;
+  static_assert(P > 0, "unsupported FFT length");
+  __host__ __device__ static constexpr int rad(int p) {
+    return p == 0 ? 8 : (L == 48 ? (p == 1 ? 3 : 2) : L == 80 ? (p == 1 ? 5 : 2) : (p == 1 ? 4 : 3));
+  }
+  __host__ __device__ static constexpr int ns(int p) { return p == 0 ? 1 : ns(p - 1) * rad(p - 1); }
+  // natural layout on entry and exit, in both directions
+  __device__ static __forceinline__ int entry_pos(bool, int t, int e) { return t + e * TPL; }
+  __device__ static __forceinline__ int exit_pos(bool, int t, int e) { return t + e * TPL; }
+};
+
+template <int L, bool POW2 = IsPow2<L>::v> struct Plan;
+template <int L> struct Plan<L, false> : MixedPlan<L> {};
+
+template <int L> struct Plan<L, true> {
   static constexpr int TPL = L / 8;
   static constexpr int LOG2 = (L == 8) ? 3 : (L == 16) ? 4 : (L == 32) ? 5 : (L == 64) ? 6
                             : (L == 128) ? 7 : (L == 256) ? 8 : -1;
@@ -91,9 +117,44 @@ template <bool INV, class C> __device__ __forceinline__ void dft8(C* v) {
   v[7] = csub(e3, o3);
 }
 
+// y_k = sum_q a_q W_3^{qk}: with c = cos(2 pi/3) = -1/2 and s = sin(2 pi/3),
+// y_{1,2} = a0 + c (a1 + a2) -/+ i s (a1 - a2) (signs swapped for the inverse).
+template <bool INV, class C> __device__ __forceinline__ void dft3(C* v) {
+  using R = decltype(C::x);
+  const R s = R(0.86602540378443864676372317075294);
+  const C a0 = v[0], t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+  const C b = cmk<C>(a0.x - R(0.5) * t1.x, a0.y - R(0.5) * t1.y);
+  const C d = cscale(INV ? mul_i(t2) : mul_mi(t2), s);
+  v[0] = cadd(a0, t1);
+  v[1] = cadd(b, d);
+  v[2] = csub(b, d);
+}
+
+// Five-point DFT from the real and imaginary parts of W_5^k:
+// c1 = cos(2 pi/5), c2 = cos(4 pi/5), s1 = sin(2 pi/5), s2 = sin(4 pi/5).
+template <bool INV, class C> __device__ __forceinline__ void dft5(C* v) {
+  using R = decltype(C::x);
+  const R c1 = R(0.30901699437494742410229341718282), c2 = R(-0.80901699437494742410229341718282);
+  const R s1 = R(0.95105651629515357211643933337938), s2 = R(0.58778525229247312916870595463907);
+  const C a0 = v[0];
+  const C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  const C b1 = cmk<C>(a0.x + c1 * t1.x + c2 * t2.x, a0.y + c1 * t1.y + c2 * t2.y);
+  const C b2 = cmk<C>(a0.x + c2 * t1.x + c1 * t2.x, a0.y + c2 * t1.y + c1 * t2.y);
+  const C e1 = cmk<C>(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+  const C e2 = cmk<C>(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+  const C d1 = INV ? mul_i(e1) : mul_mi(e1), d2 = INV ? mul_i(e2) : mul_mi(e2);
+  v[0] = cadd(a0, cadd(t1, t2));
+  v[1] = cadd(b1, d1);
+  v[4] = csub(b1, d1);
+  v[2] = cadd(b2, d2);
+  v[3] = csub(b2, d2);
+}
+
 template <int R_, bool INV, class C> __device__ __forceinline__ void dft_r(C* v) {
   if constexpr (R_ == 8) dft8<INV>(v);
+  else if constexpr (R_ == 5) dft5<INV>(v);
   else if constexpr (R_ == 4) dft4<INV>(v);
+  else if constexpr (R_ == 3) dft3<INV>(v);
   else dft2<INV>(v);
 }
 
@@ -155,10 +216,78 @@ __device__ __forceinline__ void fft_passes(C (&v)[NF][8], C* sm, int fstride, co
   }
 }
 
+// Mixed-radix passes p >= 1 through shared memory: the L/r butterflies of a
+// pass are spread over the line's L/8 threads (some threads idle when they do
+// not divide evenly); each thread reads all inputs of its butterflies before
+// the block synchronises and the outputs overwrite them in place.
+template <class C, int L, bool INV, int NF, int p, class SI>
+__device__ __forceinline__ void fft_mixed_passes(C* sm, int fstride, const C* __restrict__ tw, int t, const SI& si) {
+  using PL = MixedPlan<L>;
+  constexpr int r = PL::rad(p);
+  constexpr int Ns = PL::ns(p);
+  constexpr int NBF = L / r;                       // butterflies in this pass
+  constexpr int NB = (NBF + PL::TPL - 1) / PL::TPL;  // per thread (upper bound)
+  constexpr int STW = L / (Ns * r);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    C w[NB][r];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = t + b * PL::TPL;
+      if (j < NBF) {
+#pragma unroll
+        for (int q = 0; q < r; ++q) w[b][q] = sm[f * fstride + si(j + q * NBF)];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = t + b * PL::TPL;
+      if (j < NBF) {
+        const int k = j % Ns;
+#pragma unroll
+        for (int q = 1; q < r; ++q) {
+          const C tq = tw[q * k * STW];
+          w[b][q] = INV ? cmulc(w[b][q], tq) : cmul(w[b][q], tq);
+        }
+        dft_r<r, INV>(w[b]);
+        const int base = (j / Ns) * Ns * r + k;
+#pragma unroll
+        for (int q = 0; q < r; ++q) sm[f * fstride + si(base + q * Ns)] = w[b][q];
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (p + 1 < PL::P) fft_mixed_passes<C, L, INV, NF, p + 1, SI>(sm, fstride, tw, t, si);
+}
+
+// Mixed-radix line transform with natural entry and exit layouts (register e
+// of thread t holds position t + e L/8): the radix-8 first pass runs on the
+// registers as loaded, the later passes in shared memory, and the result is
+// read back in the same layout.
+template <class C, int L, bool INV, int NF, class SI>
+__device__ __forceinline__ void fft_mixed(C (&v)[NF][8], C* sm, int fstride, const C* __restrict__ tw, int t,
+                                          const SI& si) {
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    dft8<INV>(v[f]);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sm[f * fstride + si(8 * t + q)] = v[f][q];
+  }
+  __syncthreads();
+  fft_mixed_passes<C, L, INV, NF, 1, SI>(sm, fstride, tw, t, si);
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[f][e] = sm[f * fstride + si(t + e * MixedPlan<L>::TPL)];
+  __syncthreads();  // callers may reuse the buffer
+}
+
 template <class C, int L, bool INV, int NF, class SI>
 __device__ __forceinline__ void fft_line(C (&v)[NF][8], C* sm, int fstride, const C* __restrict__ tw, int t,
                                          const SI& si) {
-  fft_passes<C, L, INV, NF, 0, SI>(v, sm, fstride, tw, t, si);
+  if constexpr (IsPow2<L>::v) fft_passes<C, L, INV, NF, 0, SI>(v, sm, fstride, tw, t, si);
+  else fft_mixed<C, L, INV, NF, SI>(v, sm, fstride, tw, t, si);
 }
 
 // Shared-memory index maps.  Row tiles (lines contiguous in global memory):

@@ -191,10 +191,19 @@ __global__ void __launch_bounds__(MaxThreads<Op>::v, MinBlocks<Op>::v) xpass_ker
   xpass_body<Op>(a);
 }
 
+// Threads per block of a column pass: at most max(128 B / element, 32 / (L/8))
+// columns times L/8 threads.  The power-of-two lengths keep the 512 bound they
+// were tuned with; the mixed-radix lengths give the compiler the exact bound.
+template <class Op> struct ColMaxThreads {
+  static constexpr int TPL = Op::L / 8;
+  static constexpr int MC = (int)(128 / sizeof(C2<typename Op::R>));
+  static constexpr int v = IsPow2<Op::L>::v ? 512 : (MC > 32 / TPL ? MC : 32 / TPL) * TPL;
+};
+
 // ----------------------------------------------------------------------------
 // Column (y or z) pass kernel
 // ----------------------------------------------------------------------------
-template <class Op> __global__ void __launch_bounds__(512) colpass_kernel(KArgs<typename Op::R> a) {
+template <class Op> __global__ void __launch_bounds__(ColMaxThreads<Op>::v) colpass_kernel(KArgs<typename Op::R> a) {
   using R = typename Op::R;
   using C = C2<R>;
   constexpr int L = Op::L, NS = Op::NS;
@@ -248,7 +257,7 @@ template <class Op> __global__ void __launch_bounds__(512) colpass_kernel(KArgs<
 // memory from registers.
 // ----------------------------------------------------------------------------
 template <class Op>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(ColMaxThreads<Op>::v)
     colpass_tma_kernel(const __grid_constant__ CUtensorMap tm, KArgs<typename Op::R> a) {
   using R = typename Op::R;
   using C = C2<R>;
