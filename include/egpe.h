@@ -120,6 +120,9 @@ typedef struct {
   int max_iter_fp32;        /* MIXED: cap of the FP32 phase                         */
   int trace_cap;            /* entries available in trace (0: no trace)             */
   void* trace;              /* HOST array of egpe_trace_entry, or NULL              */
+  int batch;                /* n_inst > 1: advance all instances together (one launch
+                               per pass for up to 16 instances of one grid shape);
+                               0: one instance after the other                     */
 } egpe_solve_opts;
 
 /* One attempted step of the solver (accepted or rejected). */
@@ -233,7 +236,13 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
 /* Ground state by preconditioned NCG (Algorithm 1).  psi_inout[i] is the start
  * and receives the result for instance i (device pointers unless
  * opts->psi_on_host).  reports: host array of n_inst (may be NULL).
- * Returns the status of the first instance that did not converge, else OK. */
+ * Returns the status of the first instance that did not converge, else OK.
+ * With opts->batch and several instances, all instances advance together:
+ * every pass of an attempt is one launch per group of up to 16 instances of
+ * one grid shape; finished instances leave the launches at the next poll.
+ * Each instance's arithmetic, controller and result are those of a solve of
+ * that instance alone.  Reports then carry the shared wall time, graph
+ * replays and kernel launches of the whole batch. */
 egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts* opts,
                            egpe_report* reports);
 

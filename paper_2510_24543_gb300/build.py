@@ -19,13 +19,14 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libegpe.so")
-UNITS = ["capi.cu", "engine_f64.cu", "engine_f32.cu", "engine_mr_f64.cu", "engine_mr_f32.cu"]
+UNITS = ["capi.cu", "engine_f64.cu", "engine_f32.cu", "engine_mr_f64.cu", "engine_mr_f32.cu", "engine_mr5_f64.cu",
+         "engine_mr5_f32.cu", "engine_big_f64.cu", "engine_big_f32.cu"]
 # The FP32-field engine flushes denormals and uses the approximate (MUFU)
 # divide and square root: values below 1e-38 carry no weight in any sum of that
 # path, and its fields are accurate to ~1e-7 anyway.  The FP64 engine keeps
 # IEEE division and square root.
 _FP32_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
-UNIT_FLAGS = {"engine_f32.cu": _FP32_FLAGS, "engine_mr_f32.cu": _FP32_FLAGS}
+UNIT_FLAGS = {u: _FP32_FLAGS for u in UNITS if u.endswith("f32.cu")}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

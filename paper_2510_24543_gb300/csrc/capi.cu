@@ -149,6 +149,7 @@ void egpe_default_solve_opts(egpe_solve_opts* o) {
   o->max_iter_fp32 = 2000;
   o->trace_cap = 0;
   o->trace = nullptr;
+  o->batch = 1;
 }
 
 egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n_inst, egpe_precision prec,
@@ -353,6 +354,100 @@ egpe_status egpe_solver_read(egpe_handle* h, int inst, int engine, egpe_report* 
   return EGPE_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// All instances advance together (batch.cuh); same phases as the sequential
+// path per precision.
+egpe_status ncg_solve_batched(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts& o,
+                              egpe_report* reports) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int n = h->n_inst;
+  const cudaMemcpyKind kin = o.psi_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind kout = o.psi_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  egpe_trace_entry* trace = (egpe_trace_entry*)o.trace;
+  std::vector<egpe::SolveRun> runs, r32;
+  egpe_status s = EGPE_OK;
+  if (h->prec == EGPE_FP64) {
+    for (int i = 0; i < n && s == EGPE_OK; ++i) s = h->e64[i]->load_psi(psi_inout[i], kin);
+    if (s == EGPE_OK)
+      s = egpe::batch_solve<double>(h->e64, h->stream, o, 0, o.max_iter, o.tol_res, o.accept_rtol, runs, trace,
+                                    o.trace_cap, nullptr);
+    for (int i = 0; i < n && s == EGPE_OK; ++i) s = h->e64[i]->store_psi(psi_inout[i], kout);
+  } else if (h->prec == EGPE_FP32) {
+    for (int i = 0; i < n && s == EGPE_OK; ++i) s = h->e32[i]->load_psi(psi_inout[i], kin);
+    if (s == EGPE_OK)
+      s = egpe::batch_solve<float>(h->e32, h->stream, o, 1, o.max_iter, o.tol_res, o.accept_rtol_fp32, runs, trace,
+                                   o.trace_cap, nullptr);
+    for (int i = 0; i < n && s == EGPE_OK; ++i) s = h->e32[i]->store_psi(psi_inout[i], kout);
+  } else {  // MIXED: batched FP32 phase, then batched FP64 polish
+    for (int i = 0; i < n && s == EGPE_OK; ++i) {
+      s = h->e64[i]->load_psi(psi_inout[i], kin);
+      if (s == EGPE_OK) {
+        cast_d2f<<<256, 256, 0, h->stream>>>(2 * h->e64[i]->N, (const double2*)h->e64[i]->psi_slot0(),
+                                             h->e32[i]->psi_slot0());
+        if (cudaGetLastError() != cudaSuccess) s = EGPE_ERR_CUDA;
+      }
+    }
+    if (s == EGPE_OK)
+      s = egpe::batch_solve<float>(h->e32, h->stream, o, 1, o.max_iter_fp32, std::max(o.tol_res, o.tol_fp32_switch),
+                                   o.accept_rtol_fp32, r32, trace, o.trace_cap, nullptr);
+    for (int i = 0; i < n && s == EGPE_OK; ++i) {
+      cast_f2d<<<256, 256, 0, h->stream>>>(2 * h->e64[i]->N, h->e32[i]->current_psi(), h->e64[i]->psi_slot0());
+      if (cudaGetLastError() != cudaSuccess) s = EGPE_ERR_CUDA;
+      if (s == EGPE_OK) s = h->e64[i]->normalise_current();
+    }
+    const int t32 = (trace && !r32.empty()) ? r32[0].trace_len : 0;
+    const int tcap2 = trace ? std::max(0, o.trace_cap - t32) : 0;
+    if (s == EGPE_OK)
+      s = egpe::batch_solve<double>(h->e64, h->stream, o, 0, o.max_iter, o.tol_res, o.accept_rtol, runs,
+                                    tcap2 > 0 ? trace + t32 : nullptr, tcap2, nullptr);
+    for (int i = 0; i < n && s == EGPE_OK; ++i) s = h->e64[i]->store_psi(psi_inout[i], kout);
+  }
+  if (s != EGPE_OK) return s;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  egpe_status first_bad = EGPE_OK;
+  for (int i = 0; i < n; ++i) {
+    egpe::SolveRun run = runs[i];
+    egpe_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    if (h->prec == EGPE_MIXED) {
+      rep.iters_fp32 = r32[i].n;
+      run.n += r32[i].n;
+      run.attempts += r32[i].attempts;
+      run.restarts += r32[i].restarts;
+      run.armijo_total += r32[i].armijo_total;
+      run.launches += r32[i].launches;
+      run.ffts += r32[i].ffts;
+      run.kernels += r32[i].kernels;
+      run.trace_len += r32[i].trace_len;
+    }
+    if (h->prec == EGPE_FP32) rep.iters_fp32 = run.n;
+    rep.status = run.status;
+    rep.iters = run.n;
+    rep.attempts = run.attempts;
+    rep.restarts = run.restarts;
+    rep.armijo_steps = run.armijo_total;
+    rep.trace_len = i == 0 ? run.trace_len : 0;
+    rep.graph_launches = run.launches;
+    rep.E = run.E;
+    rep.mu[0] = run.mu[0];
+    rep.mu[1] = run.mu[1];
+    rep.res = run.res;
+    rep.seconds = secs;
+    rep.ffts = run.ffts;
+    rep.kernels = run.kernels;
+    if (reports) reports[i] = rep;
+    if (rep.status != EGPE_OK && first_bad == EGPE_OK) first_bad = (egpe_status)rep.status;
+  }
+  return first_bad;
+}
+
+}  // namespace
+
+extern "C" {
+
 egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts* opts,
                            egpe_report* reports) {
   if (!h || !psi_inout || !opts) return EGPE_ERR_INVALID_ARG;
@@ -363,6 +458,7 @@ egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_so
   }
   for (int i = 0; i < h->n_inst; ++i)
     if (!psi_inout[i]) return EGPE_ERR_INVALID_ARG;
+  if (h->n_inst > 1 && o.batch) return ncg_solve_batched(h, psi_inout, o, reports);
   egpe_status first_bad = EGPE_OK;
   egpe_trace_entry* trace = (egpe_trace_entry*)o.trace;
   for (int i = 0; i < h->n_inst; ++i) {

@@ -16,6 +16,20 @@
 namespace egpe {
 
 template <class R> struct KArgs;
+template <class R> struct KBatch;
+template <class R> class BatchRunner;
+
+// One recorded launch of a pipeline pass (batched replay, see batch.cuh): the
+// instance's kernel arguments and how to launch the pass for several
+// instances at once.
+template <class R> struct LaunchRec {
+  int arg = -1;                       // index of its KArgs in the recording's argument list
+  const CUtensorMap* tm = nullptr;    // column-pass tensor map (TMA launches)
+  const void* fn = nullptr;           // the batched kernel: one KBatch<R> parameter
+  int block = 0;
+  size_t smem = 0;
+  long long units = 0;                // blocks' worth of work per instance
+};
 
 void set_error(const char* what, cudaError_t e);
 void set_error_msg(const std::string& msg);
@@ -67,6 +81,8 @@ template <class R> class Engine {
   // or max_steps; the same begin / launch / poll / finish phases as the solver.
   egpe_status ite_begin(double dtau, double tol_dE, int max_steps, bool use_graph);
   egpe_status ite(double dtau, double tol_dE, int max_steps, int poll_every, bool use_graph, SolveRun& run);
+  // Records (instead of launching) the kernels of one solver attempt.
+  egpe_status record_attempt(int mode, std::vector<LaunchRec<R>>& recs, std::vector<KArgs<R>>& args);
   C* current_psi();  // valid after solve (device)
   C* psi_slot0();    // psi buffer 0 (start of a solve)
 
@@ -86,19 +102,38 @@ template <class R> class Engine {
                           double accept_rtol);
   egpe_status read_state(DevState& hs);
   template <class Op> egpe_status launch_x(KArgs<R> a);
-  egpe_status launch_point(void (*kern)(KArgs<R>), const char* name, double bytes, const KArgs<R>& a);
+  egpe_status launch_point(void (*kern)(KArgs<R>), void (*kern_b)(KBatch<R>), const char* name, double bytes,
+                           const KArgs<R>& a, long long units);
+  egpe_status record(const KArgs<R>& a, const CUtensorMap* tm, const void* fn, int block, size_t smem,
+                     long long units);
   template <class Op> egpe_status launch_col(KArgs<R> a, const CUtensorMap* tm);
   template <template <class, int> class OpT> egpe_status dispatch_x(int L, const KArgs<R>& a);
   template <template <class, int> class OpT> egpe_status dispatch_col(int L, const KArgs<R>& a, const CUtensorMap* tm);
   egpe_status plain_x(int inverse, const KArgs<R>& a);
   egpe_status plain_col(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm);
-  // Lengths 48, 80, 96 (mixed radix): defined in engine_mr.cuh, instantiated
-  // in their own translation units to keep compile times apart.
+  // Launches for a list of line lengths (engine_impl.cuh).  The lengths 48 and
+  // 96 (suffix mr), 80 (mr5) and 128, 256 (big) are compiled in translation
+  // units of their own (engine_ext.cuh) to spread the compile time.
+  template <template <class, int> class OpT, int... Ls> egpe_status dispatch_x_in(int L, const KArgs<R>& a);
+  template <template <class, int> class OpT, int... Ls>
+  egpe_status dispatch_col_in(int L, const KArgs<R>& a, const CUtensorMap* tm);
+  template <int... Ls> egpe_status plain_x_in(int inverse, const KArgs<R>& a);
+  template <int... Ls> egpe_status plain_col_in(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm);
   template <template <class, int> class OpT> egpe_status dispatch_x_mr(int L, const KArgs<R>& a);
   template <template <class, int> class OpT>
   egpe_status dispatch_col_mr(int L, const KArgs<R>& a, const CUtensorMap* tm);
   egpe_status plain_x_mr(int inverse, const KArgs<R>& a);
   egpe_status plain_col_mr(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm);
+  template <template <class, int> class OpT> egpe_status dispatch_x_mr5(int L, const KArgs<R>& a);
+  template <template <class, int> class OpT>
+  egpe_status dispatch_col_mr5(int L, const KArgs<R>& a, const CUtensorMap* tm);
+  egpe_status plain_x_mr5(int inverse, const KArgs<R>& a);
+  egpe_status plain_col_mr5(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm);
+  template <template <class, int> class OpT> egpe_status dispatch_x_big(int L, const KArgs<R>& a);
+  template <template <class, int> class OpT>
+  egpe_status dispatch_col_big(int L, const KArgs<R>& a, const CUtensorMap* tm);
+  egpe_status plain_x_big(int inverse, const KArgs<R>& a);
+  egpe_status plain_col_big(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm);
   const CUtensorMap* tmy() const { return have_maps_ ? &tmW_y_ : nullptr; }
   const CUtensorMap* tmz() const { return have_maps_ ? &tmW_z_ : nullptr; }
   int occupancy(const void* fn, int block, size_t smem);
@@ -147,6 +182,16 @@ template <class R> class Engine {
   cudaGraphExec_t graph_ite_ = nullptr;
   int ite_per_step_ = 0;
   bool run_ite_ = false;
+  std::vector<LaunchRec<R>>* rec_ = nullptr;  // recording mode when set
+  std::vector<KArgs<R>>* rec_args_ = nullptr;
+  friend class BatchRunner<R>;
 };
+
+// Solves all instances together with batched launches (batch.cuh).  Engines
+// of one precision on stream s; psi starts in each engine's slot 0.
+template <class R>
+egpe_status batch_solve(const std::vector<Engine<R>*>& eng, cudaStream_t s, const egpe_solve_opts& o, int fp32_phase,
+                        int max_iter, double tol_res, double accept_rtol, std::vector<SolveRun>& runs,
+                        egpe_trace_entry* trace_out, int trace_cap, int* graph_builds);
 
 }  // namespace egpe

@@ -1,6 +1,9 @@
 // Engine<double>: the FP64 path.
-#include "engine_impl.cuh"
+#include "batch.cuh"
 template class egpe::Engine<double>;
+template egpe_status egpe::batch_solve<double>(const std::vector<egpe::Engine<double>*>&, cudaStream_t,
+                                             const egpe_solve_opts&, int, int, double, double,
+                                             std::vector<egpe::SolveRun>&, egpe_trace_entry*, int, int*);
 
 // ---------------------------------------------------------------------------
 // egpe_energy_grad_noalloc: the FP64 energy/gradient evaluation without any

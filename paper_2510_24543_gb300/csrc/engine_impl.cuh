@@ -344,10 +344,45 @@ egpe_status Engine<R>::profile_attempt(const C* psi, int precond, int reps, std:
   return EGPE_OK;
 }
 
+// The batched kernel of a row pass (one pass for several instances).
+template <class Op> static const void* xb_fn() {
+  if constexpr (MinBlocks<Op>::v > 1) return (const void*)xpass_kernel_bmb<Op>;
+  else return (const void*)xpass_kernel_b<Op>;
+}
+
 template <class R>
-egpe_status Engine<R>::launch_point(void (*kern)(KArgs<R>), const char* name, double bytes, const KArgs<R>& a) {
+egpe_status Engine<R>::record(const KArgs<R>& a, const CUtensorMap* tm, const void* fn, int block, size_t smem,
+                              long long units) {
+  LaunchRec<R> r;
+  r.arg = (int)rec_args_->size();
+  rec_args_->push_back(a);
+  r.tm = tm;
+  r.fn = fn;
+  r.block = block;
+  r.smem = smem;
+  r.units = units;
+  rec_->push_back(r);
+  return fn ? EGPE_OK : EGPE_ERR_UNSUPPORTED;
+}
+
+template <class R>
+egpe_status Engine<R>::record_attempt(int mode, std::vector<LaunchRec<R>>& recs, std::vector<KArgs<R>>& args) {
+  recs.clear();
+  args.clear();
+  rec_ = &recs;
+  rec_args_ = &args;
+  const egpe_status s = enq_attempt(mode);
+  rec_ = nullptr;
+  rec_args_ = nullptr;
+  return s;
+}
+
+template <class R>
+egpe_status Engine<R>::launch_point(void (*kern)(KArgs<R>), void (*kern_b)(KBatch<R>), const char* name,
+                                    double bytes, const KArgs<R>& a, long long units) {
   const int occ = occupancy((const void*)kern, 256, 0);
-  const int grid = (int)std::min<size_t>((N + 511) / 512, (size_t)std::min(occ * nsm_, 16384));
+  const int grid = (int)std::min<long long>(units, (long long)std::min(occ * nsm_, 16384));
+  if (rec_) return record(a, nullptr, (const void*)kern_b, 256, 0, units);
   if (timing_) t_begin(name, 0, bytes);
   kern<<<grid, 256, 0, stream>>>(a);
   if (timing_) t_end();
@@ -368,6 +403,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
                       (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const int rows = ny * nz;
   const int groups = (rows + mx - 1) / mx;
+  if (rec_) return record(a, nullptr, xb_fn<Op>(), block, smem, groups);
   void (*kern)(KArgs<R>);
   if constexpr (MinBlocks<Op>::v > 1) kern = xpass_kernel_mb<Op>;
   else kern = xpass_kernel<Op>;
@@ -391,6 +427,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   if (tm && use_tma_) {
     const size_t smem = 2 * (size_t)M * L * sizeof(C) + L * sizeof(C) + 2 * sizeof(uint64_t) +
                         (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+    if (rec_) return record(a, tm, (const void*)colpass_tma_kernel_b<Op>, block, smem, tiles);
     const int occ = occupancy((const void*)colpass_tma_kernel<Op>, block, smem);
     const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
     if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
@@ -398,6 +435,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
     if (timing_) t_end();
   } else {
     const size_t smem = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+    if (rec_) return record(a, nullptr, (const void*)colpass_kernel_b<Op>, block, smem, tiles);
     const int occ = occupancy((const void*)colpass_kernel<Op>, block, smem);
     const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
     if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
@@ -409,55 +447,73 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   return EGPE_OK;
 }
 
+template <class R> template <template <class, int> class OpT, int... Ls>
+egpe_status Engine<R>::dispatch_x_in(int L, const KArgs<R>& a) {
+  egpe_status s = EGPE_ERR_UNSUPPORTED;
+  (void)((L == Ls ? (s = launch_x<OpT<R, Ls>>(a), true) : false) || ...);
+  return s;
+}
+
+template <class R> template <template <class, int> class OpT, int... Ls>
+egpe_status Engine<R>::dispatch_col_in(int L, const KArgs<R>& a, const CUtensorMap* tm) {
+  egpe_status s = EGPE_ERR_UNSUPPORTED;
+  (void)((L == Ls ? (s = launch_col<OpT<R, Ls>>(a, tm), true) : false) || ...);
+  return s;
+}
+
+template <class R> template <int... Ls> egpe_status Engine<R>::plain_x_in(int inverse, const KArgs<R>& a) {
+  egpe_status s = EGPE_ERR_UNSUPPORTED;
+  (void)((nx == Ls ? (s = inverse ? launch_x<XPlain<R, Ls, true>>(a) : launch_x<XPlain<R, Ls, false>>(a), true)
+                   : false) ||
+         ...);
+  return s;
+}
+
+template <class R> template <int... Ls>
+egpe_status Engine<R>::plain_col_in(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm) {
+  const int L = axis == 1 ? ny : nz;
+  egpe_status s = EGPE_ERR_UNSUPPORTED;
+  (void)((L == Ls ? (s = axis == 1 ? (inverse ? launch_col<ColPlain<R, Ls, 1, true>>(a, tm)
+                                              : launch_col<ColPlain<R, Ls, 1, false>>(a, tm))
+                                   : (inverse ? launch_col<ColPlain<R, Ls, 2, true>>(a, tm)
+                                              : launch_col<ColPlain<R, Ls, 2, false>>(a, tm)),
+                     true)
+                  : false) ||
+         ...);
+  return s;
+}
+
 template <class R> template <template <class, int> class OpT>
 egpe_status Engine<R>::dispatch_x(int L, const KArgs<R>& a) {
-  switch (L) {
-    case 16: return launch_x<OpT<R, 16>>(a);
-    case 32: return launch_x<OpT<R, 32>>(a);
-    case 64: return launch_x<OpT<R, 64>>(a);
-    case 128: return launch_x<OpT<R, 128>>(a);
-    case 256: return launch_x<OpT<R, 256>>(a);
-  }
-  return dispatch_x_mr<OpT>(L, a);
+  if (L == 128 || L == 256) return dispatch_x_big<OpT>(L, a);
+  if (L == 80) return dispatch_x_mr5<OpT>(L, a);
+  if (L == 48 || L == 96) return dispatch_x_mr<OpT>(L, a);
+  return dispatch_x_in<OpT, 16, 32, 64>(L, a);
 }
 
 template <class R> template <template <class, int> class OpT>
 egpe_status Engine<R>::dispatch_col(int L, const KArgs<R>& a, const CUtensorMap* tm) {
-  switch (L) {
-    case 16: return launch_col<OpT<R, 16>>(a, tm);
-    case 32: return launch_col<OpT<R, 32>>(a, tm);
-    case 64: return launch_col<OpT<R, 64>>(a, tm);
-    case 128: return launch_col<OpT<R, 128>>(a, tm);
-    case 256: return launch_col<OpT<R, 256>>(a, tm);
-  }
-  return dispatch_col_mr<OpT>(L, a, tm);
+  if (L == 128 || L == 256) return dispatch_col_big<OpT>(L, a, tm);
+  if (L == 80) return dispatch_col_mr5<OpT>(L, a, tm);
+  if (L == 48 || L == 96) return dispatch_col_mr<OpT>(L, a, tm);
+  return dispatch_col_in<OpT, 16, 32, 64>(L, a, tm);
 }
 
 template <class R> egpe_status Engine<R>::plain_x(int inverse, const KArgs<R>& a) {
-#define EGPE_PX(LL) \
-  case LL: return inverse ? launch_x<XPlain<R, LL, true>>(a) : launch_x<XPlain<R, LL, false>>(a);
-  switch (nx) {
-    EGPE_PX(16) EGPE_PX(32) EGPE_PX(64) EGPE_PX(128) EGPE_PX(256)
-  }
-#undef EGPE_PX
-  return plain_x_mr(inverse, a);
+  if (nx == 128 || nx == 256) return plain_x_big(inverse, a);
+  if (nx == 80) return plain_x_mr5(inverse, a);
+  if (nx == 48 || nx == 96) return plain_x_mr(inverse, a);
+  return plain_x_in<16, 32, 64>(inverse, a);
 }
 
 template <class R>
 egpe_status Engine<R>::plain_col(int axis, int inverse, const KArgs<R>& a, const CUtensorMap* tm) {
   const int L = axis == 1 ? ny : nz;
-#define EGPE_PC(LL)                                                                             \
-  case LL:                                                                                      \
-    if (axis == 1)                                                                              \
-      return inverse ? launch_col<ColPlain<R, LL, 1, true>>(a, tm) : launch_col<ColPlain<R, LL, 1, false>>(a, tm); \
-    return inverse ? launch_col<ColPlain<R, LL, 2, true>>(a, tm) : launch_col<ColPlain<R, LL, 2, false>>(a, tm);
-  switch (L) {
-    EGPE_PC(16) EGPE_PC(32) EGPE_PC(64) EGPE_PC(128) EGPE_PC(256)
-  }
-#undef EGPE_PC
-  return plain_col_mr(axis, inverse, a, tm);
+  if (L == 128 || L == 256) return plain_col_big(axis, inverse, a, tm);
+  if (L == 80) return plain_col_mr5(axis, inverse, a, tm);
+  if (L == 48 || L == 96) return plain_col_mr(axis, inverse, a, tm);
+  return plain_col_in<16, 32, 64>(axis, inverse, a, tm);
 }
-
 
 // Energy / gradient pipeline: 6 complex 3D transforms.
 template <class R> egpe_status Engine<R>::enq_eg(int trial, int gate, int ctrl) {
@@ -479,7 +535,8 @@ template <class R> egpe_status Engine<R>::enq_eg(int trial, int gate, int ctrl) 
   a.ctrl = 0;
   EGPE_TRY(dispatch_x<XInvW3>(nx, a));
   a.ctrl = ctrl;
-  return launch_point(eg_point_kernel<R>, "energy+LHY pointwise", 9.0 * N * sizeof(C), a);
+  return launch_point(eg_point_kernel<R>, eg_point_kernel_b<R>, "energy+LHY pointwise", 9.0 * N * sizeof(C), a,
+                      (long long)((N + 511) / 512));
 }
 
 // Preconditioner pipeline: 4 transforms for the kinetic modes, none otherwise.
@@ -503,14 +560,8 @@ template <class R> egpe_status Engine<R>::enq_pc(int mode, int gate, int ctrl, i
     return dispatch_x<XInvPC>(nx, a);
   }
   a.ctrl = ctrl;
-  const int occ = occupancy((const void*)pc_point_kernel<R>, 256, 0);
-  const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)std::min(occ * nsm_, 16384));
-  if (timing_) t_begin("pointwise precond sums", 0, (a.diag ? 13.0 : 12.0) * N * sizeof(C));
-  pc_point_kernel<R><<<grid, 256, 0, stream>>>(a);
-  if (timing_) t_end();
-  ++kernels_;
-  EGPE_CUDA(cudaGetLastError());
-  return EGPE_OK;
+  return launch_point(pc_point_kernel<R>, pc_point_kernel_b<R>, "pointwise precond sums",
+                      (a.diag ? 13.0 : 12.0) * N * sizeof(C), a, (long long)((N + 255) / 256));
 }
 
 // Line-search pipeline: forward transforms of p_1, p_2 and one packed pair.
@@ -535,7 +586,8 @@ template <class R> egpe_status Engine<R>::enq_lc(int gate, int ctrl, int pgiven)
   a.ctrl = 0;
   EGPE_TRY(dispatch_x<XInvW1F2>(nx, a));
   a.ctrl = ctrl;
-  return launch_point(lc_point_kernel<R>, "line sums+LHY pointwise", 9.0 * N * sizeof(C), a);
+  return launch_point(lc_point_kernel<R>, lc_point_kernel_b<R>, "line sums+LHY pointwise", 9.0 * N * sizeof(C), a,
+                      (long long)((N + 511) / 512));
 }
 
 template <class R> egpe_status Engine<R>::enq_attempt(int mode) {
@@ -792,12 +844,8 @@ template <class R> egpe_status Engine<R>::enq_ite_step(int gate) {
   {
     KArgs<R> a = *base_;
     a.gate = gate;
-    const int grid = (int)std::min<size_t>((N + 255) / 256, (size_t)nsm_ * 8);
-    if (timing_) t_begin("ITE renormalise", 0, 4.0 * N * sizeof(C));
-    ite_scale_kernel<R><<<grid, 256, 0, stream>>>(a);
-    if (timing_) t_end();
-    ++kernels_;
-    EGPE_CUDA(cudaGetLastError());
+    EGPE_TRY(launch_point(ite_scale_kernel<R>, ite_scale_kernel_b<R>, "ITE renormalise", 4.0 * N * sizeof(C), a,
+                          (long long)((N + 255) / 256)));
   }
   return enq_eg(0, gate, 2);
 }

@@ -1,3 +1,4 @@
-// Mixed-radix (48, 80, 96) launches of Engine<double>.
-#include "engine_mr.cuh"
-EGPE_MR_INSTANTIATE(double)
+// Mixed-radix lengths 48 and 96 of Engine<double>.
+#include "engine_ext.cuh"
+EGPE_EXT_DEFINE(mr, 48, 96)
+EGPE_EXT_INSTANTIATE(double, mr)

@@ -70,6 +70,16 @@ template <class R> __device__ __forceinline__ bool gate_open(const KArgs<R>& a) 
   return a.gate == GATE_NEW_ITER ? (ph == PH_NEW_ITER) : (ph != PH_DONE);
 }
 
+// Batched launches: one launch runs the same pass for up to KB_MAX instances
+// of one grid shape, blockIdx.y selecting the instance.  The descriptors (and
+// the column passes' tensor maps) travel in the kernel's parameter block.
+constexpr int KB_MAX = 16;
+template <class R> struct KBatch {
+  CUtensorMap tm[KB_MAX];
+  KArgs<R> k[KB_MAX];
+};
+static_assert(sizeof(KBatch<double>) <= 32764, "batched kernel parameters exceed the 32 KB limit");
+
 // Points whose global loads are issued together before any store of the chunk
 // (the buffers may alias as far as the compiler knows, so loads and stores are
 // grouped explicitly to keep several loads in flight per thread).
@@ -190,6 +200,15 @@ template <class Op>
 __global__ void __launch_bounds__(MaxThreads<Op>::v, MinBlocks<Op>::v) xpass_kernel_mb(KArgs<typename Op::R> a) {
   xpass_body<Op>(a);
 }
+template <class Op>
+__global__ void __launch_bounds__(MaxThreads<Op>::v) xpass_kernel_b(const __grid_constant__ KBatch<typename Op::R> kb) {
+  xpass_body<Op>(kb.k[blockIdx.y]);
+}
+template <class Op>
+__global__ void __launch_bounds__(MaxThreads<Op>::v, MinBlocks<Op>::v)
+    xpass_kernel_bmb(const __grid_constant__ KBatch<typename Op::R> kb) {
+  xpass_body<Op>(kb.k[blockIdx.y]);
+}
 
 // Threads per block of a column pass: at most max(128 B / element, 32 / (L/8))
 // columns times L/8 threads.  The power-of-two lengths keep the 512 bound they
@@ -203,7 +222,7 @@ template <class Op> struct ColMaxThreads {
 // ----------------------------------------------------------------------------
 // Column (y or z) pass kernel
 // ----------------------------------------------------------------------------
-template <class Op> __global__ void __launch_bounds__(ColMaxThreads<Op>::v) colpass_kernel(KArgs<typename Op::R> a) {
+template <class Op> __device__ __forceinline__ void colpass_body(const KArgs<typename Op::R>& a) {
   using R = typename Op::R;
   using C = C2<R>;
   constexpr int L = Op::L, NS = Op::NS;
@@ -247,6 +266,13 @@ template <class Op> __global__ void __launch_bounds__(ColMaxThreads<Op>::v) colp
     }
   }
 }
+template <class Op> __global__ void __launch_bounds__(ColMaxThreads<Op>::v) colpass_kernel(KArgs<typename Op::R> a) {
+  colpass_body<Op>(a);
+}
+template <class Op>
+__global__ void __launch_bounds__(ColMaxThreads<Op>::v) colpass_kernel_b(const __grid_constant__ KBatch<typename Op::R> kb) {
+  colpass_body<Op>(kb.k[blockIdx.y]);
+}
 
 // ----------------------------------------------------------------------------
 // Column (y or z) pass fed by TMA.  The tensor map describes the workspace as
@@ -257,16 +283,15 @@ template <class Op> __global__ void __launch_bounds__(ColMaxThreads<Op>::v) colp
 // memory from registers.
 // ----------------------------------------------------------------------------
 template <class Op>
-__global__ void __launch_bounds__(ColMaxThreads<Op>::v)
-    colpass_tma_kernel(const __grid_constant__ CUtensorMap tm, KArgs<typename Op::R> a) {
+__device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
   using R = typename Op::R;
   using C = C2<R>;
   constexpr int L = Op::L, NS = Op::NS;
   constexpr int NSR = NS > 0 ? NS : 1;
   if (!gate_open(a)) return;
-  extern __shared__ __align__(128) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw_tma[];
   const int tileC = a.M * L;
-  C* tiles = reinterpret_cast<C*>(smraw);  // two tiles
+  C* tiles = reinterpret_cast<C*>(smraw_tma);  // two tiles
   C* tw = tiles + 2 * tileC;
   uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
   RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(bar + 2);
@@ -299,7 +324,7 @@ __global__ void __launch_bounds__(ColMaxThreads<Op>::v)
     const int c2 = (Op::AXIS == 1) ? f * a.nz + o : f * a.nz;
     fence_proxy_async();
     mbar_expect_tx(&bar[b], bytes);
-    tma_load_3d(tiles + b * tileC, &tm, c0, c1, c2, &bar[b]);
+    tma_load_3d(tiles + b * tileC, tm, c0, c1, c2, &bar[b]);
   };
   if (tid == 0 && (int)blockIdx.x < tiles_n) issue(blockIdx.x, 0);
   bool timed_out = false, next_pending = false;
@@ -344,6 +369,16 @@ __global__ void __launch_bounds__(ColMaxThreads<Op>::v)
       if (threadIdx.x == 0) Op::finish(a, u);
     }
   }
+}
+template <class Op>
+__global__ void __launch_bounds__(ColMaxThreads<Op>::v)
+    colpass_tma_kernel(const __grid_constant__ CUtensorMap tm, KArgs<typename Op::R> a) {
+  colpass_tma_body<Op>(&tm, a);
+}
+template <class Op>
+__global__ void __launch_bounds__(ColMaxThreads<Op>::v)
+    colpass_tma_kernel_b(const __grid_constant__ KBatch<typename Op::R> kb) {
+  colpass_tma_body<Op>(&kb.tm[blockIdx.y], kb.k[blockIdx.y]);
 }
 
 struct NoUni {};
@@ -864,7 +899,7 @@ template <class R_, int L_> struct XInvPC {
 
 // Pointwise preconditioner (modes none and diagonal): one pass, no transform.
 template <class R>
-__global__ void __launch_bounds__(256) pc_point_kernel(KArgs<R> a) {
+__device__ __forceinline__ void pc_point_body(const KArgs<R>& a) {
   using C = C2<R>;
   if (!gate_open(a)) return;
   __shared__ RedSmem<PC_NS> red;
@@ -901,6 +936,11 @@ __global__ void __launch_bounds__(256) pc_point_kernel(KArgs<R> a) {
     if (threadIdx.x == 0 && a.ctrl) ctrl_after_pc(a.st);
   }
 }
+template <class R> __global__ void __launch_bounds__(256) pc_point_kernel(KArgs<R> a) { pc_point_body(a); }
+template <class R> __global__ void __launch_bounds__(256) pc_point_kernel_b(const __grid_constant__ KBatch<R> kb) {
+  pc_point_body(kb.k[blockIdx.y]);
+}
+
 
 // ----------------------------------------------------------------------------
 // Line-search pipeline (Sec. V): p = -z + beta p_prev - c psi (projected
@@ -1262,7 +1302,7 @@ template <class R_, int L_> struct XInvKin {
 };
 
 // psi_i <- psi_i / ||psi_i|| with the norms the last half step reduced.
-template <class R> __global__ void __launch_bounds__(256) ite_scale_kernel(KArgs<R> a) {
+template <class R> __device__ __forceinline__ void ite_scale_body(const KArgs<R>& a) {
   if (!gate_open(a)) return;
   const int cur = __ldcg(&a.st->cur);
   const double dV = __ldcg(&a.st->dV);
@@ -1275,6 +1315,11 @@ template <class R> __global__ void __launch_bounds__(256) ite_scale_kernel(KArgs
     ps[N + idx] = cscale(ps[N + idx], s2);
   }
 }
+template <class R> __global__ void __launch_bounds__(256) ite_scale_kernel(KArgs<R> a) { ite_scale_body(a); }
+template <class R> __global__ void __launch_bounds__(256) ite_scale_kernel_b(const __grid_constant__ KBatch<R> kb) {
+  ite_scale_body(kb.k[blockIdx.y]);
+}
+
 
 // ----------------------------------------------------------------------------
 // Split epilogues: the last x pass only inverts the workspace in place, and a
@@ -1326,7 +1371,7 @@ template <class R> __device__ __forceinline__ R trap_at(const KArgs<R>& a, size_
 
 // Energy/gradient epilogue, pointwise: W fields 0, 1 hold T psi_1, T psi_2 and
 // field 2 holds Phi_1 + i Phi_2 (already inverse transformed).
-template <class R> __global__ void __launch_bounds__(256) eg_point_kernel(KArgs<R> a) {
+template <class R> __device__ __forceinline__ void eg_point_body(const KArgs<R>& a) {
   using C = C2<R>;
   constexpr int NP = 2;
   if (!gate_open(a)) return;
@@ -1395,9 +1440,14 @@ template <class R> __global__ void __launch_bounds__(256) eg_point_kernel(KArgs<
     if (threadIdx.x == 0) eg_ctrl(a);
   }
 }
+template <class R> __global__ void __launch_bounds__(256) eg_point_kernel(KArgs<R> a) { eg_point_body(a); }
+template <class R> __global__ void __launch_bounds__(256) eg_point_kernel_b(const __grid_constant__ KBatch<R> kb) {
+  eg_point_body(kb.k[blockIdx.y]);
+}
+
 
 // Line-search epilogue, pointwise: W field 2 holds Phi[rho] (inverse transformed).
-template <class R> __global__ void __launch_bounds__(256) lc_point_kernel(KArgs<R> a) {
+template <class R> __device__ __forceinline__ void lc_point_body(const KArgs<R>& a) {
   using C = C2<R>;
   constexpr int NP = 2;
   if (!gate_open(a)) return;
@@ -1462,6 +1512,11 @@ template <class R> __global__ void __launch_bounds__(256) lc_point_kernel(KArgs<
     }
   }
 }
+template <class R> __global__ void __launch_bounds__(256) lc_point_kernel(KArgs<R> a) { lc_point_body(a); }
+template <class R> __global__ void __launch_bounds__(256) lc_point_kernel_b(const __grid_constant__ KBatch<R> kb) {
+  lc_point_body(kb.k[blockIdx.y]);
+}
+
 
 // ----------------------------------------------------------------------------
 // Small pointwise kernels: retraction sums and apply, residual norm, casts.
