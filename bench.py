@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-tts", action="store_true", help="skip time-to-ground-state")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-ite", action="store_true", help="skip the NCG-vs-ITE comparison on the 64^3 workload")
+    ap.add_argument("--no-scan", action="store_true", help="skip the 64-instance parameter scan")
     ap.add_argument("--fp32-switch", type=float, default=1e-4)
     return ap.parse_args()
 
@@ -324,6 +325,12 @@ def run_ours(args):
             ite = ncg_vs_ite(E)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             ite = {"error": str(ex)[:300]}
+    scan = None
+    if not args.no_scan:
+        try:
+            scan = scan_benchmark(E)
+        except Exception as ex:  # reported, not fatal for the iteration numbers
+            scan = {"error": str(ex)[:300]}
     clk = clocks.stop()
     E.egpe_destroy(h)
 
@@ -342,7 +349,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2: ~25 complex64 fields of 16.8 MB resident per instance",
                            "step": "one NCG attempt (precondition + line coefficients + trial E/grad + controller)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launch32,
-                "clocks": clk, "fp64": fp64, "time_to_ground_state": tts, "ncg_vs_ite": ite}
+                "clocks": clk, "fp64": fp64, "time_to_ground_state": tts, "ncg_vs_ite": ite,
+                "scan": scan}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -435,6 +443,60 @@ def ncg_vs_ite(E):
         return out
     finally:
         E.egpe_destroy(h)
+
+
+def scan_benchmark(E, tol_res=1e-6, fp32_switch=1e-4):
+    """The 64-instance parameter scan (16 each of 48^3, 64^3, 80^3, 96^3; Latin
+    hypercube over g12 and g_dd; P_Delta o P_V preconditioner): wall time to the
+    ground states of all instances, mixed precision batched (FP32 phase to
+    ||r|| < fp32_switch, FP64 polish) against plain FP64 one instance after the
+    other, both stopped at ||r|| < tol_res.  Accuracy: each energy against the
+    lower of the two methods' energies for that instance (the two can settle in
+    different local minima of this multistable problem)."""
+    import torch
+
+    from paper_2510_24543_gb300 import inputs as I
+
+    ws = I.scan_workloads()
+    grids = [E.make_grid(w.n, w.L) for w in ws]
+    prms = [E.params_from_workload(w) for w in ws]
+    starts = [torch.from_numpy(I.gaussian_start(w)) for w in ws]
+
+    def run(prec, batch, tol):
+        h = E.egpe_create(grids, prms, prec)
+        try:
+            o = E.egpe_default_solve_opts()
+            o.precond = E.PRECOND[ws[0].precond]
+            o.tol_res = tol
+            o.tol_fp32_switch = fp32_switch
+            o.max_iter = 6000
+            o.max_iter_fp32 = 6000
+            o.batch = batch
+            xs = [s.to("cuda") for s in starts]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, reps, _ = E.egpe_ncg_solve(h, xs, o, len(ws))
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, reps
+        finally:
+            E.egpe_destroy(h)
+
+    run(E.EGPE_MIXED, 1, 1e-3)  # warm-up: code paged in, occupancy queries cached
+    out = {"instances": len(ws), "grids": "16 each of 48^3, 64^3, 80^3, 96^3", "precond": ws[0].precond,
+           "tol_res": tol_res, "fp32_switch": fp32_switch, "accuracy_target": 1e-8}
+    runs = {}
+    for name, prec, batch in (("fp64_one_by_one", E.EGPE_FP64, 0), ("mixed_batched", E.EGPE_MIXED, 1)):
+        runs[name] = run(prec, batch, tol_res)
+    Ebest = [min(runs[k][1][i]["E"] for k in runs) for i in range(len(ws))]
+    for name, (secs, reps) in runs.items():
+        d = [(r["E"] - b) / abs(b) for r, b in zip(reps, Ebest)]
+        iters = sum(r["iters"] for r in reps)
+        out[name] = {"seconds": round(secs, 4), "iters_total": iters, "iters_fp32_total": sum(r["iters_fp32"] for r in reps),
+                     "instances_within_1e-8_of_best": sum(x <= 1e-8 for x in d),
+                     "worse_than_best": {str(i): x for i, x in enumerate(d) if x > 1e-8},
+                     "all_converged": all(r["status"] == 0 for r in reps)}
+    out["speedup_mixed_batched_vs_fp64_one_by_one"] = round(runs["fp64_one_by_one"][0] / runs["mixed_batched"][0], 3)
+    return out
 
 
 def cpu_baseline(w):

@@ -123,6 +123,9 @@ typedef struct {
   int batch;                /* n_inst > 1: advance all instances together (one launch
                                per pass for up to 16 instances of one grid shape);
                                0: one instance after the other                     */
+  int stall_iters_fp32;     /* FP32 fields (FP32 handles, MIXED's FP32 phase): stop
+                               when the best ||r|| has not dropped by 10% within this
+                               many iterations (its round-off floor); 0: off       */
 } egpe_solve_opts;
 
 /* One attempted step of the solver (accepted or rejected). */
@@ -298,8 +301,9 @@ egpe_status egpe_solver_step(egpe_handle* h, int inst, int engine, int attempts)
 egpe_status egpe_solver_read(egpe_handle* h, int inst, int engine, egpe_report* report, void* psi_out);
 
 /* Defaults: kinetic preconditioner, HS+, K_r = 20, tol_res 1e-8, c1 1e-4,
- * 30 halvings, theta_max = pi/2, accept_rtol 1e-13 (FP64) / 2e-6 (FP32),
- * pv_floor 1e-2, graph replay with polls every 8 attempts. */
+ * 30 halvings, theta_max = pi/2, accept_rtol 1e-13 (FP64) / 1e-6 (FP32),
+ * pv_floor 1e-2, graph replay with polls every 8 attempts, MIXED switch at
+ * ||r|| < 1e-4, no FP32 stall limit, batched instances. */
 void egpe_default_solve_opts(egpe_solve_opts* opts);
 
 /* Human-readable status; never NULL. */

@@ -165,8 +165,10 @@ template <class R> class BatchRunner {
             L.kb->k[c] = args[c][rc.arg];
             if (rc.tm) L.kb->tm[c] = *rc.tm;
           }
+          // one full wave over all instances of the chunk: a rounded-up share
+          // would spill a few blocks into a second wave
           const int occ = e0.occupancy(r0.fn, r0.block, r0.smem);
-          const long long fill = ((long long)occ * e0.nsm_ + nc - 1) / nc;
+          const long long fill = ((long long)occ * e0.nsm_) / nc;
           const long long gx = std::max<long long>(1, std::min<long long>(r0.units, std::min<long long>(fill, 16384)));
           L.grid = dim3((unsigned)gx, (unsigned)nc, 1);
           launches.push_back(std::move(L));

@@ -150,6 +150,7 @@ void egpe_default_solve_opts(egpe_solve_opts* o) {
   o->trace_cap = 0;
   o->trace = nullptr;
   o->batch = 1;
+  o->stall_iters_fp32 = 0;
 }
 
 egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n_inst, egpe_precision prec,
@@ -295,7 +296,7 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
 static bool opts_ok(const egpe_solve_opts& o) {
   return !(o.precond < 0 || o.precond > 3 || o.beta_rule < 0 || o.beta_rule > 1 || o.max_iter < 0 || o.armijo_max < 0 ||
            o.armijo_max > 60 || !(o.tol_res >= 0.0) || !(o.theta_max > 0.0) || !(o.pv_floor > 0.0) ||
-           o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace));
+           o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace) || o.stall_iters_fp32 < 0);
 }
 
 egpe_status egpe_solver_start(egpe_handle* h, int inst, int engine, const void* psi, const egpe_solve_opts* opts) {

@@ -57,7 +57,7 @@ enum Phase { PH_NEW_ITER = 0, PH_TRIAL = 1, PH_DONE = 2 };
 enum Gate { GATE_ALWAYS = 0, GATE_NEW_ITER = 1, GATE_ACTIVE = 2 };
 
 struct SolveOptsDev {
-  int precond, restart_period, max_iter, armijo_max, trace_cap, fp32_phase, beta_rule, pad;
+  int precond, restart_period, max_iter, armijo_max, trace_cap, fp32_phase, beta_rule, stall_iters;
   double tol_res, tol_dE, armijo_c1, theta_max, accept_rtol, pv_floor;
 };
 
@@ -89,6 +89,8 @@ struct DevState {
   double rz, rz_prev;  // Re<r, P^{-1} r> of this and of the previous iteration (PR+ beta)
   double dV, invN;
   long long ffts;
+  double res_best;     // smallest residual so far and the iteration that reached it
+  int n_best, pad2;
 };
 
 // Gauss-Legendre node constants of the LHY u-integral, in field precision.

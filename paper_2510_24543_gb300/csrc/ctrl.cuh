@@ -215,6 +215,18 @@ __device__ inline void ctrl_after_pc(DevState* st) {
     st->phase = PH_DONE;
     return;
   }
+  // FP32 fields: stop once the residual has stalled at its round-off floor
+  // (no 10% decrease of the best residual within stall_iters iterations).
+  if (op.stall_iters > 0) {
+    if (st->n == 0 || st->res < 0.9 * st->res_best) {
+      st->res_best = st->res;
+      st->n_best = st->n;
+    } else if (st->n - st->n_best >= op.stall_iters) {
+      st->status = 5;
+      st->phase = PH_DONE;
+      return;
+    }
+  }
   bool restart = (op.restart_period <= 0) ? (st->n == 0) : (st->n % op.restart_period == 0);
   double beta = 0.0;
   st->rz = (pc[PC_ZR1] + pc[PC_ZR2]) * dV;

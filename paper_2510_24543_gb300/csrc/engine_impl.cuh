@@ -624,6 +624,7 @@ egpe_status Engine<R>::reset_state(const egpe_solve_opts* o, int fp32_phase, int
     h.opt.theta_max = o->theta_max;
     h.opt.accept_rtol = accept_rtol;
     h.opt.pv_floor = o->pv_floor;
+    h.opt.stall_iters = fp32_phase ? o->stall_iters_fp32 : 0;
   }
   EGPE_CUDA(cudaMemcpyAsync(st_, &h, sizeof(DevState), cudaMemcpyHostToDevice, stream));
   return EGPE_OK;

@@ -44,7 +44,7 @@ class egpe_solve_opts(ct.Structure):
                 ("tol_dE", ct.c_double), ("armijo_c1", ct.c_double), ("theta_max", ct.c_double),
                 ("accept_rtol", ct.c_double), ("accept_rtol_fp32", ct.c_double), ("pv_floor", ct.c_double),
                 ("tol_fp32_switch", ct.c_double), ("max_iter_fp32", ct.c_int), ("trace_cap", ct.c_int),
-                ("trace", ct.c_void_p), ("batch", ct.c_int)]
+                ("trace", ct.c_void_p), ("batch", ct.c_int), ("stall_iters_fp32", ct.c_int)]
 
 
 class egpe_trace_entry(ct.Structure):

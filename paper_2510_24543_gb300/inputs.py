@@ -104,7 +104,7 @@ def scan_workloads(count: int = 64, seed: int = 4242) -> List[Workload]:
         g12, gdd = float(samples[0][k]), float(samples[1][k])
         out.append(Workload(f"scan[{k}] {s}^3", (s, s, s), (10.0, 10.0, 10.0), (1.0, 1.0, 2.0),
                             _sym(400, 400, g12), _sym(gdd, gdd, gdd), 60.0, 2000 + k,
-                            "kinetic"))
+                            "kinetic+diagonal"))
     return out
 
 
