@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-ite", action="store_true", help="skip the NCG-vs-ITE comparison on the 64^3 workload")
     ap.add_argument("--no-scan", action="store_true", help="skip the 64-instance parameter scan")
+    ap.add_argument("--no-tune", action="store_true", help="untuned launch shapes (no autotuning)")
     ap.add_argument("--fp32-switch", type=float, default=1e-4)
     return ap.parse_args()
 
@@ -171,6 +172,7 @@ def run_ours(args):
     from paper_2510_24543_gb300 import egpe as E
     from paper_2510_24543_gb300 import inputs as I
 
+    from paper_2510_24543_gb300 import autotune as AT
     from paper_2510_24543_gb300 import replicas as RP
 
     rank, world, local = dist_env()
@@ -203,6 +205,16 @@ def run_ours(args):
     psi64 = torch.from_numpy(psi0_np).to("cuda")
     psi32 = psi64.to(torch.complex64)
     pc = E.PRECOND[args.precond]
+    device_name = torch.cuda.get_device_name(local)
+    tuning = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        used = AT.tune_handle(h, [w.n], E.EGPE_MIXED, pc, lambda i, e: psi64 if e == 0 else psi32, device_name)
+        tuning = {"seconds": round(time.perf_counter() - t0, 3),
+                  "changed": [{"engine": k.split("|")[2], "kernel": f"{t['name']} L={t['L']}", "choice": t["choice"],
+                               "default": t["default_choice"], "ms_best": round(t["ms_best"], 5),
+                               "ms_default": round(t["ms_default"], 5)}
+                              for k, v in used.items() for t in v if t["choice"] != t["default_choice"]]}
     clocks = Clocks(local)
     clocks.start()
 
@@ -291,6 +303,8 @@ def run_ours(args):
 
     # ---- end to end through the public solve call with host buffers
     h32 = E.egpe_create([grid], [prm], E.EGPE_FP32, stream.cuda_stream)
+    if not args.no_tune:
+        AT.tune_handle(h32, [w.n], E.EGPE_FP32, pc, lambda i, e: psi32, device_name)
     host32 = torch.from_numpy(psi0_np.astype("complex64")).pin_memory()
     calls = max(1, math.ceil(args.steps / args.chunk))
     e2e_iters, e2e_s = 0, 0.0
@@ -322,13 +336,13 @@ def run_ours(args):
     ite = None
     if not args.no_ite:
         try:
-            ite = ncg_vs_ite(E)
+            ite = ncg_vs_ite(E, tune=not args.no_tune)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             ite = {"error": str(ex)[:300]}
     scan = None
     if not args.no_scan:
         try:
-            scan = scan_benchmark(E)
+            scan = scan_benchmark(E, tune=not args.no_tune)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             scan = {"error": str(ex)[:300]}
     clk = clocks.stop()
@@ -350,7 +364,7 @@ def run_ours(args):
                            "step": "one NCG attempt (precondition + line coefficients + trial E/grad + controller)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launch32,
                 "clocks": clk, "fp64": fp64, "time_to_ground_state": tts, "ncg_vs_ite": ite,
-                "scan": scan}
+                "scan": scan, "autotune": tuning}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -395,7 +409,7 @@ def time_to_ground_state(E, h, grid, prm, psi64, pc, fp32_switch):
         E.egpe_destroy(hd)
 
 
-def ncg_vs_ite(E):
+def ncg_vs_ite(E, tune=True):
     """The paper's comparison of NCG with imaginary-time evolution (Sec. VI.B),
     both on the GPU in FP64 on the 64^3 droplet workload from the same seeded
     start, both stopped at |E^{k+1} - E^k| < 1e-6 (Sec. VI.A): iterations or
@@ -409,6 +423,11 @@ def ncg_vs_ite(E):
     psi0 = torch.from_numpy(I.gaussian_start(w)).to("cuda")
     h = E.egpe_create([E.make_grid(w.n, w.L)], [E.params_from_workload(w)], E.EGPE_FP64)
     try:
+        if tune:
+            from paper_2510_24543_gb300 import autotune as AT
+            AT.tune_handle(h, [w.n], E.EGPE_FP64, E.PRECOND["kinetic+diagonal"], lambda i, e: psi0,
+                           torch.cuda.get_device_name())
+
         def ncg(tol_res, tol_dE):
             o = E.egpe_default_solve_opts()
             o.precond = E.PRECOND["kinetic+diagonal"]
@@ -445,7 +464,7 @@ def ncg_vs_ite(E):
         E.egpe_destroy(h)
 
 
-def scan_benchmark(E, tol_res=1e-6, fp32_switch=1e-4):
+def scan_benchmark(E, tol_res=1e-6, fp32_switch=1e-4, tune=True):
     """The 64-instance parameter scan (16 each of 48^3, 64^3, 80^3, 96^3; Latin
     hypercube over g12 and g_dd; P_Delta o P_V preconditioner): wall time to the
     ground states of all instances, mixed precision batched (FP32 phase to
@@ -462,9 +481,16 @@ def scan_benchmark(E, tol_res=1e-6, fp32_switch=1e-4):
     prms = [E.params_from_workload(w) for w in ws]
     starts = [torch.from_numpy(I.gaussian_start(w)) for w in ws]
 
+    from paper_2510_24543_gb300 import autotune as AT
+    device = torch.cuda.get_device_name()
+
     def run(prec, batch, tol):
         h = E.egpe_create(grids, prms, prec)
         try:
+            if tune:
+                AT.tune_handle(h, [w.n for w in ws], prec, E.PRECOND[ws[0].precond],
+                               lambda i, e: starts[i].to("cuda").to(torch.complex128 if e == 0 else torch.complex64),
+                               device)
             o = E.egpe_default_solve_opts()
             o.precond = E.PRECOND[ws[0].precond]
             o.tol_res = tol

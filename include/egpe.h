@@ -99,6 +99,17 @@ typedef struct {
   double shift[2];       /* alpha_i = mu_i - Re <psi_i, Phi_i psi_i>     */
 } egpe_energy_terms;
 
+/* One tuned launch shape (egpe_autotune / egpe_set_tuning). */
+typedef struct {
+  char key[160];            /* kernel instantiation (stable within one build)        */
+  char name[48];            /* readable pass name                                   */
+  int L;                    /* line length of the pass                              */
+  int kind;                 /* 0 row pass: choice = rows per block; 1 column pass:
+                               choice 1 = TMA-fed tile loads, 0 = plain loads       */
+  int choice, default_choice;
+  double ms_best, ms_default;  /* device ms per launch: chosen and untuned shape     */
+} egpe_tuning;
+
 /* Options of egpe_ncg_solve (Algorithm 1 with the readings named below). */
 typedef struct {
   int precond;              /* EGPE_PRECOND_*                                        */
@@ -235,6 +246,23 @@ egpe_status egpe_fft(egpe_handle* h, int inst, const void* in, void* out, int nf
  * output arrays are host memory owned by the caller. */
 egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
                                  int cap, char* names, double* ms, double* bytes, int* count);
+
+/* Launch-shape autotuner (no counterpart in the paper: it picks how the
+ * transforms of Sec. VI.B are tiled on this GPU).  Times every kernel of one
+ * attempt of the instance's engine (0 FP64, 1 FP32) from psi (device) with
+ * each candidate shape -- rows per block of the row passes, TMA-fed or plain
+ * loads of the column passes -- `reps` launches each (controller off), keeps
+ * the fastest in the handle for every later call (captured graphs are
+ * rebuilt), and writes up to cap results to out (host).  The arithmetic does
+ * not change with the shape.  Leaves the instance's solver state reset. */
+egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
+                          egpe_tuning* out, int cap, int* count);
+
+/* Applies tuned shapes (key and choice of each entry; host array) to the
+ * instance's engine, e.g. from a cache of an earlier egpe_autotune of the same
+ * build, device and grid.  Entries whose key the engine never launches are
+ * ignored; out-of-range choices fall back to the untuned shape. */
+egpe_status egpe_set_tuning(egpe_handle* h, int inst, int engine, const egpe_tuning* t, int count);
 
 /* Ground state by preconditioned NCG (Algorithm 1).  psi_inout[i] is the start
  * and receives the result for instance i (device pointers unless

@@ -293,6 +293,44 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
   return EGPE_OK;
 }
 
+egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
+                          egpe_tuning* out, int cap, int* count) {
+  if (bad_inst(h, inst) || !psi || precond < 0 || precond > 3 || reps < 1 || cap < 0 || (cap > 0 && !out))
+    return EGPE_ERR_INVALID_ARG;
+  std::vector<egpe::TuneResult> res;
+  egpe_status s;
+  if (engine == 0 && !h->e64.empty()) s = h->e64[inst]->autotune((const double2*)psi, precond, reps, res);
+  else if (engine == 1 && !h->e32.empty()) s = h->e32[inst]->autotune((const float2*)psi, precond, reps, res);
+  else return EGPE_ERR_INVALID_ARG;
+  if (s != EGPE_OK) return s;
+  const int n = (int)std::min<size_t>(res.size(), (size_t)cap);
+  for (int k = 0; k < n; ++k) {
+    egpe_tuning& t = out[k];
+    std::memset(&t, 0, sizeof(t));
+    std::strncpy(t.key, res[k].key.c_str(), sizeof(t.key) - 1);
+    std::strncpy(t.name, res[k].name.c_str(), sizeof(t.name) - 1);
+    t.L = res[k].L;
+    t.kind = res[k].kind;
+    t.choice = res[k].choice;
+    t.default_choice = res[k].default_choice;
+    t.ms_best = res[k].ms_best;
+    t.ms_default = res[k].ms_default;
+  }
+  if (count) *count = n;
+  return EGPE_OK;
+}
+
+egpe_status egpe_set_tuning(egpe_handle* h, int inst, int engine, const egpe_tuning* t, int count) {
+  if (bad_inst(h, inst) || count < 0 || (count > 0 && !t)) return EGPE_ERR_INVALID_ARG;
+  for (int k = 0; k < count; ++k) {
+    std::string key(t[k].key, strnlen(t[k].key, sizeof(t[k].key)));
+    if (engine == 0 && !h->e64.empty()) h->e64[inst]->set_tuning(key, t[k].choice);
+    else if (engine == 1 && !h->e32.empty()) h->e32[inst]->set_tuning(key, t[k].choice);
+    else return EGPE_ERR_INVALID_ARG;
+  }
+  return EGPE_OK;
+}
+
 static bool opts_ok(const egpe_solve_opts& o) {
   return !(o.precond < 0 || o.precond > 3 || o.beta_rule < 0 || o.beta_rule > 1 || o.max_iter < 0 || o.armijo_max < 0 ||
            o.armijo_max > 60 || !(o.tol_res >= 0.0) || !(o.theta_max > 0.0) || !(o.pv_floor > 0.0) ||

@@ -29,6 +29,24 @@ template <class R> struct LaunchRec {
   int block = 0;
   size_t smem = 0;
   long long units = 0;                // blocks' worth of work per instance
+  // launch-shape tuning (autotune): the single-instance kernels and shape data
+  int kind = 0;                       // 0 row pass, 1 column pass, 2 pointwise
+  const char* key = nullptr;          // identifies the op instantiation
+  const char* name = nullptr;
+  int L = 0;
+  const void* fn1 = nullptr;          // row pass / plain column pass (KArgs parameter)
+  const void* fn1_tma = nullptr;      // column pass fed by TMA (CUtensorMap, KArgs)
+  int tpl = 0, max_threads = 0, mx = 0;
+  size_t rowbytes = 0, smem_fixed = 0, smem_plain = 0, smem_tma = 0;
+  long long rows = 0;
+};
+
+// One tuned launch shape: rows per block (row passes) or 1 = TMA-fed / 0 =
+// plain loads (column passes).
+struct TuneResult {
+  std::string key, name;
+  int L = 0, kind = 0, choice = 0, default_choice = 0;
+  double ms_best = 0.0, ms_default = 0.0;
 };
 
 void set_error(const char* what, cudaError_t e);
@@ -81,6 +99,20 @@ template <class R> class Engine {
   // or max_steps; the same begin / launch / poll / finish phases as the solver.
   egpe_status ite_begin(double dtau, double tol_dE, int max_steps, bool use_graph);
   egpe_status ite(double dtau, double tol_dE, int max_steps, int poll_every, bool use_graph, SolveRun& run);
+  // Launch-shape autotuning: times every candidate shape of each kernel of one
+  // attempt from psi (reps launches each, controller off) and keeps the fastest.
+  egpe_status autotune(const C* psi, int precond, int reps, std::vector<TuneResult>& out);
+  // Applies previously tuned shapes (by key); unknown keys are ignored.
+  void set_tuning(const std::string& key, int choice) {
+    tune_[key] = choice;
+    drop_graphs();
+  }
+  void clear_tuning() {
+    tune_.clear();
+    drop_graphs();
+  }
+  // Captured graphs hold launch shapes: drop them when the shapes change.
+  void drop_graphs();
   // Records (instead of launching) the kernels of one solver attempt.
   egpe_status record_attempt(int mode, std::vector<LaunchRec<R>>& recs, std::vector<KArgs<R>>& args);
   C* current_psi();  // valid after solve (device)
@@ -182,6 +214,7 @@ template <class R> class Engine {
   cudaGraphExec_t graph_ite_ = nullptr;
   int ite_per_step_ = 0;
   bool run_ite_ = false;
+  std::unordered_map<std::string, int> tune_;  // tuned launch shapes by op key
   std::vector<LaunchRec<R>>* rec_ = nullptr;  // recording mode when set
   std::vector<KArgs<R>>* rec_args_ = nullptr;
   friend class BatchRunner<R>;

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <typeinfo>
 #include <vector>
 
 #include "engine.h"
@@ -232,6 +233,16 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   return reset_state(nullptr, 0, 0, 0.0, 0.0);
 }
 
+template <class R> void Engine<R>::drop_graphs() {
+  for (auto& gx : graph_)
+    if (gx) {
+      cudaGraphExecDestroy(gx);
+      gx = nullptr;
+    }
+  if (graph_ite_) cudaGraphExecDestroy(graph_ite_);
+  graph_ite_ = nullptr;
+}
+
 template <class R> void Engine<R>::destroy() {
   for (auto& k : tlog_) {
     cudaEventDestroy(k.a);
@@ -377,6 +388,128 @@ egpe_status Engine<R>::record_attempt(int mode, std::vector<LaunchRec<R>>& recs,
   return s;
 }
 
+// Launch-shape autotuning.  Each distinct kernel of one attempt is launched
+// on its own (controller off, gate open) with every candidate shape and timed
+// with CUDA events; the fastest shape is kept in tune_ (by op key) and used by
+// every later launch, recording and graph capture of this engine.
+template <class R>
+egpe_status Engine<R>::autotune(const C* psi, int precond, int reps, std::vector<TuneResult>& out) {
+  out.clear();
+  reps = std::max(1, reps);
+  egpe_solve_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.precond = precond & 3;
+  o.restart_period = 20;
+  o.armijo_max = 30;
+  o.armijo_c1 = 1e-4;
+  o.theta_max = 1.5707963267948966;
+  o.pv_floor = 1e-2;
+  EGPE_CUDA(cudaMemcpyAsync(base_->psi[0], psi, 2 * N * sizeof(C), cudaMemcpyDeviceToDevice, stream));
+  EGPE_TRY(reset_state(&o, sizeof(R) == 4, 1 << 30, 0.0, sizeof(R) == 4 ? 1e-6 : 1e-13));
+  EGPE_CUDA(cudaMemsetAsync(base_->rb[0], 0, 8 * N * sizeof(C), stream));
+  EGPE_TRY(enq_eg(0, GATE_ALWAYS, 1));
+  EGPE_TRY(enq_attempt(o.precond));  // realistic coefficients in the state
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  std::vector<LaunchRec<R>> recs;
+  std::vector<KArgs<R>> args;
+  const auto saved = tune_;
+  tune_.clear();  // record the untuned shapes
+  egpe_status s = record_attempt(o.precond, recs, args);
+  tune_ = saved;
+  EGPE_TRY(s);
+  cudaEvent_t e0, e1;
+  EGPE_CUDA(cudaEventCreate(&e0));
+  EGPE_CUDA(cudaEventCreate(&e1));
+  std::unordered_map<std::string, int> seen;
+  egpe_status st = EGPE_OK;
+  for (const LaunchRec<R>& r : recs) {
+    if (r.kind > 1 || !r.key || seen.count(r.key)) continue;
+    seen[r.key] = 1;
+    KArgs<R> a = args[r.arg];
+    a.ctrl = 0;
+    a.gate = GATE_ALWAYS;
+    std::vector<int> cand;
+    if (r.kind == 0) {
+      for (int mx = r.mx; mx >= 1; mx /= 2)
+        if (mx * r.tpl >= 32 || mx == r.mx) cand.push_back(mx);
+      const int up = r.mx * 2;
+      if (up * r.tpl <= r.max_threads && (size_t)up * r.rowbytes + r.smem_fixed <= 200 * 1024) cand.push_back(up);
+    } else {
+      cand.push_back(0);
+      if (r.tm && use_tma_) cand.push_back(1);
+    }
+    TuneResult tr;
+    tr.key = r.key;
+    tr.name = r.name ? r.name : "";
+    tr.L = r.L;
+    tr.kind = r.kind;
+    tr.default_choice = r.mx;
+    double best = 1e30;
+    for (int c : cand) {
+      const void* fn;
+      int block;
+      size_t smem;
+      long long units;
+      CUtensorMap tmc;
+      void* params[2];
+      if (r.kind == 0) {
+        a.MX = c;
+        fn = r.fn1;
+        block = c * r.tpl;
+        smem = r.smem_fixed + (size_t)c * r.rowbytes;
+        units = (r.rows + c - 1) / c;
+        params[0] = &a;
+      } else {
+        fn = c ? r.fn1_tma : r.fn1;
+        block = r.block;
+        smem = c ? r.smem_tma : r.smem_plain;
+        units = r.units;
+        if (c) {
+          tmc = *r.tm;
+          params[0] = &tmc;
+          params[1] = &a;
+        } else {
+          params[0] = &a;
+        }
+      }
+      const int occ = occupancy(fn, block, smem);
+      const dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(units, std::min(occ * nsm_, 16384))));
+      double tmin = 1e30;
+      for (int k = 0; k <= reps && st == EGPE_OK; ++k) {
+        cudaEventRecord(e0, stream);
+        cudaError_t le = cudaLaunchKernel(fn, grid, dim3((unsigned)block), params, smem, stream);
+        cudaEventRecord(e1, stream);
+        if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          set_error("autotune launch", le != cudaSuccess ? le : cudaGetLastError());
+          st = EGPE_ERR_CUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (k > 0) tmin = std::min(tmin, (double)ms);  // the first launch warms up
+      }
+      if (st != EGPE_OK) break;
+      if (c == r.mx) tr.ms_default = tmin;
+      if (tmin < best) {
+        best = tmin;
+        tr.choice = c;
+      }
+    }
+    if (st != EGPE_OK) break;
+    tr.ms_best = best;
+    tune_[tr.key] = tr.choice;
+    out.push_back(tr);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  EGPE_TRY(st);
+  drop_graphs();
+  // leave a clean state: the next solve starts from its own psi
+  EGPE_TRY(reset_state(nullptr, 0, 0, 0.0, 0.0));
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  return EGPE_OK;
+}
+
 template <class R>
 egpe_status Engine<R>::launch_point(void (*kern)(KArgs<R>), void (*kern_b)(KBatch<R>), const char* name,
                                     double bytes, const KArgs<R>& a, long long units) {
@@ -397,16 +530,39 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   const size_t rowbytes = (size_t)NF * LP * sizeof(C);
   int mx = std::max(1, 32 / TPL);
   while ((mx * 2) * TPL <= MaxThreads<Op>::v && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
+  const int mx_default = mx;
+  if (!tune_.empty()) {
+    auto it = tune_.find(typeid(Op).name());
+    if (it != tune_.end() && it->second >= 1 && it->second * TPL <= MaxThreads<Op>::v &&
+        (size_t)it->second * rowbytes <= 200 * 1024)
+      mx = it->second;
+  }
   a.MX = mx;
   const int block = mx * TPL;
-  const size_t smem = L * sizeof(C) + (Op::USES_LHY ? (size_t)a.Q * sizeof(LhyNode<R>) : 0) + mx * rowbytes +
-                      (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const size_t smem_fixed =
+      L * sizeof(C) + (Op::USES_LHY ? (size_t)a.Q * sizeof(LhyNode<R>) : 0) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const size_t smem = smem_fixed + mx * rowbytes;
   const int rows = ny * nz;
   const int groups = (rows + mx - 1) / mx;
-  if (rec_) return record(a, nullptr, xb_fn<Op>(), block, smem, groups);
   void (*kern)(KArgs<R>);
   if constexpr (MinBlocks<Op>::v > 1) kern = xpass_kernel_mb<Op>;
   else kern = xpass_kernel<Op>;
+  if (rec_) {
+    EGPE_TRY(record(a, nullptr, xb_fn<Op>(), block, smem, groups));
+    LaunchRec<R>& r = rec_->back();
+    r.kind = 0;
+    r.key = typeid(Op).name();
+    r.name = Op::NAME;
+    r.L = L;
+    r.fn1 = (const void*)kern;
+    r.tpl = TPL;
+    r.max_threads = MaxThreads<Op>::v;
+    r.mx = mx_default;
+    r.rowbytes = rowbytes;
+    r.smem_fixed = smem_fixed;
+    r.rows = rows;
+    return EGPE_OK;
+  }
   const int occ = occupancy((const void*)kern, block, smem);
   const int grid = std::min(groups, std::min(occ * nsm_, 16384));
   if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
@@ -424,18 +580,39 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   const int block = M * TPL;
   const int other = (Op::AXIS == 1) ? nz : ny;
   const int tiles = (nx / M) * other * a.nf;
-  if (tm && use_tma_) {
-    const size_t smem = 2 * (size_t)M * L * sizeof(C) + L * sizeof(C) + 2 * sizeof(uint64_t) +
-                        (NS > 0 ? sizeof(RedSmem<NS>) : 0);
-    if (rec_) return record(a, tm, (const void*)colpass_tma_kernel_b<Op>, block, smem, tiles);
+  const size_t smem_tma =
+      2 * (size_t)M * L * sizeof(C) + L * sizeof(C) + 2 * sizeof(uint64_t) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const size_t smem_plain = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  bool tma = tm && use_tma_;
+  if (tma && !tune_.empty()) {
+    auto it = tune_.find(typeid(Op).name());
+    if (it != tune_.end()) tma = it->second != 0;
+  }
+  if (rec_) {
+    if (tma) EGPE_TRY(record(a, tm, (const void*)colpass_tma_kernel_b<Op>, block, smem_tma, tiles));
+    else EGPE_TRY(record(a, nullptr, (const void*)colpass_kernel_b<Op>, block, smem_plain, tiles));
+    LaunchRec<R>& r = rec_->back();
+    r.kind = 1;
+    r.key = typeid(Op).name();
+    r.name = Op::NAME;
+    r.L = L;
+    r.fn1 = (const void*)colpass_kernel<Op>;
+    r.fn1_tma = (const void*)colpass_tma_kernel<Op>;
+    r.tm = tm;  // kept for tuning even when this launch uses plain loads
+    r.smem_plain = smem_plain;
+    r.smem_tma = smem_tma;
+    r.mx = (tm && use_tma_) ? 1 : 0;  // the untuned choice
+    return EGPE_OK;
+  }
+  if (tma) {
+    const size_t smem = smem_tma;
     const int occ = occupancy((const void*)colpass_tma_kernel<Op>, block, smem);
     const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
     if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
     colpass_tma_kernel<Op><<<grid, block, smem, stream>>>(*tm, a);
     if (timing_) t_end();
   } else {
-    const size_t smem = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
-    if (rec_) return record(a, nullptr, (const void*)colpass_kernel_b<Op>, block, smem, tiles);
+    const size_t smem = smem_plain;
     const int occ = occupancy((const void*)colpass_kernel<Op>, block, smem);
     const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
     if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));

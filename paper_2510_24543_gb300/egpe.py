@@ -58,6 +58,12 @@ class egpe_ite_opts(ct.Structure):
                 ("use_graph", ct.c_int), ("psi_on_host", ct.c_int)]
 
 
+class egpe_tuning(ct.Structure):
+    _fields_ = [("key", ct.c_char * 160), ("name", ct.c_char * 48), ("L", ct.c_int), ("kind", ct.c_int),
+                ("choice", ct.c_int), ("default_choice", ct.c_int), ("ms_best", ct.c_double),
+                ("ms_default", ct.c_double)]
+
+
 class egpe_report(ct.Structure):
     _fields_ = [("status", ct.c_int), ("iters", ct.c_int), ("iters_fp32", ct.c_int), ("attempts", ct.c_int),
                 ("restarts", ct.c_int), ("armijo_steps", ct.c_int), ("trace_len", ct.c_int),
@@ -94,6 +100,9 @@ _SIGS = {
     "egpe_ite_solve": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(egpe_ite_opts),
                                   ct.POINTER(egpe_report)]),
     "egpe_default_ite_opts": (None, [ct.POINTER(egpe_ite_opts)]),
+    "egpe_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int,
+                                 ct.POINTER(egpe_tuning), ct.c_int, ct.POINTER(ct.c_int)]),
+    "egpe_set_tuning": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(egpe_tuning), ct.c_int]),
     "egpe_default_solve_opts": (None, [ct.POINTER(egpe_solve_opts)]),
     "egpe_status_string": (ct.c_char_p, [ct.c_int]),
     "egpe_last_error": (ct.c_char_p, []),
@@ -295,6 +304,26 @@ def egpe_ite_solve(h: int, psis, opts: egpe_ite_opts, n_inst: int = 1):
     if status in (1, 2, 3):
         raise EgpeError("egpe_ite_solve", status)
     return status, [_report_dict(r) for r in reps]
+
+
+def egpe_autotune(h: int, inst: int, engine: int, psi, precond: int, reps: int = 5, cap: int = 64):
+    """Tunes the instance's launch shapes from psi; returns one dict per kernel."""
+    arr = (egpe_tuning * cap)()
+    n = ct.c_int(0)
+    _check("egpe_autotune", load().egpe_autotune(ct.c_void_p(h), inst, engine, ct.c_void_p(_ptr(psi)), precond,
+                                                 reps, arr, cap, ct.byref(n)))
+    return [dict(key=t.key.decode(), name=t.name.decode(), L=t.L, kind=t.kind, choice=t.choice,
+                 default_choice=t.default_choice, ms_best=t.ms_best, ms_default=t.ms_default)
+            for t in arr[:n.value]]
+
+
+def egpe_set_tuning(h: int, inst: int, engine: int, entries) -> None:
+    """Applies tuned shapes (dicts with key and choice)."""
+    arr = (egpe_tuning * max(1, len(entries)))()
+    for k, e in enumerate(entries):
+        arr[k].key = e["key"].encode()[:159]
+        arr[k].choice = int(e["choice"])
+    _check("egpe_set_tuning", load().egpe_set_tuning(ct.c_void_p(h), inst, engine, arr, len(entries)))
 
 
 def _report_dict(r) -> dict:
