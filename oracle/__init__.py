@@ -21,6 +21,8 @@ routines (``tests/test_oracle_pins.py``).  Parity status per function:
 * preconditioners, beta, projection, retraction, NCG loop: pinned (invariants,
   harmonic closed form, descent, symmetry, agreement with ITE)
 * ITE reference: pinned (harmonic closed form, agreement with NCG)
+* parameter derivatives dE/d(g, g_dd, kappa, eta_s, trap): pinned (central
+  differences of the energy, Hellmann-Feynman at a converged ground state)
 * the paper's Table I energies: parity unpinned (the paper's physical
   parameters for that table are incomplete)
 """
@@ -29,5 +31,5 @@ from .egpe import (  # noqa: F401
     gauss_legendre_01, inner, kinetic_apply, trap_potential, dipolar_potentials,
     lhy_density_and_mu, evaluate, energy_grad, line_coeffs, line_coeffs_detail,
     preconditioner_shift, precondition, project, retract, ncg_solve, ite_solve,
-    PRECOND_MODES,
+    lhy_eta_derivatives, param_grad, PARAM_NAMES, PRECOND_MODES,
 )

@@ -220,6 +220,79 @@ def energy_grad(grid: Grid, prm: Params, psi: np.ndarray):
     return ev.E, ev.mu, ev.Hpsi
 
 
+PARAM_NAMES = ("g11", "g12", "g22", "gdd11", "gdd12", "gdd22", "kappa", "eta_s", "trap_x", "trap_y", "trap_z")
+
+
+def lhy_eta_derivatives(prm: Params, n1: np.ndarray, n2: np.ndarray):
+    """Partial derivatives of the LHY density F (Eq. 1) with respect to the
+    entries of eta(u) = g + g_dd (3u^2 - 1), accumulated over the u-rule:
+    returns dF/dg11, dF/dg22, dF/dg12 (the symmetric pair g12 = g21 moved
+    together) and the same with the extra factor 3u^2 - 1 (dF/dgdd_ij).
+
+    With A = eta11 n1 + eta22 n2, delta = eta11 n1 - eta22 n2,
+    s^2 = delta^2 + 4 eta12 eta21 n1 n2 and V_+- = A +- s:
+      dV_+-/deta11 = n1 +- delta n1 / s,   dV_+-/deta22 = n2 -+ delta n2 / s,
+      dV_+-/deta12 (pair) = +- 4 eta12 n1 n2 / s,
+    and d max(V,0)^{5/2} = (5/2) max(V,0)^{3/2} dV (terms / s taken as 0 where s = 0).
+    """
+    u, w = gauss_legendre_01(prm.nodes)
+    out = [np.zeros_like(n1) for _ in range(6)]
+    for uq, wq in zip(u, w):
+        x = 3.0 * uq * uq - 1.0
+        eta = _eta(prm, uq)
+        e11, e22, e12 = eta[0, 0], eta[1, 1], eta[0, 1]
+        delta = e11 * n1 - e22 * n2
+        s = np.sqrt(delta ** 2 + 4.0 * eta[0, 1] * eta[1, 0] * n1 * n2)
+        A = e11 * n1 + e22 * n2
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv_s = np.where(s > 0, 1.0 / np.where(s > 0, s, 1.0), 0.0)
+        for sign in (1.0, -1.0):
+            V = np.maximum(A + sign * s, 0.0)
+            f = 2.5 * V ** 1.5
+            d11 = n1 + sign * delta * n1 * inv_s
+            d22 = n2 - sign * delta * n2 * inv_s
+            d12 = sign * 4.0 * e12 * n1 * n2 * inv_s
+            for k, d in enumerate((d11, d22, d12)):
+                out[k] += wq * f * d
+                out[3 + k] += wq * x * f * d
+    c5 = prm.c5
+    return [c5 * a for a in out]
+
+
+def param_grad(grid: Grid, prm: Params, psi: np.ndarray) -> Dict[str, float]:
+    """Partial derivatives of E (Eq. 1) with respect to its parameters at fixed psi.
+
+    Contact: dE/dg_ii = 1/2 int n_i^2, dE/dg12 = int n1 n2 (g12 = g21 together).
+    Dipolar: dE/dgdd_ii = 1/2 int n_i (K * n_i), dE/dgdd12 = int n1 (K * n2), K the
+    k-space kernel 3k_z^2/|k|^2 - 1.  LHY: through eta(u) (lhy_eta_derivatives),
+    dE/dkappa = E_LHY / kappa, dE/deta_s = -(5/2) E_LHY / eta_s.  Trap (V = 1/2
+    sum lambda_a^2 x_a^2): dE/dlambda_a = lambda_a int x_a^2 (n1 + n2).
+    At a normalised ground state these are dE0/dp (Hellmann-Feynman).
+    """
+    n = (np.abs(psi) ** 2).astype(np.float64)
+    dV = grid.dV
+    Kn = [idft(grid.kdd * dft(n[i])).real for i in range(2)]
+    L = lhy_eta_derivatives(prm, n[0], n[1])
+    F, _, _ = lhy_density_and_mu(prm, n[0], n[1])
+    E_lhy = dV * np.sum(F)
+    x, y, z = grid.x
+    nt = n[0] + n[1]
+    out = {
+        "g11": dV * (0.5 * np.sum(n[0] * n[0]) + np.sum(L[0])),
+        "g22": dV * (0.5 * np.sum(n[1] * n[1]) + np.sum(L[1])),
+        "g12": dV * (np.sum(n[0] * n[1]) + np.sum(L[2])),
+        "gdd11": dV * (0.5 * np.sum(n[0] * Kn[0]) + np.sum(L[3])),
+        "gdd22": dV * (0.5 * np.sum(n[1] * Kn[1]) + np.sum(L[4])),
+        "gdd12": dV * (np.sum(n[0] * Kn[1]) + np.sum(L[5])),
+        "kappa": E_lhy / prm.kappa,
+        "eta_s": -2.5 * E_lhy / prm.eta_s,
+        "trap_x": prm.trap[0] * dV * np.sum(x[None, None, :] ** 2 * nt),
+        "trap_y": prm.trap[1] * dV * np.sum(y[None, :, None] ** 2 * nt),
+        "trap_z": prm.trap[2] * dV * np.sum(z[:, None, None] ** 2 * nt),
+    }
+    return {k: float(v) for k, v in out.items()}
+
+
 # ----------------------------------------------------------------------------
 # Analytic line-search coefficients (Sec. V)
 # ----------------------------------------------------------------------------

@@ -13,6 +13,8 @@ import pytest
 import oracle as O
 from paper_2510_24543_gb300 import inputs as I
 
+from . import _common as _cm
+
 
 def _prm(g=((0, 0), (0, 0)), gdd=((0, 0), (0, 0)), kappa=0.0, eta_s=1.0, nodes=32, trap=(1, 1, 1)):
     return O.Params(np.array(g, float), np.array(gdd, float), kappa, eta_s, nodes, trap)
@@ -438,3 +440,90 @@ def test_oracle_matches_stored_c1_values():
     E0, Ep, Epp = O.line_coeffs(g, prm, psi, p, ev)
     assert abs(Ep - gold["line_coeffs"]["Ep"]) < 1e-11 * abs(Ep)
     assert abs(Epp - gold["line_coeffs"]["Epp"]) < 1e-11 * abs(Epp)
+
+
+# ---------------------------------------------------------------- parameter derivatives
+def _with_param(prm, name, value):
+    import copy
+    q = copy.deepcopy(prm)
+    if name in ("g11", "g22"):
+        i = 0 if name == "g11" else 1
+        q.g[i, i] = value
+    elif name == "g12":
+        q.g[0, 1] = q.g[1, 0] = value
+    elif name in ("gdd11", "gdd22"):
+        i = 0 if name == "gdd11" else 1
+        q.gdd[i, i] = value
+    elif name == "gdd12":
+        q.gdd[0, 1] = q.gdd[1, 0] = value
+    elif name == "kappa":
+        q.kappa = value
+    elif name == "eta_s":
+        q.eta_s = value
+    else:
+        t = list(q.trap)
+        t["xyz".index(name[-1])] = value
+        q.trap = tuple(t)
+    return q
+
+
+def _param_value(prm, name):
+    return {"g11": prm.g[0, 0], "g22": prm.g[1, 1], "g12": prm.g[0, 1], "gdd11": prm.gdd[0, 0],
+            "gdd22": prm.gdd[1, 1], "gdd12": prm.gdd[0, 1], "kappa": prm.kappa, "eta_s": prm.eta_s,
+            "trap_x": prm.trap[0], "trap_y": prm.trap[1], "trap_z": prm.trap[2]}[name]
+
+
+def test_param_grad_matches_central_differences():
+    """Every partial derivative against Richardson-extrapolated central
+    differences of the energy, on a complex state with distinct couplings
+    (a dropped LHY term or a wrong factor 1/2 fails by far more than 1e-6)."""
+    w = _cm.mixed_workload((12, 10, 16))
+    g, prm = _cm.oracle_case(w)
+    psi = I.random_state(w.n, w.L, 5, width=(1.2, 1.5, 0.9))
+    d = O.param_grad(g, prm, psi)
+    for name in O.PARAM_NAMES:
+        p0 = _param_value(prm, name)
+        h = 1e-3 * abs(p0)
+
+        def E(v):
+            return O.evaluate(g, _with_param(prm, name, v), psi).E
+
+        d1 = (E(p0 + h) - E(p0 - h)) / (2 * h)
+        d2 = (E(p0 + h / 2) - E(p0 - h / 2)) / h
+        fd = (4 * d2 - d1) / 3
+        assert abs(d[name] - fd) < 1e-6 * max(abs(fd), 1e-3 * abs(O.evaluate(g, prm, psi).E)), name
+
+
+def test_lhy_eta_derivatives_vanish_without_lhy_and_scale_with_kappa():
+    w = _cm.mixed_workload((8, 8, 8))
+    g, prm = _cm.oracle_case(w)
+    psi = I.random_state(w.n, w.L, 6)
+    n = np.abs(psi) ** 2
+    a = O.lhy_eta_derivatives(prm, n[0], n[1])
+    b = O.lhy_eta_derivatives(_with_param(prm, "kappa", 2 * prm.kappa), n[0], n[1])
+    for x, y in zip(a, b):
+        assert np.allclose(2 * x, y, rtol=1e-14, atol=0)
+    z = O.lhy_eta_derivatives(_with_param(prm, "kappa", 0.0), n[0], n[1])
+    assert all(np.all(v == 0) for v in z)
+
+
+def test_hellmann_feynman_at_a_ground_state():
+    """At a converged ground state dE0/dp equals the partial derivative at
+    fixed psi (the normalisation does not depend on p): checked for g12,
+    gdd12 and the z trap frequency against central differences of solved
+    ground-state energies."""
+    w = I.Workload("hf", (16, 16, 16), (6.0, 6.0, 6.0), (1.0, 1.0, 1.5), ((60.0, 25.0), (25.0, 50.0)),
+                   ((40.0, 20.0), (20.0, 30.0)), 10.0, 7, "kinetic", 8)
+    g, prm = _cm.oracle_case(w)
+    psi0 = I.gaussian_start(w)
+    opts = O.SolveOpts(precond="kinetic+diagonal", tol_res=1e-10, max_iter=4000)
+    psi, rep = O.ncg_solve(g, prm, psi0, opts)
+    assert rep["status"] == "converged"
+    d = O.param_grad(g, prm, psi)
+    for name in ("g12", "gdd12", "trap_z"):
+        p0 = _param_value(prm, name)
+        h = 1e-3 * abs(p0)
+        Ep = O.ncg_solve(g, _with_param(prm, name, p0 + h), psi, opts)[1]["E"]
+        Em = O.ncg_solve(g, _with_param(prm, name, p0 - h), psi, opts)[1]["E"]
+        fd = (Ep - Em) / (2 * h)
+        assert abs(fd - d[name]) < 1e-6 * max(1.0, abs(d[name])), name
