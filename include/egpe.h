@@ -167,6 +167,15 @@ typedef struct {
   long long kernels;        /* kernel launches issued (including masked ones)       */
 } egpe_report;
 
+/* Parameters of egpe_param_grad's output, in this order: the contact couplings
+ * g11, g12 (= g21, moved together), g22; the dipolar coefficients gdd11,
+ * gdd12 (= gdd21), gdd22; the LHY prefactor kappa and scale eta_s; the trap
+ * frequencies lambda_x, lambda_y, lambda_z. */
+enum {
+  EGPE_P_G11 = 0, EGPE_P_G12, EGPE_P_G22, EGPE_P_GDD11, EGPE_P_GDD12, EGPE_P_GDD22,
+  EGPE_P_KAPPA, EGPE_P_ETA_S, EGPE_P_TRAP_X, EGPE_P_TRAP_Y, EGPE_P_TRAP_Z, EGPE_NPARAM
+};
+
 typedef struct egpe_handle egpe_handle;
 
 /* Create a handle for n_inst instances (grids[i], params[i]) of the given
@@ -211,6 +220,24 @@ egpe_status egpe_energy_grad(egpe_handle* h, int inst, const void* psi, double* 
 /* As egpe_energy_grad, returning every energy term (host struct). */
 egpe_status egpe_energy_terms_eval(egpe_handle* h, int inst, const void* psi,
                                    egpe_energy_terms* terms, void* grad);
+
+/* Partial derivatives of E (Eq. 1) with respect to its parameters at fixed
+ * psi (device field of the instance's precision; the FP64 engine for MIXED
+ * handles), written to dEdp[EGPE_NPARAM] (host):
+ *   dE/dg_ii = 1/2 int n_i^2 + int dF/deta_ii,  dE/dg12 = int n1 n2 + int dF/deta12,
+ *   dE/dgdd_ii = 1/2 int n_i (K*n_i) + int w dF/deta_ii,  dE/dgdd12 = int n1 (K*n2) + ...,
+ *   dE/dkappa = E_LHY/kappa (NaN when kappa = 0), dE/deta_s = -5/2 E_LHY/eta_s,
+ *   dE/dlambda_a = lambda_a int x_a^2 (n1 + n2),
+ * with K the k-space dipolar kernel, w = 3u^2 - 1 and F the LHY density through
+ * eta(u) = g + gdd w.  The paper has no such pass; at a normalised ground
+ * state these are the derivatives of the ground-state energy
+ * (Hellmann-Feynman).  Also the parameter half of the autograd binding. */
+egpe_status egpe_param_grad(egpe_handle* h, int inst, const void* psi, double* dEdp);
+
+/* Replaces the couplings, LHY constants and trap of instance inst (same grid
+ * and precision; validated as in egpe_create).  Captured graphs are rebuilt;
+ * the next call uses the new parameters. */
+egpe_status egpe_set_params(egpe_handle* h, int inst, const egpe_params* params);
 
 /* Coefficients of the energy along the geodesic psi_i(alpha) =
  * cos(alpha ||p_i||) psi_i + sin(alpha ||p_i||) p_i/||p_i|| (Sec. V):

@@ -293,6 +293,24 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
   return EGPE_OK;
 }
 
+egpe_status egpe_param_grad(egpe_handle* h, int inst, const void* psi, double* dEdp) {
+  if (bad_inst(h, inst) || !psi || !dEdp) return EGPE_ERR_INVALID_ARG;
+  if (h->prec == EGPE_FP32) return h->e32[inst]->param_grad((const float2*)psi, dEdp);
+  return h->e64[inst]->param_grad((const double2*)psi, dEdp);
+}
+
+egpe_status egpe_set_params(egpe_handle* h, int inst, const egpe_params* params) {
+  if (bad_inst(h, inst) || !params) return EGPE_ERR_INVALID_ARG;
+  egpe_status s = validate(h->grids[inst], *params);
+  if (s != EGPE_OK) return s;
+  if (!h->e64.empty()) {
+    s = h->e64[inst]->set_params(*params);
+    if (s != EGPE_OK) return s;
+  }
+  if (!h->e32.empty()) s = h->e32[inst]->set_params(*params);
+  return s;
+}
+
 egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
                           egpe_tuning* out, int cap, int* count) {
   if (bad_inst(h, inst) || !psi || precond < 0 || precond > 3 || reps < 1 || cap < 0 || (cap > 0 && !out))

@@ -49,7 +49,12 @@ enum LcSlot {  // line-coefficient sums
 };
 enum LczSlot { LCZ_TPP1 = 0, LCZ_TPP2, LCZ_NS };
 enum RtSlot { RT_P1 = 0, RT_P2, RT_PSIP1, RT_PSIP2, RT_PSI1, RT_PSI2, RT_NS };
+enum PgSlot {  // parameter-derivative sums (x dV later)
+  PG_N11 = 0, PG_N12, PG_N22, PG_K11, PG_K12, PG_K22, PG_X2, PG_Y2, PG_Z2,
+  PG_F, PG_L11, PG_L22, PG_L12, PG_M11, PG_M22, PG_M12, PG_NS
+};
 static constexpr int MAX_NS = 16;
+static_assert(PG_NS <= MAX_NS, "reduction slots");
 
 // Phases of the on-device solver state machine.
 enum Phase { PH_NEW_ITER = 0, PH_TRIAL = 1, PH_DONE = 2 };
@@ -76,6 +81,7 @@ struct DevState {
   double lc[MAX_NS];
   double lcz[4];
   double rt[MAX_NS];
+  double pg[MAX_NS];
   // flow control
   int phase, status, n, attempts, restarts, armijo_total, armijo_k, kind;
   int cur, fallback, trace_len, restart_flag;

@@ -76,6 +76,10 @@ template <class R> class Engine {
   egpe_status retract(const C* psi, const C* p, const double theta[2], C* out);
   egpe_status fft(const C* in, C* out, int nf, int inverse);
   egpe_status normalise_current();
+  // Partial derivatives of E at psi with respect to the parameters (index
+  // EGPE_P_*), and an in-place change of the parameters (same grid).
+  egpe_status param_grad(const C* psi, double out[EGPE_NPARAM]);
+  egpe_status set_params(const egpe_params& p);
 
   // Solver: psi start must already be in psi buffer 0 (load_psi / cast).
   egpe_status load_psi(const void* src, cudaMemcpyKind kind);
@@ -129,6 +133,8 @@ template <class R> class Engine {
   egpe_status enq_lc(int gate, int ctrl, int pgiven);
   egpe_status enq_attempt(int mode);
   egpe_status enq_kin(int potential, int gate);
+  egpe_status enq_pg(int gate);
+  egpe_status apply_params(const egpe_params& p);
   egpe_status enq_ite_step(int gate);
   egpe_status reset_state(const egpe_solve_opts* o, int fp32_phase, int max_iter, double tol_res,
                           double accept_rtol);
@@ -195,6 +201,7 @@ template <class R> class Engine {
   C* twy_ = nullptr;
   C* twz_ = nullptr;
   LhyNode<R>* nodes_ = nullptr;
+  int nodes_q_ = 0;
   double* partials_ = nullptr;
   unsigned* counter_ = nullptr;
   DevState* st_ = nullptr;

@@ -36,10 +36,13 @@
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvW1F2>(int, const KArgs<R>&);                      \
   template egpe_status Engine<R>::dispatch_x_##SFX<XFwdKin>(int, const KArgs<R>&);                       \
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvKin>(int, const KArgs<R>&);                       \
+  template egpe_status Engine<R>::dispatch_x_##SFX<XFwdPG>(int, const KArgs<R>&);                        \
+  template egpe_status Engine<R>::dispatch_x_##SFX<XInvPG>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_col_##SFX<ZEg>(int, const KArgs<R>&, const CUtensorMap*);     \
   template egpe_status Engine<R>::dispatch_col_##SFX<ZPc>(int, const KArgs<R>&, const CUtensorMap*);     \
   template egpe_status Engine<R>::dispatch_col_##SFX<ZLc>(int, const KArgs<R>&, const CUtensorMap*);     \
   template egpe_status Engine<R>::dispatch_col_##SFX<ZKin>(int, const KArgs<R>&, const CUtensorMap*);    \
+  template egpe_status Engine<R>::dispatch_col_##SFX<ZPg>(int, const KArgs<R>&, const CUtensorMap*);     \
   template egpe_status Engine<R>::plain_x_##SFX(int, const KArgs<R>&);                                   \
   template egpe_status Engine<R>::plain_col_##SFX(int, int, const KArgs<R>&, const CUtensorMap*);        \
   }

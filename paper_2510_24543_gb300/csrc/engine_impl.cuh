@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <limits>
 #include <typeinfo>
 #include <vector>
 
@@ -119,6 +120,106 @@ static void gauss_legendre01(int Q, std::vector<long double>& u, std::vector<lon
   }
 }
 
+// Couplings, trap and LHY node table of the instance (at create, and again
+// when the parameters change: egpe_set_params).  The node table keeps its
+// nodes with det eta > 0 first (Qm_ of them).
+template <class R> egpe_status Engine<R>::apply_params(const egpe_params& p) {
+  prm_ = p;
+  const int Q = p.lhy_nodes;
+  std::vector<long double> u, w;
+  gauss_legendre01(Q, u, w);
+  std::vector<LhyNode<R>> h;
+  std::vector<LhyNode<R>> hneg;
+  const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
+  for (int q = 0; q < Q; ++q) {
+    const long double s = 3.0L * u[q] * u[q] - 1.0L;
+    const long double e12 = p.g[0][1] + p.gdd[0][1] * s;
+    const long double det = (p.g[0][0] + p.gdd[0][0] * s) * (p.g[1][1] + p.gdd[1][1] * s) - e12 * e12;
+    LhyNode<R> nd;
+    nd.w = (R)s;
+    nd.W = (R)(c5 * w[q]);
+    nd.Ww = (R)(c5 * w[q] * s);
+    nd.e12sq = (R)(e12 * e12);
+    (det > 0.0L ? h : hneg).push_back(nd);
+  }
+  Qm_ = (int)h.size();
+  h.insert(h.end(), hneg.begin(), hneg.end());
+  // kernels still reading the old table finish first
+  EGPE_CUDA(cudaStreamSynchronize(stream));
+  if (nodes_ && nodes_q_ != Q) {
+    cudaFree(nodes_);
+    nodes_ = nullptr;
+  }
+  if (!nodes_) {
+    EGPE_CUDA(cudaMalloc(&nodes_, Q * sizeof(LhyNode<R>)));
+    nodes_q_ = Q;
+  }
+  EGPE_CUDA(cudaMemcpy(nodes_, h.data(), Q * sizeof(LhyNode<R>), cudaMemcpyHostToDevice));
+  KArgs<R>& a = *base_;
+  a.vx = (R)(0.5 * p.trap[0] * p.trap[0]);
+  a.vy = (R)(0.5 * p.trap[1] * p.trap[1]);
+  a.vz = (R)(0.5 * p.trap[2] * p.trap[2]);
+  a.g11 = (R)p.g[0][0];
+  a.g12 = (R)p.g[0][1];
+  a.g21 = (R)p.g[1][0];
+  a.g22 = (R)p.g[1][1];
+  a.d11 = (R)p.gdd[0][0];
+  a.d12 = (R)p.gdd[0][1];
+  a.d21 = (R)p.gdd[1][0];
+  a.d22 = (R)p.gdd[1][1];
+  a.Q = Q;
+  a.Qm = Qm_;
+  a.nodes = nodes_;
+  return EGPE_OK;
+}
+
+template <class R> egpe_status Engine<R>::set_params(const egpe_params& p) {
+  EGPE_TRY(apply_params(p));
+  drop_graphs();  // captured launches hold the old couplings
+  return EGPE_OK;
+}
+
+// Parameter-derivative pass: one packed density field through the dipolar
+// kernel (4 transform passes) and the sums of the last row pass.
+template <class R> egpe_status Engine<R>::enq_pg(int gate) {
+  KArgs<R> a = *base_;
+  a.gate = gate;
+  a.flag = 0;
+  a.ctrl = 0;
+  a.nf = 1;
+  a.f0 = 0;
+  EGPE_TRY(dispatch_x<XFwdPG>(nx, a));
+  KArgs<R> y = a;
+  y.gin = a.W;
+  y.gout = a.W;
+  EGPE_TRY(plain_col(1, 0, y, tmy()));
+  EGPE_TRY(dispatch_col<ZPg>(nz, a, tmz()));
+  EGPE_TRY(plain_col(1, 1, y, tmy()));
+  return dispatch_x<XInvPG>(nx, a);
+}
+
+template <class R> egpe_status Engine<R>::param_grad(const C* psi, double out[EGPE_NPARAM]) {
+  EGPE_TRY(reset_state(nullptr, 0, 0, 0.0, 0.0));
+  EGPE_CUDA(cudaMemcpyAsync(base_->psi[0], psi, 2 * N * sizeof(C), cudaMemcpyDeviceToDevice, stream));
+  EGPE_TRY(enq_pg(GATE_ALWAYS));
+  DevState hs;
+  EGPE_TRY(read_state(hs));
+  const double* s = hs.pg;
+  const double kap = prm_.lhy_kappa, eta = prm_.lhy_eta_scale;
+  out[EGPE_P_G11] = dV * (0.5 * s[PG_N11] + s[PG_L11]);
+  out[EGPE_P_G12] = dV * (s[PG_N12] + s[PG_L12]);
+  out[EGPE_P_G22] = dV * (0.5 * s[PG_N22] + s[PG_L22]);
+  out[EGPE_P_GDD11] = dV * (0.5 * s[PG_K11] + s[PG_M11]);
+  out[EGPE_P_GDD12] = dV * (s[PG_K12] + s[PG_M12]);
+  out[EGPE_P_GDD22] = dV * (0.5 * s[PG_K22] + s[PG_M22]);
+  out[EGPE_P_KAPPA] = kap != 0.0 ? dV * s[PG_F] / kap : std::numeric_limits<double>::quiet_NaN();
+  out[EGPE_P_ETA_S] = -2.5 * dV * s[PG_F] / eta;
+  out[EGPE_P_TRAP_X] = prm_.trap[0] * dV * s[PG_X2];
+  out[EGPE_P_TRAP_Y] = prm_.trap[1] * dV * s[PG_Y2];
+  out[EGPE_P_TRAP_Z] = prm_.trap[2] * dV * s[PG_Z2];
+  return EGPE_OK;
+}
+
 template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_params& p, cudaStream_t s) {
   grid_ = g;
   prm_ = p;
@@ -158,30 +259,6 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
     EGPE_CUDA(cudaMalloc(tws[ax], L * sizeof(C)));
     EGPE_CUDA(cudaMemcpy(*tws[ax], h.data(), L * sizeof(C), cudaMemcpyHostToDevice));
   }
-  // LHY node constants
-  {
-    const int Q = p.lhy_nodes;
-    std::vector<long double> u, w;
-    gauss_legendre01(Q, u, w);
-    std::vector<LhyNode<R>> h;
-    std::vector<LhyNode<R>> hneg;
-    const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
-    for (int q = 0; q < Q; ++q) {
-      const long double s = 3.0L * u[q] * u[q] - 1.0L;
-      const long double e12 = p.g[0][1] + p.gdd[0][1] * s;
-      const long double det = (p.g[0][0] + p.gdd[0][0] * s) * (p.g[1][1] + p.gdd[1][1] * s) - e12 * e12;
-      LhyNode<R> nd;
-      nd.w = (R)s;
-      nd.W = (R)(c5 * w[q]);
-      nd.Ww = (R)(c5 * w[q] * s);
-      nd.e12sq = (R)(e12 * e12);
-      (det > 0.0L ? h : hneg).push_back(nd);
-    }
-    Qm_ = (int)h.size();
-    h.insert(h.end(), hneg.begin(), hneg.end());
-    EGPE_CUDA(cudaMalloc(&nodes_, Q * sizeof(LhyNode<R>)));
-    EGPE_CUDA(cudaMemcpy(nodes_, h.data(), Q * sizeof(LhyNode<R>), cudaMemcpyHostToDevice));
-  }
   EGPE_CUDA(cudaMalloc(&partials_, (size_t)16384 * MAX_NS * sizeof(double)));
   EGPE_CUDA(cudaMalloc(&counter_, 64 * sizeof(unsigned)));
   EGPE_CUDA(cudaMemset(counter_, 0, 64 * sizeof(unsigned)));
@@ -205,21 +282,8 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   a.dkx = (R)(pi / g.L[0]);
   a.dky = (R)(pi / g.L[1]);
   a.dkz = (R)(pi / g.L[2]);
-  a.vx = (R)(0.5 * p.trap[0] * p.trap[0]);
-  a.vy = (R)(0.5 * p.trap[1] * p.trap[1]);
-  a.vz = (R)(0.5 * p.trap[2] * p.trap[2]);
-  a.g11 = (R)p.g[0][0];
-  a.g12 = (R)p.g[0][1];
-  a.g21 = (R)p.g[1][0];
-  a.g22 = (R)p.g[1][1];
-  a.d11 = (R)p.gdd[0][0];
-  a.d12 = (R)p.gdd[0][1];
-  a.d21 = (R)p.gdd[1][0];
-  a.d22 = (R)p.gdd[1][1];
   a.invN = (R)(1.0 / (double)N);
-  a.Q = p.lhy_nodes;
-  a.Qm = Qm_;
-  a.nodes = nodes_;
+  EGPE_TRY(apply_params(p));
   a.twx = twx_;
   a.twy = twy_;
   a.twz = twz_;

@@ -1322,6 +1322,131 @@ template <class R> __global__ void __launch_bounds__(256) ite_scale_kernel_b(con
 
 
 // ----------------------------------------------------------------------------
+// Parameter derivatives at fixed psi (the adjoint pass of the energy with
+// respect to its couplings, Eq. 1): x fwd of zeta = n1 + i n2 -> y -> z with the
+// dipolar kernel K(k) -> y inv -> x inv: K*n1 = Re, K*n2 = Im (the kernel is real
+// and even), then the contact, dipolar, trap and LHY (through eta) sums.
+// ----------------------------------------------------------------------------
+template <class R_, int L_> struct XFwdPG {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr const char* NAME = "x-fwd densities (param grad)";
+  static double alg_bytes(const KArgs<R>& a) { return 3.0 * a.N * sizeof(C); }
+  static constexpr int L = L_, NF = 1, NS = 0;
+  static constexpr bool INV = false, USES_LHY = false;
+  struct Uni {
+    int cur;
+  };
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) { u.cur = __ldcg(&a.st->cur); }
+  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*) {
+    const C* ps = a.psi[u.cur];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const size_t idx = valid ? (size_t)row * a.nx + Plan<L>::entry_pos(false, t, e) : 0;
+      const C p1 = ps[idx], p2 = ps[(size_t)a.N + idx];
+      v[0][e] = valid ? cmk<C>(cabs2(p1), cabs2(p2)) : cmk<C>(0, 0);
+    }
+  }
+  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*,
+                               const LhyNode<R>*) {
+    if (!valid) return;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a.W[(size_t)row * a.nx + Plan<L>::exit_pos(false, t, e)] = v[0][e];
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct ZPg {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr const char* NAME = "z dipolar kernel (param grad)";
+  static double alg_bytes(const KArgs<R>& a) { return 2.0 * a.N * sizeof(C); }
+  static constexpr int L = L_, NS = 0, AXIS = 2;
+  using Uni = NoUni;
+  static __device__ void uniform(const KArgs<R>&, Uni&) {}
+  static constexpr bool FIRST_INV = false;
+  static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  static __device__ void process(const KArgs<R>& a, Uni&, int, int x, int y, size_t base, size_t ls, int t,
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
+    fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
+    const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
+    const R kxy2 = kx * kx + ky * ky;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const R kz = wavenum<R>(Plan<L>::exit_pos(false, t, e), a.nz, a.dkz);
+      const R k2 = kxy2 + kz * kz;
+      v[0][e] = cscale(v[0][e], (k2 > R(0)) ? (R(3) * kz * kz / k2 - R(1)) * a.invN : R(0));
+    }
+    fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
+  }
+  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+template <class R_, int L_> struct XInvPG {
+  using R = R_;
+  using C = C2<R>;
+  static constexpr int MAXT = 128;
+  static constexpr const char* NAME = "x-inv parameter sums";
+  static double alg_bytes(const KArgs<R>& a) { return 3.0 * a.N * sizeof(C); }
+  static constexpr int L = L_, NF = 1, NS = PG_NS;
+  static constexpr bool INV = true, USES_LHY = true;
+  struct Uni {
+    int cur;
+  };
+  static __device__ void uniform(const KArgs<R>& a, Uni& u) { u.cur = __ldcg(&a.st->cur); }
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      v[0][e] = valid ? a.W[(size_t)row * a.nx + Plan<L>::entry_pos(true, t, e)] : cmk<C>(0, 0);
+  }
+  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[1][8], PAcc<R>* acc,
+                               const LhyNode<R>* nodes) {
+    if (!valid) return;
+    const C* ps = a.psi[u.cur];
+    const int y = row % a.ny, z = row / a.ny;
+    const R Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
+    const LhyCoef<R> cf = lhy_coef(a);
+    R s[PG_NS];
+#pragma unroll
+    for (int k = 0; k < PG_NS; ++k) s[k] = R(0);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int x = Plan<L>::exit_pos(true, t, e);
+      const size_t idx = (size_t)row * a.nx + x;
+      const R n1 = cabs2(ps[idx]), n2 = cabs2(ps[(size_t)a.N + idx]);
+      const R X = -a.Lx + (R)x * a.hx;
+      const R nt = n1 + n2;
+      R lh[7];
+      lhy_eta_sums<R>(nodes, a.Q, cf, n1, n2, lh);
+      s[PG_N11] += n1 * n1;
+      s[PG_N12] += n1 * n2;
+      s[PG_N22] += n2 * n2;
+      s[PG_K11] += n1 * v[0][e].x;
+      s[PG_K12] += n1 * v[0][e].y;
+      s[PG_K22] += n2 * v[0][e].y;
+      s[PG_X2] += X * X * nt;
+      s[PG_Y2] += Y * Y * nt;
+      s[PG_Z2] += Z * Z * nt;
+      s[PG_F] += lh[0];
+      s[PG_L11] += lh[1];
+      s[PG_L22] += lh[2];
+      s[PG_L12] += lh[3];
+      s[PG_M11] += lh[4];
+      s[PG_M22] += lh[5];
+      s[PG_M12] += lh[6];
+    }
+#pragma unroll
+    for (int k = 0; k < PG_NS; ++k) acc[k].add(s[k]);
+  }
+  static __device__ double* out(const KArgs<R>& a, Uni&) { return a.st->pg; }
+  static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+
+// ----------------------------------------------------------------------------
 // Split epilogues: the last x pass only inverts the workspace in place, and a
 // pointwise kernel with high occupancy evaluates the LHY quadrature, H psi and
 // the sums.  (Same arithmetic as the fused XInvEG / XInvLC epilogues; the LHY

@@ -195,4 +195,42 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
   for (int j = 0; j < NP; ++j) H[j] = R(2.5) * h[j];
 }
 
+// F and its partial derivatives with respect to the entries of
+// eta(u) = g + gdd (3u^2 - 1), summed over the u-rule (one point; the
+// parameter-derivative pass):  o[0] = F,  o[1..3] = dF/d(g11, g22, g12),
+// o[4..6] = dF/d(gdd11, gdd22, gdd12).  With V_+- = A +- s and f_+- =
+// (5/2) max(V_+-,0)^{3/2}:  dV_+-/deta11 = n1 +- delta n1/s,
+// dV_+-/deta22 = n2 -+ delta n2/s, dV_+-/deta12 = +-4 eta12 n1 n2/s (g12 = g21
+// moved together); terms / s are 0 where s = 0.
+template <class R>
+__device__ __forceinline__ void lhy_eta_sums(const LhyNode<R>* __restrict__ nd, int Q, const LhyCoef<R>& c, R n1,
+                                             R n2, R (&o)[7]) {
+#pragma unroll
+  for (int k = 0; k < 7; ++k) o[k] = R(0);
+  const LhyPt<R> p = lhy_pt(c, n1, n2);
+  for (int q = 0; q < Q; ++q) {
+    const LhyNode<R>& e = nd[q];
+    const R A = p.A0 + p.A1 * e.w;
+    const R d = p.D0 + p.D1 * e.w;
+    const R s2 = d * d + e.e12sq * p.q4;
+    R rs, s;
+    inv_s(s2, rs, s);
+    const R e12 = c.g12 + c.d12 * e.w;
+    const R vp = fmax(A + s, R(0)), vm = fmax(A - s, R(0));
+    const R rp = sqrt_pos(vp), rm = sqrt_pos(vm);
+    const R fp = R(2.5) * vp * rp, fm = R(2.5) * vm * rm;
+    o[0] += e.W * (vp * vp * rp + vm * vm * rm);
+    const R sum = fp + fm, dif = fp - fm;
+    const R t11 = sum * n1 + dif * d * n1 * rs;
+    const R t22 = sum * n2 - dif * d * n2 * rs;
+    const R t12 = dif * R(4) * e12 * n1 * n2 * rs;
+    o[1] += e.W * t11;
+    o[2] += e.W * t22;
+    o[3] += e.W * t12;
+    o[4] += e.Ww * t11;
+    o[5] += e.Ww * t22;
+    o[6] += e.Ww * t12;
+  }
+}
+
 }  // namespace egpe

@@ -20,6 +20,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device mem
           5: "not converged", 6: "stagnated", 7: "timeout", 8: "unsupported"}
 EGPE_FP64, EGPE_FP32, EGPE_MIXED = 0, 1, 2
 PRECOND = {"none": 0, "kinetic": 1, "diagonal": 2, "kinetic+diagonal": 3}
+# order of egpe_param_grad's output (EGPE_P_*)
+PARAM_NAMES = ("g11", "g12", "g22", "gdd11", "gdd12", "gdd22", "kappa", "eta_s", "trap_x", "trap_y", "trap_z")
 
 
 class egpe_grid(ct.Structure):
@@ -100,6 +102,8 @@ _SIGS = {
     "egpe_ite_solve": (ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_void_p), ct.POINTER(egpe_ite_opts),
                                   ct.POINTER(egpe_report)]),
     "egpe_default_ite_opts": (None, [ct.POINTER(egpe_ite_opts)]),
+    "egpe_param_grad": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_double)]),
+    "egpe_set_params": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(egpe_params)]),
     "egpe_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int,
                                  ct.POINTER(egpe_tuning), ct.c_int, ct.POINTER(ct.c_int)]),
     "egpe_set_tuning": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(egpe_tuning), ct.c_int]),
@@ -304,6 +308,17 @@ def egpe_ite_solve(h: int, psis, opts: egpe_ite_opts, n_inst: int = 1):
     if status in (1, 2, 3):
         raise EgpeError("egpe_ite_solve", status)
     return status, [_report_dict(r) for r in reps]
+
+
+def egpe_param_grad(h: int, inst: int, psi) -> dict:
+    """dE/dp at fixed psi for p in PARAM_NAMES."""
+    out = (ct.c_double * len(PARAM_NAMES))()
+    _check("egpe_param_grad", load().egpe_param_grad(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), out))
+    return {k: out[i] for i, k in enumerate(PARAM_NAMES)}
+
+
+def egpe_set_params(h: int, inst: int, params: egpe_params) -> None:
+    _check("egpe_set_params", load().egpe_set_params(ct.c_void_p(h), inst, ct.byref(params)))
 
 
 def egpe_autotune(h: int, inst: int, engine: int, psi, precond: int, reps: int = 5, cap: int = 64):
