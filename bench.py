@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-ite", action="store_true", help="skip the NCG-vs-ITE comparison on the 64^3 workload")
     ap.add_argument("--no-scan", action="store_true", help="skip the 64-instance parameter scan")
     ap.add_argument("--no-tune", action="store_true", help="untuned launch shapes (no autotuning)")
+    ap.add_argument("--no-cont", action="store_true", help="skip continuation along the scan")
     ap.add_argument("--fp32-switch", type=float, default=1e-4)
     return ap.parse_args()
 
@@ -345,6 +346,12 @@ def run_ours(args):
             scan = scan_benchmark(E, tune=not args.no_tune)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             scan = {"error": str(ex)[:300]}
+    cont = None
+    if not args.no_cont:
+        try:
+            cont = continuation_benchmark(E, tune=not args.no_tune)
+        except Exception as ex:  # reported, not fatal for the iteration numbers
+            cont = {"error": str(ex)[:300]}
     clk = clocks.stop()
     E.egpe_destroy(h)
 
@@ -364,7 +371,7 @@ def run_ours(args):
                            "step": "one NCG attempt (precondition + line coefficients + trial E/grad + controller)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launch32,
                 "clocks": clk, "fp64": fp64, "time_to_ground_state": tts, "ncg_vs_ite": ite,
-                "scan": scan, "autotune": tuning}
+                "scan": scan, "continuation": cont, "autotune": tuning}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -522,6 +529,87 @@ def scan_benchmark(E, tol_res=1e-6, fp32_switch=1e-4, tune=True):
                      "worse_than_best": {str(i): x for i, x in enumerate(d) if x > 1e-8},
                      "all_converged": all(r["status"] == 0 for r in reps)}
     out["speedup_mixed_batched_vs_fp64_one_by_one"] = round(runs["fp64_one_by_one"][0] / runs["mixed_batched"][0], 3)
+    return out
+
+
+def continuation_benchmark(E, tol_res=1e-6, tune=True):
+    """Continuation along the 64-instance scan (the paper's proposal for
+    phase-diagram sweeps): per grid size, the 16 parameter points are chained
+    nearest-neighbour in the normalised (g12, g_dd) plane and solved with
+    egpe_ncg_continuation (each solve warm-started from the previous ground
+    state), against cold solves of the same points from their seeded starts;
+    mixed precision, P_Delta o P_V, ||r|| < tol_res."""
+    import torch
+
+    from paper_2510_24543_gb300 import autotune as AT
+    from paper_2510_24543_gb300 import inputs as I
+
+    ws = I.scan_workloads()
+    device = torch.cuda.get_device_name()
+    out = {"instances": len(ws), "tol_res": tol_res, "groups": []}
+    tot = {"cold_s": 0.0, "warm_s": 0.0, "cold_iters": 0, "warm_iters": 0}
+    same = lower = higher = 0
+    for size in (48, 64, 80, 96):
+        grp = [w for w in ws if w.n[0] == size]
+        pts = [((w.g[0][1] - 100.0) / 250.0, (w.gdd[0][0] - 250.0) / 200.0) for w in grp]
+        order, left = [min(range(len(grp)), key=lambda i: pts[i][0])], set(range(len(grp)))
+        left.discard(order[0])
+        while left:
+            last = pts[order[-1]]
+            nxt = min(left, key=lambda i: (pts[i][0] - last[0]) ** 2 + (pts[i][1] - last[1]) ** 2)
+            order.append(nxt)
+            left.discard(nxt)
+        path = [grp[i] for i in order]
+        prms = [E.params_from_workload(w) for w in path]
+        h = E.egpe_create([E.make_grid(path[0].n, path[0].L)], [prms[0]], E.EGPE_MIXED)
+        try:
+            if tune:
+                AT.tune_handle(h, [path[0].n], E.EGPE_MIXED, E.PRECOND[path[0].precond],
+                               lambda i, e: torch.from_numpy(I.gaussian_start(path[0])).to("cuda").to(
+                                   torch.complex128 if e == 0 else torch.complex64), device)
+            o = E.egpe_default_solve_opts()
+            o.precond = E.PRECOND[path[0].precond]
+            o.tol_res = tol_res
+            o.max_iter = 6000
+            o.max_iter_fp32 = 6000
+            cold = []
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for w, p in zip(path, prms):
+                E.egpe_set_params(h, 0, p)
+                x = torch.from_numpy(I.gaussian_start(w)).to("cuda")
+                st, reps, _ = E.egpe_ncg_solve(h, [x], o, 1)
+                cold.append(reps[0])
+            torch.cuda.synchronize()
+            t_cold = time.perf_counter() - t0
+            x = torch.from_numpy(I.gaussian_start(path[0])).to("cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, warm = E.egpe_ncg_continuation(h, 0, prms, x, o)
+            torch.cuda.synchronize()
+            t_warm = time.perf_counter() - t0
+        finally:
+            E.egpe_destroy(h)
+        for c, wr in zip(cold, warm):
+            best = min(c["E"], wr["E"])
+            dc, dw = (c["E"] - best) / abs(best), (wr["E"] - best) / abs(best)
+            if dc <= 1e-8 and dw <= 1e-8:
+                same += 1
+            elif dw <= 1e-8:
+                lower += 1
+            else:
+                higher += 1
+        g = {"grid": size, "cold_s": round(t_cold, 3), "warm_s": round(t_warm, 3),
+             "cold_iters": sum(r["iters"] for r in cold), "warm_iters": sum(r["iters"] for r in warm),
+             "all_converged": all(r["status"] == 0 for r in cold + warm)}
+        out["groups"].append(g)
+        for k in tot:
+            tot[k] += g[k]
+    out.update({k: round(v, 3) if isinstance(v, float) else v for k, v in tot.items()})
+    out["speedup"] = round(tot["cold_s"] / tot["warm_s"], 3)
+    out["points_same_minimum"] = same
+    out["points_warm_lower"] = lower
+    out["points_warm_higher"] = higher
     return out
 
 

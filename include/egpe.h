@@ -335,6 +335,18 @@ egpe_status egpe_ite_solve(egpe_handle* h, void* const* psi_inout, const egpe_it
  * device pointers. */
 void egpe_default_ite_opts(egpe_ite_opts* o);
 
+/* Numerical continuation (named by the paper as the extension for
+ * phase-diagram sweeps, Sec. VII): ground states of instance inst along a path
+ * of parameter sets path[0..npoints) on its grid, each solve (as in
+ * egpe_ncg_solve with opts) started from the previous ground state.
+ * psi_inout: the start of the first solve; receives the last ground state.
+ * psi_out: NULL, or npoints pointers (entries may be NULL) that receive each
+ * point's ground state (same memory kind as psi_inout).  reports: host array
+ * of npoints or NULL.  The instance keeps the last point's parameters.
+ * Returns the first failing point's status (the path continues past it). */
+egpe_status egpe_ncg_continuation(egpe_handle* h, int inst, const egpe_params* path, int npoints, void* psi_inout,
+                                  void* const* psi_out, const egpe_solve_opts* opts, egpe_report* reports);
+
 /* Stepping interface: the phases of egpe_ncg_solve one by one, for callers
  * that interleave their own work (event timing, checkpoints) with the solver.
  * engine: 0 the FP64 path (psi complex128), 1 the FP32 path (psi complex64;

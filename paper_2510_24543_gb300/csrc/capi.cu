@@ -501,6 +501,82 @@ egpe_status ncg_solve_batched(egpe_handle* h, void* const* psi_inout, const egpe
   return first_bad;
 }
 
+// One instance, one precision path (FP64, FP32, or MIXED: FP32 phase then
+// FP64 polish), from psi (device or host per o.psi_on_host) back into psi.
+egpe_status solve_one(egpe_handle* h, int i, void* psi, const egpe_solve_opts& o, egpe_trace_entry* tr, int tcap,
+                      egpe_report& rep) {
+  const auto t0 = std::chrono::steady_clock::now();
+  std::memset(&rep, 0, sizeof(rep));
+  egpe::SolveRun run{};
+  egpe_status s = EGPE_OK;
+  const cudaMemcpyKind kin = o.psi_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind kout = o.psi_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (h->prec == EGPE_FP64) {
+    auto* e = h->e64[i];
+    s = e->load_psi(psi, kin);
+    if (s == EGPE_OK) s = e->solve(o, 0, o.max_iter, o.tol_res, o.accept_rtol, run, tr, tcap, 0);
+    if (s == EGPE_OK) s = e->store_psi(psi, kout);
+  } else if (h->prec == EGPE_FP32) {
+    auto* e = h->e32[i];
+    s = e->load_psi(psi, kin);
+    if (s == EGPE_OK) s = e->solve(o, 1, o.max_iter, o.tol_res, o.accept_rtol_fp32, run, tr, tcap, 0);
+    if (s == EGPE_OK) s = e->store_psi(psi, kout);
+  } else {  // MIXED: FP32 phase, then FP64 polish
+    auto* e64 = h->e64[i];
+    auto* e32 = h->e32[i];
+    s = e64->load_psi(psi, kin);
+    const size_t n2 = 2 * e64->N;
+    if (s == EGPE_OK) {
+      cast_d2f<<<256, 256, 0, h->stream>>>(n2, (const double2*)e64->psi_slot0(), e32->psi_slot0());
+      if (cudaGetLastError() != cudaSuccess) s = EGPE_ERR_CUDA;
+    }
+    egpe::SolveRun r32{};
+    if (s == EGPE_OK)
+      s = e32->solve(o, 1, o.max_iter_fp32, std::max(o.tol_res, o.tol_fp32_switch), o.accept_rtol_fp32, r32, tr,
+                     tcap, 0);
+    if (s == EGPE_OK) {
+      cast_f2d<<<256, 256, 0, h->stream>>>(n2, e32->current_psi(), e64->psi_slot0());
+      if (cudaGetLastError() != cudaSuccess) s = EGPE_ERR_CUDA;
+    }
+    if (s == EGPE_OK) s = e64->normalise_current();
+    egpe_trace_entry* tr2 = tr ? tr + r32.trace_len : nullptr;
+    const int tcap2 = tr ? std::max(0, tcap - r32.trace_len) : 0;
+    if (s == EGPE_OK)
+      s = e64->solve(o, 0, o.max_iter, o.tol_res, o.accept_rtol, run, tcap2 > 0 ? tr2 : nullptr, tcap2, 0);
+    if (s == EGPE_OK) s = e64->store_psi(psi, kout);
+    rep.iters_fp32 = r32.n;
+    run.n += r32.n;
+    run.attempts += r32.attempts;
+    run.restarts += r32.restarts;
+    run.armijo_total += r32.armijo_total;
+    run.launches += r32.launches;
+    run.ffts += r32.ffts;
+    run.kernels += r32.kernels;
+    run.trace_len += r32.trace_len;
+  }
+  const auto t1 = std::chrono::steady_clock::now();
+  if (s != EGPE_OK) {
+    rep.status = s;
+  } else {
+    rep.status = run.status;
+  }
+  rep.iters = run.n;
+  if (h->prec == EGPE_FP32) rep.iters_fp32 = run.n;
+  rep.attempts = run.attempts;
+  rep.restarts = run.restarts;
+  rep.armijo_steps = run.armijo_total;
+  rep.trace_len = run.trace_len;
+  rep.graph_launches = run.launches;
+  rep.E = run.E;
+  rep.mu[0] = run.mu[0];
+  rep.mu[1] = run.mu[1];
+  rep.res = run.res;
+  rep.seconds = std::chrono::duration<double>(t1 - t0).count();
+  rep.ffts = run.ffts;
+  rep.kernels = run.kernels;
+  return s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -519,80 +595,49 @@ egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_so
   egpe_status first_bad = EGPE_OK;
   egpe_trace_entry* trace = (egpe_trace_entry*)o.trace;
   for (int i = 0; i < h->n_inst; ++i) {
-    const auto t0 = std::chrono::steady_clock::now();
     egpe_report rep;
-    std::memset(&rep, 0, sizeof(rep));
-    egpe::SolveRun run{};
-    egpe_status s = EGPE_OK;
-    const cudaMemcpyKind kin = o.psi_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    const cudaMemcpyKind kout = o.psi_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    egpe_trace_entry* tr = (i == 0) ? trace : nullptr;  // trace follows the first instance
-    int tcap = (i == 0) ? o.trace_cap : 0;
-    if (h->prec == EGPE_FP64) {
-      auto* e = h->e64[i];
-      s = e->load_psi(psi_inout[i], kin);
-      if (s == EGPE_OK) s = e->solve(o, 0, o.max_iter, o.tol_res, o.accept_rtol, run, tr, tcap, 0);
-      if (s == EGPE_OK) s = e->store_psi(psi_inout[i], kout);
-    } else if (h->prec == EGPE_FP32) {
-      auto* e = h->e32[i];
-      s = e->load_psi(psi_inout[i], kin);
-      if (s == EGPE_OK) s = e->solve(o, 1, o.max_iter, o.tol_res, o.accept_rtol_fp32, run, tr, tcap, 0);
-      if (s == EGPE_OK) s = e->store_psi(psi_inout[i], kout);
-    } else {  // MIXED: FP32 phase, then FP64 polish
-      auto* e64 = h->e64[i];
-      auto* e32 = h->e32[i];
-      s = e64->load_psi(psi_inout[i], kin);
-      const size_t n2 = 2 * e64->N;
-      if (s == EGPE_OK) {
-        cast_d2f<<<256, 256, 0, h->stream>>>(n2, (const double2*)e64->psi_slot0(), e32->psi_slot0());
-        if (cudaGetLastError() != cudaSuccess) s = EGPE_ERR_CUDA;
-      }
-      egpe::SolveRun r32{};
-      if (s == EGPE_OK)
-        s = e32->solve(o, 1, o.max_iter_fp32, std::max(o.tol_res, o.tol_fp32_switch), o.accept_rtol_fp32, r32, tr,
-                       tcap, 0);
-      if (s == EGPE_OK) {
-        cast_f2d<<<256, 256, 0, h->stream>>>(n2, e32->current_psi(), e64->psi_slot0());
-        if (cudaGetLastError() != cudaSuccess) s = EGPE_ERR_CUDA;
-      }
-      if (s == EGPE_OK) s = e64->normalise_current();
-      egpe_trace_entry* tr2 = tr ? tr + r32.trace_len : nullptr;
-      const int tcap2 = tr ? std::max(0, tcap - r32.trace_len) : 0;
-      if (s == EGPE_OK)
-        s = e64->solve(o, 0, o.max_iter, o.tol_res, o.accept_rtol, run, tcap2 > 0 ? tr2 : nullptr, tcap2, 0);
-      if (s == EGPE_OK) s = e64->store_psi(psi_inout[i], kout);
-      rep.iters_fp32 = r32.n;
-      run.n += r32.n;
-      run.attempts += r32.attempts;
-      run.restarts += r32.restarts;
-      run.armijo_total += r32.armijo_total;
-      run.launches += r32.launches;
-      run.ffts += r32.ffts;
-      run.kernels += r32.kernels;
-      run.trace_len += r32.trace_len;
-    }
-    const auto t1 = std::chrono::steady_clock::now();
-    if (s != EGPE_OK) {
-      rep.status = s;
-    } else {
-      rep.status = run.status;
-    }
-    rep.iters = run.n;
-    if (h->prec == EGPE_FP32) rep.iters_fp32 = run.n;
-    rep.attempts = run.attempts;
-    rep.restarts = run.restarts;
-    rep.armijo_steps = run.armijo_total;
-    rep.trace_len = run.trace_len;
-    rep.graph_launches = run.launches;
-    rep.E = run.E;
-    rep.mu[0] = run.mu[0];
-    rep.mu[1] = run.mu[1];
-    rep.res = run.res;
-    rep.seconds = std::chrono::duration<double>(t1 - t0).count();
-    rep.ffts = run.ffts;
-    rep.kernels = run.kernels;
+    // the trace follows the first instance
+    const egpe_status s = solve_one(h, i, psi_inout[i], o, i == 0 ? trace : nullptr, i == 0 ? o.trace_cap : 0, rep);
     if (reports) reports[i] = rep;
     if (s != EGPE_OK) return s;
+    if (rep.status != EGPE_OK && first_bad == EGPE_OK) first_bad = (egpe_status)rep.status;
+  }
+  return first_bad;
+}
+
+egpe_status egpe_ncg_continuation(egpe_handle* h, int inst, const egpe_params* path, int npoints, void* psi_inout,
+                                  void* const* psi_out, const egpe_solve_opts* opts, egpe_report* reports) {
+  if (bad_inst(h, inst) || !path || npoints < 1 || !psi_inout || !opts) return EGPE_ERR_INVALID_ARG;
+  const egpe_solve_opts& o = *opts;
+  if (!opts_ok(o)) {
+    egpe::set_error_msg("egpe_ncg_continuation: bad options");
+    return EGPE_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < npoints; ++k) {
+    const egpe_status v = validate(h->grids[inst], path[k]);
+    if (v != EGPE_OK) return v;
+  }
+  const size_t bytes = 2 * (h->prec == EGPE_FP32 ? h->e32[inst]->N * sizeof(float2) : h->e64[inst]->N * sizeof(double2));
+  egpe_status first_bad = EGPE_OK;
+  for (int k = 0; k < npoints; ++k) {
+    egpe_status s = egpe_set_params(h, inst, &path[k]);
+    if (s != EGPE_OK) return s;
+    egpe_report rep;
+    s = solve_one(h, inst, psi_inout, o, nullptr, 0, rep);  // warm start: psi_inout holds the last state
+    if (reports) reports[k] = rep;
+    if (s != EGPE_OK) return s;
+    if (psi_out && psi_out[k]) {
+      if (o.psi_on_host) {
+        std::memcpy(psi_out[k], psi_inout, bytes);
+      } else {
+        cudaError_t e = cudaMemcpyAsync(psi_out[k], psi_inout, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+          egpe::set_error("egpe_ncg_continuation copy", e);
+          return EGPE_ERR_CUDA;
+        }
+      }
+    }
     if (rep.status != EGPE_OK && first_bad == EGPE_OK) first_bad = (egpe_status)rep.status;
   }
   return first_bad;

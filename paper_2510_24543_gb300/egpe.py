@@ -103,6 +103,9 @@ _SIGS = {
                                   ct.POINTER(egpe_report)]),
     "egpe_default_ite_opts": (None, [ct.POINTER(egpe_ite_opts)]),
     "egpe_param_grad": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_void_p, ct.POINTER(ct.c_double)]),
+    "egpe_ncg_continuation": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(egpe_params), ct.c_int, ct.c_void_p,
+                                         ct.POINTER(ct.c_void_p), ct.POINTER(egpe_solve_opts),
+                                         ct.POINTER(egpe_report)]),
     "egpe_set_params": (ct.c_int, [ct.c_void_p, ct.c_int, ct.POINTER(egpe_params)]),
     "egpe_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int,
                                  ct.POINTER(egpe_tuning), ct.c_int, ct.POINTER(ct.c_int)]),
@@ -307,6 +310,22 @@ def egpe_ite_solve(h: int, psis, opts: egpe_ite_opts, n_inst: int = 1):
     status = lib.egpe_ite_solve(ct.c_void_p(h), ptrs, ct.byref(opts), reps)
     if status in (1, 2, 3):
         raise EgpeError("egpe_ite_solve", status)
+    return status, [_report_dict(r) for r in reps]
+
+
+def egpe_ncg_continuation(h: int, inst: int, path, psi, opts: egpe_solve_opts, psi_out=None):
+    """Ground states along a parameter path (list of egpe_params), each solve
+    warm-started from the previous one.  Returns (status, [report dicts])."""
+    n = len(path)
+    P = (egpe_params * n)(*path)
+    outs = None
+    if psi_out is not None:
+        outs = (ct.c_void_p * n)(*[ct.c_void_p(_ptr(x)) for x in psi_out])
+    reps = (egpe_report * n)()
+    status = load().egpe_ncg_continuation(ct.c_void_p(h), inst, P, n, ct.c_void_p(_ptr(psi)), outs, ct.byref(opts),
+                                          reps)
+    if status in (1, 2, 3):
+        raise EgpeError("egpe_ncg_continuation", status)
     return status, [_report_dict(r) for r in reps]
 
 
