@@ -26,7 +26,7 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-PRECOND_MODES = {"none": 0, "kinetic": 1, "diagonal": 2, "kinetic+diagonal": 3}
+PRECOND_MODES = {"none": 0, "kinetic": 1, "diagonal": 2, "kinetic+diagonal": 3, "blend": 4}
 
 
 # ----------------------------------------------------------------------------
@@ -397,7 +397,7 @@ def preconditioner_shift(grid: Grid, ev: Evaluation, psi: np.ndarray) -> np.ndar
 
 
 def precondition(grid: Grid, prm: Params, ev: Evaluation, psi: np.ndarray, r: np.ndarray,
-                 mode: str, pv_floor: float = 1e-2) -> np.ndarray:
+                 mode: str, pv_floor: float = 1e-2, blend: float = 0.5) -> np.ndarray:
     """z = P^{-1} r with P^{-1} = P_Delta^{-1} P_V^{-1} (Sec. IV.B, composition formula).
 
     P_V,i(r) = max(|alpha_i| + V + sum_j g_ij n_j + mu_LHY^(i), pv_floor |alpha_i|):
@@ -407,9 +407,16 @@ def precondition(grid: Grid, prm: Params, ev: Evaluation, psi: np.ndarray, r: np
     positive kinetic operator).  Mode "none" returns r; "kinetic" applies P_Delta
     only; "diagonal" P_V only; "kinetic+diagonal" P_V first, then P_Delta, as the
     composition formula is written.  |alpha_i| keeps both operators positive.
+    Mode "blend" is the weighted combination the paper names as possible (Sec.
+    IV.B) and as an extension (Sec. VII), read as the convex combination
+    z = blend P_V^{-1} r + (1 - blend) P_Delta^{-1} r.
     """
     if mode not in PRECOND_MODES:
         raise ValueError(mode)
+    if mode == "blend":
+        zv = precondition(grid, prm, ev, psi, r, "diagonal", pv_floor)
+        zd = precondition(grid, prm, ev, psi, r, "kinetic", pv_floor)
+        return blend * zv + (1.0 - blend) * zd
     alpha = np.abs(preconditioner_shift(grid, ev, psi))
     z = r.astype(np.complex128).copy()
     n = ev.n
@@ -465,6 +472,7 @@ class SolveOpts:
     accept_rtol: float = 1e-13     # round-off allowance: accept if E_t < E + accept_rtol |E|
     pv_floor: float = 1e-2
     beta_rule: str = "HS"          # "HS" (Hestenes-Stiefel+) or "PR" (Polak-Ribiere+)
+    blend: float = 0.5             # weight of P_V in the "blend" preconditioner
 
 
 def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = SolveOpts(),
@@ -514,7 +522,7 @@ def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = Solve
         if n_it >= opts.max_iter:
             status = "not_converged"
             break
-        z = precondition(grid, prm, ev, psi, r, opts.precond, opts.pv_floor)
+        z = precondition(grid, prm, ev, psi, r, opts.precond, opts.pv_floor, opts.blend)
         restart = (n_it % opts.restart_period == 0) or p_prev is None
         beta = 0.0
         rz = sum(inner(grid, r[i], z[i]).real for i in range(2))

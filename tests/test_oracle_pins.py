@@ -527,3 +527,30 @@ def test_hellmann_feynman_at_a_ground_state():
         Em = O.ncg_solve(g, _with_param(prm, name, p0 - h), psi, opts)[1]["E"]
         fd = (Ep - Em) / (2 * h)
         assert abs(fd - d[name]) < 1e-6 * max(1.0, abs(d[name])), name
+
+
+# ---------------------------------------------------------------- blended preconditioner
+def test_blend_limits_and_same_minimum():
+    """The weighted combination reduces to P_V (weight 1) and P_Delta (weight
+    0), is positive definite (Re<r, z> > 0), and the solver reaches the same
+    minimum with it as with P_Delta alone."""
+    w = _cm.mixed_workload((12, 10, 16))
+    g, prm = _cm.oracle_case(w)
+    psi = I.random_state(w.n, w.L, 8, width=(1.2, 1.5, 0.9))
+    ev = O.evaluate(g, prm, psi)
+    r = I.random_fields(psi.shape, 9)
+    zv = O.precondition(g, prm, ev, psi, r, "diagonal")
+    zd = O.precondition(g, prm, ev, psi, r, "kinetic")
+    assert np.array_equal(O.precondition(g, prm, ev, psi, r, "blend", blend=1.0), zv)
+    assert np.array_equal(O.precondition(g, prm, ev, psi, r, "blend", blend=0.0), zd)
+    zb = O.precondition(g, prm, ev, psi, r, "blend", blend=0.3)
+    for i in range(2):
+        assert O.inner(g, r[i], zb[i]).real > 0
+    w2 = I.Workload("bl", (16, 16, 16), (6.0, 6.0, 6.0), (1.0, 1.0, 1.5), ((60.0, 25.0), (25.0, 50.0)),
+                    ((40.0, 20.0), (20.0, 30.0)), 10.0, 7, "kinetic", 8)
+    g2, prm2 = _cm.oracle_case(w2)
+    psi0 = I.gaussian_start(w2)
+    _, ra = O.ncg_solve(g2, prm2, psi0, O.SolveOpts(precond="kinetic", tol_res=1e-10))
+    _, rb = O.ncg_solve(g2, prm2, psi0, O.SolveOpts(precond="blend", blend=0.5, tol_res=1e-10))
+    assert ra["status"] == rb["status"] == "converged"
+    assert abs(ra["E"] - rb["E"]) < 1e-12 * abs(ra["E"])
