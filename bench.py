@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-scan", action="store_true", help="skip the 64-instance parameter scan")
     ap.add_argument("--no-tune", action="store_true", help="untuned launch shapes (no autotuning)")
     ap.add_argument("--no-cont", action="store_true", help="skip continuation along the scan")
+    ap.add_argument("--no-pcstudy", action="store_true", help="skip the preconditioner study")
     ap.add_argument("--fp32-switch", type=float, default=1e-4)
     return ap.parse_args()
 
@@ -346,6 +347,12 @@ def run_ours(args):
             scan = scan_benchmark(E, tune=not args.no_tune)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             scan = {"error": str(ex)[:300]}
+    pcs = None
+    if not args.no_pcstudy:
+        try:
+            pcs = precond_study(E)
+        except Exception as ex:  # reported, not fatal for the iteration numbers
+            pcs = {"error": str(ex)[:300]}
     cont = None
     if not args.no_cont:
         try:
@@ -371,7 +378,8 @@ def run_ours(args):
                            "step": "one NCG attempt (precondition + line coefficients + trial E/grad + controller)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launch32,
                 "clocks": clk, "fp64": fp64, "time_to_ground_state": tts, "ncg_vs_ite": ite,
-                "scan": scan, "continuation": cont, "autotune": tuning}
+                "scan": scan, "continuation": cont,
+                "precond_study": pcs, "autotune": tuning}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -529,6 +537,41 @@ def scan_benchmark(E, tol_res=1e-6, fp32_switch=1e-4, tune=True):
                      "worse_than_best": {str(i): x for i, x in enumerate(d) if x > 1e-8},
                      "all_converged": all(r["status"] == 0 for r in reps)}
     out["speedup_mixed_batched_vs_fp64_one_by_one"] = round(runs["fp64_one_by_one"][0] / runs["mixed_batched"][0], 3)
+    return out
+
+
+def precond_study(E, tol_res=1e-6, per_grid=4):
+    """Iterations and time to ||r|| < tol_res per preconditioner (Sec. IV.B and
+    the paper's Fig. 1a/b comparison of P_V and P_Delta, here on synthetic scan
+    instances): 4 instances of each scan grid, FP64, solved together."""
+    import torch
+
+    from paper_2510_24543_gb300 import inputs as I
+
+    scan = I.scan_workloads()
+    ws = [scan[16 * g + k] for g in range(4) for k in range(per_grid)]
+    grids = [E.make_grid(w.n, w.L) for w in ws]
+    prms = [E.params_from_workload(w) for w in ws]
+    out = {"instances": len(ws), "tol_res": tol_res, "precision": "fp64", "modes": {}}
+    for mode in ("kinetic", "diagonal", "kinetic+diagonal", "blend"):
+        h = E.egpe_create(grids, prms, E.EGPE_FP64)
+        try:
+            o = E.egpe_default_solve_opts()
+            o.precond = E.PRECOND[mode]
+            o.tol_res = tol_res
+            o.max_iter = 6000
+            o.pc_blend = 0.5
+            xs = [torch.from_numpy(I.gaussian_start(w)).to("cuda") for w in ws]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, reps, _ = E.egpe_ncg_solve(h, xs, o, len(ws))
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+        finally:
+            E.egpe_destroy(h)
+        its = sorted(r["iters"] for r in reps)
+        out["modes"][mode] = {"seconds": round(secs, 3), "iters_total": sum(its), "iters_median": its[len(its) // 2],
+                              "iters_max": its[-1], "converged": sum(r["status"] == 0 for r in reps)}
     return out
 
 

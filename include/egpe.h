@@ -66,7 +66,10 @@ enum {
   EGPE_PRECOND_NONE = 0,            /* z = r                                  */
   EGPE_PRECOND_KINETIC = 1,         /* z = P_Delta^{-1} r                     */
   EGPE_PRECOND_DIAGONAL = 2,        /* z = P_V^{-1} r                         */
-  EGPE_PRECOND_KINETIC_DIAGONAL = 3 /* z = P_Delta^{-1} P_V^{-1} r (formula order) */
+  EGPE_PRECOND_KINETIC_DIAGONAL = 3, /* z = P_Delta^{-1} P_V^{-1} r (formula order) */
+  EGPE_PRECOND_BLEND = 4             /* z = w P_V^{-1} r + (1-w) P_Delta^{-1} r, w = pc_blend
+                                        (the weighted combination of Sec. IV.B; 0.5 in
+                                        egpe_precondition)                  */
 };
 
 /* Periodic box [-L_a, L_a), n_a points per axis (a = x, y, z). */
@@ -137,6 +140,7 @@ typedef struct {
   int stall_iters_fp32;     /* FP32 fields (FP32 handles, MIXED's FP32 phase): stop
                                when the best ||r|| has not dropped by 10% within this
                                many iterations (its round-off floor); 0: off       */
+  double pc_blend;          /* EGPE_PRECOND_BLEND: weight w of P_V, in [0, 1]       */
 } egpe_solve_opts;
 
 /* One attempted step of the solver (accepted or rejected). */

@@ -43,7 +43,7 @@ template <class R> class BatchRunner {
     std::vector<int> phase;
     EGPE_TRY(gather(phase));
     std::vector<int> active = live(phase);
-    const int mode = o.precond & 3;
+    const int mode = o.precond;
     const int poll = std::max(1, o.poll_every);
     const long long max_launch = (long long)(max_iter + 2) * (long long)(o.armijo_max + 2) + 4;
     long long replays = 0, kernels = 0;

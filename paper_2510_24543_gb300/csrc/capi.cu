@@ -151,6 +151,7 @@ void egpe_default_solve_opts(egpe_solve_opts* o) {
   o->trace = nullptr;
   o->batch = 1;
   o->stall_iters_fp32 = 0;
+  o->pc_blend = 0.5;
 }
 
 egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n_inst, egpe_precision prec,
@@ -245,7 +246,7 @@ egpe_status egpe_line_coeffs(egpe_handle* h, int inst, const void* psi, const vo
 }
 
 egpe_status egpe_precondition(egpe_handle* h, int inst, int mode, const void* psi, const void* r, void* z) {
-  if (bad_inst(h, inst) || !psi || !z || mode < 0 || mode > 3) return EGPE_ERR_INVALID_ARG;
+  if (bad_inst(h, inst) || !psi || !z || mode < 0 || mode > 4) return EGPE_ERR_INVALID_ARG;
   if (h->prec == EGPE_FP32)
     return h->e32[inst]->precondition(mode, (const float2*)psi, (const float2*)r, (float2*)z);
   return h->e64[inst]->precondition(mode, (const double2*)psi, (const double2*)r, (double2*)z);
@@ -268,7 +269,7 @@ egpe_status egpe_fft(egpe_handle* h, int inst, const void* in, void* out, int nf
 
 egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
                                  int cap, char* names, double* ms, double* bytes, int* count) {
-  if (bad_inst(h, inst) || !psi || precond < 0 || precond > 3 || reps < 1 || cap < 1 || !names || !ms || !bytes ||
+  if (bad_inst(h, inst) || !psi || precond < 0 || precond > 4 || reps < 1 || cap < 1 || !names || !ms || !bytes ||
       !count)
     return EGPE_ERR_INVALID_ARG;
   std::vector<std::string> nm;
@@ -313,7 +314,7 @@ egpe_status egpe_set_params(egpe_handle* h, int inst, const egpe_params* params)
 
 egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
                           egpe_tuning* out, int cap, int* count) {
-  if (bad_inst(h, inst) || !psi || precond < 0 || precond > 3 || reps < 1 || cap < 0 || (cap > 0 && !out))
+  if (bad_inst(h, inst) || !psi || precond < 0 || precond > 4 || reps < 1 || cap < 0 || (cap > 0 && !out))
     return EGPE_ERR_INVALID_ARG;
   std::vector<egpe::TuneResult> res;
   egpe_status s;
@@ -350,7 +351,7 @@ egpe_status egpe_set_tuning(egpe_handle* h, int inst, int engine, const egpe_tun
 }
 
 static bool opts_ok(const egpe_solve_opts& o) {
-  return !(o.precond < 0 || o.precond > 3 || o.beta_rule < 0 || o.beta_rule > 1 || o.max_iter < 0 || o.armijo_max < 0 ||
+  return !(o.precond < 0 || o.precond > 4 || !(o.pc_blend >= 0.0 && o.pc_blend <= 1.0) || o.beta_rule < 0 || o.beta_rule > 1 || o.max_iter < 0 || o.armijo_max < 0 ||
            o.armijo_max > 60 || !(o.tol_res >= 0.0) || !(o.theta_max > 0.0) || !(o.pv_floor > 0.0) ||
            o.trace_cap < 0 || (o.trace_cap > 0 && !o.trace) || o.stall_iters_fp32 < 0);
 }

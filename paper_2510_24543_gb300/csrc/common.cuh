@@ -63,7 +63,7 @@ enum Gate { GATE_ALWAYS = 0, GATE_NEW_ITER = 1, GATE_ACTIVE = 2 };
 
 struct SolveOptsDev {
   int precond, restart_period, max_iter, armijo_max, trace_cap, fp32_phase, beta_rule, stall_iters;
-  double tol_res, tol_dE, armijo_c1, theta_max, accept_rtol, pv_floor;
+  double tol_res, tol_dE, armijo_c1, theta_max, accept_rtol, pv_floor, pc_blend;
 };
 
 struct TraceDev {

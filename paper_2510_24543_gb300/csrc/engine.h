@@ -212,10 +212,10 @@ template <class R> class Engine {
   int Qm_ = 0;  // LHY nodes with det eta > 0 (stored first)
   long long kernels_ = 0;
   std::unordered_map<unsigned long long, int> occ_;
-  cudaGraphExec_t graph_[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t graph_[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int run_mode_ = 0, run_graph_ = 1;
   long long run_k0_ = 0, run_launches_ = 0, per_attempt_ = 0;
-  int graph_max_iter_[4] = {0, 0, 0, 0};
+  int graph_max_iter_[5] = {0, 0, 0, 0, 0};
   R* kin_tab_ = nullptr;            // ITE kinetic half-step factors and dtau
   std::vector<R> kin_host_;
   cudaGraphExec_t graph_ite_ = nullptr;

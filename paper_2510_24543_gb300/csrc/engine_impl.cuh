@@ -379,7 +379,7 @@ egpe_status Engine<R>::profile_attempt(const C* psi, int precond, int reps, std:
                                        std::vector<double>& ms, std::vector<double>& bytes) {
   egpe_solve_opts o;
   std::memset(&o, 0, sizeof(o));
-  o.precond = precond & 3;
+  o.precond = precond;
   o.restart_period = 20;
   o.armijo_max = 30;
   o.armijo_c1 = 1e-4;
@@ -462,7 +462,7 @@ egpe_status Engine<R>::autotune(const C* psi, int precond, int reps, std::vector
   reps = std::max(1, reps);
   egpe_solve_opts o;
   std::memset(&o, 0, sizeof(o));
-  o.precond = precond & 3;
+  o.precond = precond;
   o.restart_period = 20;
   o.armijo_max = 30;
   o.armijo_c1 = 1e-4;
@@ -785,11 +785,12 @@ template <class R> egpe_status Engine<R>::enq_pc(int mode, int gate, int ctrl, i
   KArgs<R> a = *base_;
   a.gate = gate;
   a.flag = rgiven;
-  a.diag = (mode & 2) ? 1 : 0;
+  a.diag = (mode == 2 || mode == 3) ? 1 : 0;
+  a.blend = mode == 4 ? 1 : 0;
   a.ctrl = 0;
   a.nf = 2;
   a.f0 = 0;
-  if (mode & 1) {
+  if (mode == 1 || mode == 3 || mode == 4) {
     EGPE_TRY(dispatch_x<XFwdPC>(nx, a));
     KArgs<R> y = a;
     y.gin = a.W;
@@ -848,6 +849,7 @@ egpe_status Engine<R>::reset_state(const egpe_solve_opts* o, int fp32_phase, int
   h.dV = dV;
   h.invN = 1.0 / (double)N;
   h.opt.pv_floor = 1e-2;
+  h.opt.pc_blend = 0.5;
   h.opt.armijo_c1 = 1e-4;
   h.opt.theta_max = 1.5707963267948966;
   h.opt.restart_period = 20;
@@ -865,6 +867,7 @@ egpe_status Engine<R>::reset_state(const egpe_solve_opts* o, int fp32_phase, int
     h.opt.theta_max = o->theta_max;
     h.opt.accept_rtol = accept_rtol;
     h.opt.pv_floor = o->pv_floor;
+    h.opt.pc_blend = o->pc_blend;
     h.opt.stall_iters = fp32_phase ? o->stall_iters_fp32 : 0;
   }
   EGPE_CUDA(cudaMemcpyAsync(st_, &h, sizeof(DevState), cudaMemcpyHostToDevice, stream));
@@ -998,7 +1001,7 @@ template <class R> egpe_status Engine<R>::store_psi(void* dst, cudaMemcpyKind ki
 template <class R>
 egpe_status Engine<R>::solve_begin(const egpe_solve_opts& o, int fp32_phase, int max_iter, double tol_res,
                                    double accept_rtol, bool want_trace, int trace_cap) {
-  const int mode = o.precond & 3;
+  const int mode = o.precond;
   if (want_trace && trace_cap > trace_alloc_) {
     // the trace buffer is captured by the graphs: allocate once, generously
     const int want = std::max(trace_cap, 65536);

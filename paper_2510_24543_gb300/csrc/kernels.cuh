@@ -62,6 +62,7 @@ template <class R> struct KArgs {
   int flag;                  // op-specific (trial / r given / p given)
   int ctrl;                  // run the controller step in the last block
   int diag;                  // P_V part of the preconditioner
+  int blend;                 // weighted P_V / P_Delta combination (mode 4)
 };
 
 template <class R> __device__ __forceinline__ bool gate_open(const KArgs<R>& a) {
@@ -665,11 +666,13 @@ template <class R_, int L_> struct XInvEG {
 template <class R> struct PcUni {
   int cur, nsel, rgiven;
   R mu[2], shift[2], floor_[2];
+  R wv;  // weight of P_V in the blended preconditioner
 };
 template <class R> __device__ __forceinline__ void pc_uniform(const KArgs<R>& a, PcUni<R>& u) {
   u.cur = __ldcg(&a.st->cur);
   u.nsel = __ldcg(&a.st->n) & 1;
   u.rgiven = a.flag;
+  u.wv = (R)__ldcg(&a.st->opt.pc_blend);
   const double fl = __ldcg(&a.st->opt.pv_floor);
   for (int i = 0; i < 2; ++i) {
     u.mu[i] = (R)__ldcg(&a.st->mu[i]);
@@ -867,6 +870,9 @@ template <class R_, int L_> struct XInvPC {
   static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], PAcc<R>* acc,
                                const LhyNode<R>*) {
     if (!valid) return;
+    const int yy = row % a.ny, zz = row / a.ny;
+    const R Yc = -a.Ly + (R)yy * a.hy, Zc = -a.Lz + (R)zz * a.hz;
+    const R vyz = a.vy * Yc * Yc + a.vz * Zc * Zc;
     R s[PC_NS];
 #pragma unroll
     for (int k = 0; k < PC_NS; ++k) s[k] = 0;
@@ -879,10 +885,25 @@ template <class R_, int L_> struct XInvPC {
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
         const int e = e0 + j;
-        const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e);
-        a.z[idx] = v[0][e];
-        a.z[(size_t)a.N + idx] = v[1][e];
-        pc_sum_add<R>(in[j], v[0][e], v[1][e], s);
+        const int x = Plan<L>::exit_pos(true, t, e);
+        const size_t idx = (size_t)row * a.nx + x;
+        C z1 = v[0][e], z2 = v[1][e];
+        if (a.blend) {  // z = (1 - w) P_Delta^{-1} r + w P_V^{-1} r
+          const C ml = a.ax[u.cur][(size_t)a.N + idx];
+          const R X = -a.Lx + (R)x * a.hx;
+          const R V = a.vx * X * X + vyz;
+          const R n1 = cabs2(in[j].p1), n2 = cabs2(in[j].p2);
+          R P1 = u.shift[0] + V + a.g11 * n1 + a.g12 * n2 + ml.x;
+          R P2 = u.shift[1] + V + a.g21 * n1 + a.g22 * n2 + ml.y;
+          P1 = P1 > u.floor_[0] ? P1 : u.floor_[0];
+          P2 = P2 > u.floor_[1] ? P2 : u.floor_[1];
+          const R wd = R(1) - u.wv, w1 = u.wv / P1, w2 = u.wv / P2;
+          z1 = cmk<C>(wd * z1.x + w1 * in[j].r1.x, wd * z1.y + w1 * in[j].r1.y);
+          z2 = cmk<C>(wd * z2.x + w2 * in[j].r2.x, wd * z2.y + w2 * in[j].r2.y);
+        }
+        a.z[idx] = z1;
+        a.z[(size_t)a.N + idx] = z2;
+        pc_sum_add<R>(in[j], z1, z2, s);
       }
     }
 #pragma unroll

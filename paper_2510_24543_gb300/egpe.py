@@ -19,7 +19,7 @@ EGPE_OK = 0
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "non-finite value",
           5: "not converged", 6: "stagnated", 7: "timeout", 8: "unsupported"}
 EGPE_FP64, EGPE_FP32, EGPE_MIXED = 0, 1, 2
-PRECOND = {"none": 0, "kinetic": 1, "diagonal": 2, "kinetic+diagonal": 3}
+PRECOND = {"none": 0, "kinetic": 1, "diagonal": 2, "kinetic+diagonal": 3, "blend": 4}
 # order of egpe_param_grad's output (EGPE_P_*)
 PARAM_NAMES = ("g11", "g12", "g22", "gdd11", "gdd12", "gdd22", "kappa", "eta_s", "trap_x", "trap_y", "trap_z")
 
@@ -46,7 +46,8 @@ class egpe_solve_opts(ct.Structure):
                 ("tol_dE", ct.c_double), ("armijo_c1", ct.c_double), ("theta_max", ct.c_double),
                 ("accept_rtol", ct.c_double), ("accept_rtol_fp32", ct.c_double), ("pv_floor", ct.c_double),
                 ("tol_fp32_switch", ct.c_double), ("max_iter_fp32", ct.c_int), ("trace_cap", ct.c_int),
-                ("trace", ct.c_void_p), ("batch", ct.c_int), ("stall_iters_fp32", ct.c_int)]
+                ("trace", ct.c_void_p), ("batch", ct.c_int), ("stall_iters_fp32", ct.c_int),
+                ("pc_blend", ct.c_double)]
 
 
 class egpe_trace_entry(ct.Structure):

@@ -158,7 +158,7 @@ def test_line_coeffs(E, case):
 
 
 # ----------------------------------------------------------------- a7/a8: preconditioners
-@pytest.mark.parametrize("mode", ["none", "kinetic", "diagonal", "kinetic+diagonal"])
+@pytest.mark.parametrize("mode", ["none", "kinetic", "diagonal", "kinetic+diagonal", "blend"])
 def test_precondition(E, mode):
     w = mixed_workload((32, 16, 64))
     psi = I.random_state(w.n, w.L, 31, width=(1.2, 1.5, 0.9))
@@ -236,6 +236,24 @@ def test_ncg_lockstep_first_iterations(E, beta_rule):
         assert abs(a["beta"] - b["beta"]) < 1e-7 * max(1.0, abs(b["beta"])), k
         assert rel(a["alpha"], b["alpha"]) < 1e-7, k
         assert rel(a["E_trial"], b["E_new"]) < 1e-11, k
+
+
+def test_ncg_lockstep_blended_preconditioner(E):
+    """Weighted P_V / P_Delta combination (weight 0.3): iterations in lockstep."""
+    w = I.PRESETS["c1"]
+    psi0 = I.gaussian_start(w)
+    g, prm = oracle_case(w)
+    otr = []
+    O.ncg_solve(g, prm, psi0, O.SolveOpts(precond="blend", blend=0.3, tol_res=1e-8, max_iter=8), trace=otr)
+    st, rep, tr, _ = _solve_gpu(E, w, psi0, "blend", 1e-8, trace_cap=64, max_iter=8, pc_blend=0.3)
+    acc = [t for t in tr if t["flags"] & 1]
+    oacc = [t for t in otr if t["accepted"]]
+    assert len(acc) == len(oacc) == 8
+    for a, b in zip(acc, oacc):
+        assert rel(a["E"], b["E"]) < 1e-11
+        assert rel(a["res"], b["res"]) < 1e-8
+        assert abs(a["beta"] - b["beta"]) < 1e-7 * max(1.0, abs(b["beta"]))
+        assert rel(a["alpha"], b["alpha"]) < 1e-7
 
 
 @pytest.mark.parametrize("precond", ["kinetic", "kinetic+diagonal"])
