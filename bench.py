@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="untuned launch shapes (no autotuning)")
     ap.add_argument("--no-cont", action="store_true", help="skip continuation along the scan")
     ap.add_argument("--no-pcstudy", action="store_true", help="skip the preconditioner study")
+    ap.add_argument("--no-pgrad", action="store_true", help="skip the parameter-derivative timing")
     ap.add_argument("--fp32-switch", type=float, default=1e-4)
     return ap.parse_args()
 
@@ -347,6 +348,12 @@ def run_ours(args):
             scan = scan_benchmark(E, tune=not args.no_tune)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             scan = {"error": str(ex)[:300]}
+    pgrad = None
+    if not args.no_pgrad:
+        try:
+            pgrad = param_grad_timing(E)
+        except Exception as ex:  # reported, not fatal for the iteration numbers
+            pgrad = {"error": str(ex)[:300]}
     pcs = None
     if not args.no_pcstudy:
         try:
@@ -379,7 +386,7 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launch32,
                 "clocks": clk, "fp64": fp64, "time_to_ground_state": tts, "ncg_vs_ite": ite,
                 "scan": scan, "continuation": cont,
-                "precond_study": pcs, "autotune": tuning}
+                "precond_study": pcs, "param_grad": pgrad, "autotune": tuning}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -537,6 +544,41 @@ def scan_benchmark(E, tol_res=1e-6, fp32_switch=1e-4, tune=True):
                      "worse_than_best": {str(i): x for i, x in enumerate(d) if x > 1e-8},
                      "all_converged": all(r["status"] == 0 for r in reps)}
     out["speedup_mixed_batched_vs_fp64_one_by_one"] = round(runs["fp64_one_by_one"][0] / runs["mixed_batched"][0], 3)
+    return out
+
+
+def param_grad_timing(E, reps=5):
+    """Device time of the parameter-derivative pass (dE/d(g, g_dd, kappa, eta_s,
+    lambda), the autograd extension) on the 256x256x128 workload beside one
+    energy/gradient evaluation, FP64 and FP32 fields; wall time per call with a
+    synchronisation on both sides."""
+    import torch
+
+    from paper_2510_24543_gb300 import inputs as I
+
+    w = I.PRESETS["c5"]
+    psi64 = torch.from_numpy(I.gaussian_start(w)).to("cuda")
+    out = {"workload": w.name, "points": w.points}
+    for name, prec, psi in (("fp64", E.EGPE_FP64, psi64), ("fp32", E.EGPE_FP32, psi64.to(torch.complex64))):
+        h = E.egpe_create([E.make_grid(w.n, w.L)], [E.params_from_workload(w)], prec)
+        try:
+            grad = torch.empty_like(psi)
+            E.egpe_param_grad(h, 0, psi)
+            E.egpe_energy_grad(h, 0, psi, grad)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                E.egpe_param_grad(h, 0, psi)
+            torch.cuda.synchronize()
+            t_pg = (time.perf_counter() - t0) / reps
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                E.egpe_energy_grad(h, 0, psi, grad)
+            torch.cuda.synchronize()
+            t_eg = (time.perf_counter() - t0) / reps
+        finally:
+            E.egpe_destroy(h)
+        out[name] = {"param_grad_ms": round(t_pg * 1e3, 3), "energy_grad_ms": round(t_eg * 1e3, 3)}
     return out
 
 

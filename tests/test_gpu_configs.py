@@ -111,3 +111,19 @@ def test_c3_mixed_solve_energy_against_oracle(E):
         assert abs(O.inner(g, psi_m[i], psi_m[i]).real - 1.0) < 1e-12
     # both precisions land on the same minimum (unique up to the residual tolerance)
     assert rel(rep_m["E"], rep_d["E"]) < 1e-11
+
+
+def test_c5_param_grad_full_size(E):
+    """256x256x128: the parameter derivatives of the energy (the autograd
+    extension on the largest workload) against the oracle at the seeded start."""
+    w = I.PRESETS["c5"]
+    psi = I.gaussian_start(w)
+    g, prm = oracle_case(w)
+    ref = O.param_grad(g, prm, psi)
+    h = _handle(E, w, E.EGPE_FP64)
+    try:
+        d = E.egpe_param_grad(h, 0, torch.from_numpy(psi).to("cuda"))
+    finally:
+        E.egpe_destroy(h)
+    for k, v in ref.items():
+        assert abs(d[k] - v) < 1e-11 * max(abs(v), 1e-6), (k, d[k], v)
