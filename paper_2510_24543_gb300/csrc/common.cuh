@@ -105,6 +105,9 @@ template <class R> struct LhyNode {
   R W;      // kappa eta_s^{-5/2} times the quadrature weight on [0,1]
   R Ww;     // W w
   R e12sq;  // eta12(u_q)^2 = (g12 + gdd12 w)^2
+  R gq;     // 2 sqrt(max(det eta(u_q), 0)): V+ V- = 4 n1 n2 det eta, so sqrt(V-) = gq sqrt(n1 n2) / sqrt(V+)
+  R Www;    // W w^2
+  R pad0, pad1;
 };
 
 // Couplings entering the LHY terms (symmetric: eta12 = eta21).

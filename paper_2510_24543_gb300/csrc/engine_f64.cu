@@ -199,6 +199,9 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
       nd.W = (double)(c5 * w);
       nd.Ww = (double)(c5 * w * sdd);
       nd.e12sq = (double)(e12 * e12);
+      nd.gq = (double)(det > 0.0L ? 2.0L * sqrtl(det) : 0.0L);
+      nd.Www = (double)(c5 * w * sdd * sdd);
+      nd.pad0 = nd.pad1 = 0.0;
       if (det > 0.0L) {
         nodes[qm++] = nd;
       } else {

@@ -140,6 +140,9 @@ template <class R> egpe_status Engine<R>::apply_params(const egpe_params& p) {
     nd.W = (R)(c5 * w[q]);
     nd.Ww = (R)(c5 * w[q] * s);
     nd.e12sq = (R)(e12 * e12);
+    nd.gq = (R)(det > 0.0L ? 2.0L * sqrtl(det) : 0.0L);
+    nd.Www = (R)(c5 * w[q] * s * s);
+    nd.pad0 = nd.pad1 = (R)0;
     (det > 0.0L ? h : hneg).push_back(nd);
   }
   Qm_ = (int)h.size();

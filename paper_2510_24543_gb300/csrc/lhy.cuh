@@ -108,9 +108,37 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
     }
   };
   if constexpr (std::is_same<R, float>::value) {
-    // FP32: one loop (the skipped branch is cheap there, registers are not)
+    // FP32: one loop over all nodes; one reciprocal square root of V+ gives
+    // sqrt(V+) and, through V+ V- = 4 n1 n2 det eta, sqrt(V-) = gq sqrt(n1 n2) / sqrt(V+)
+    // (clamped to sqrt(V+), which also makes it 0 where V+ is clamped to 0)
+    R sq[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) sq[j] = sqrt_pos(n1[j] * n2[j]);
 #pragma unroll 2
-    for (int k = 0; k < Q; ++k) node(nd[k], std::true_type{});
+    for (int k = 0; k < Q; ++k) {
+      const LhyNode<R>& e = nd[k];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const R A = p[j].A0 + p[j].A1 * e.w;
+        const R d = p[j].D0 + p[j].D1 * e.w;
+        const R s2 = d * d + e.e12sq * p[j].q4;
+        const R rs = rsqrt_(s2 + s2_eps<R>());
+        const R vp = fmax(A + s2 * rs, R(0));
+        const R rp = rsqrt_(vp + s2_eps<R>());
+        const R P1 = vp * rp;
+        const R M1 = fmin(e.gq * sq[j] * rp, P1);
+        const R vm = M1 * M1;
+        const R p32 = vp * P1, m32 = vm * M1;
+        f[j] += e.W * (vp * p32 + vm * m32);
+        const R sum32 = p32 + m32;
+        const R t = (p32 - m32) * rs;
+        S0[j] += e.W * sum32;
+        S1[j] += e.Ww * sum32;
+        T0[j] += e.W * t;
+        T1[j] += e.Ww * t;
+        T2[j] += e.Www * t;
+      }
+    }
   } else {
 #pragma unroll 2
     for (int k = 0; k < Qm; ++k) node(nd[k], std::true_type{});
@@ -182,9 +210,36 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
     }
   };
   if constexpr (std::is_same<R, float>::value) {
-    // FP32: one loop (the skipped branch is cheap there, registers are not)
+    // FP32: sqrt(V-) from sqrt(V+) as in lhy_points, and the two branches summed
+    // in closed form: with P1,M1 = sqrt(V+-), P3,M3 = V+-^{3/2}, V1+- = A1 +- t1,
+    //   sum_+- [2 K+- V^{3/2} + 3/2 V^{1/2} V1^2]
+    //     = (Q2 - t1^2)/s (P3 - M3) + 3/2 [(P1 + M1)(A1^2 + t1^2) + 2 A1 t1 (P1 - M1)]
+    // with K+- = +-(Q2 - t1^2)/(2s), Q2 = delta1^2 + 4 eta12^2 n1' n2'.
+    R sq[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) sq[j] = sqrt_pos(n1[j] * n2[j]);
 #pragma unroll 2
-    for (int k = 0; k < Q; ++k) node(nd[k], std::true_type{});
+    for (int k = 0; k < Q; ++k) {
+      const LhyNode<R>& e = nd[k];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const R A = p[j].A0 + p[j].A1 * e.w;
+        const R d = p[j].D0 + p[j].D1 * e.w;
+        const R s2 = d * d + e.e12sq * p[j].q4;
+        const R rs = rsqrt_(s2 + s2_eps<R>());
+        const R vp = fmax(A + s2 * rs, R(0));
+        const R rp = rsqrt_(vp + s2_eps<R>());
+        const R P1 = vp * rp;
+        const R M1 = fmin(e.gq * sq[j] * rp, P1);
+        const R dP3 = vp * P1 - M1 * M1 * M1;
+        const R A1 = B0[j] + B1[j] * e.w;
+        const R d1 = E0[j] + E1[j] * e.w;
+        const R t1 = (d * d1 + e.e12sq * m[j]) * rs;
+        const R K2 = (d1 * d1 + e.e12sq * mp[j] - t1 * t1) * rs;
+        const R br = (P1 + M1) * (A1 * A1 + t1 * t1) + R(2) * A1 * t1 * (P1 - M1);
+        h[j] += e.W * (K2 * dP3 + R(1.5) * br);
+      }
+    }
   } else {
 #pragma unroll 2
     for (int k = 0; k < Qm; ++k) node(nd[k], std::true_type{});
