@@ -173,6 +173,23 @@ template <class R> egpe_status Engine<R>::apply_params(const egpe_params& p) {
   a.Q = Q;
   a.Qm = Qm_;
   a.nodes = nodes_;
+  // LHY skip threshold: with eb = max over u of |eta11| + |eta22| + |eta12| every branch
+  // potential obeys V <= 2 eb n (n = n1 + n2), so F <= 2 c5 (2 eb n)^{5/2} and
+  // mu_LHY <= 15 c5 eb (2 eb n)^{3/2}; below nskip these are under 1e-40 and 1e-30.
+  {
+    double eb = 0.0;
+    for (double w : {-1.0, 2.0})
+      eb = std::max(eb, std::fabs(p.g[0][0] + p.gdd[0][0] * w) + std::fabs(p.g[1][1] + p.gdd[1][1] * w) +
+                            std::fabs(p.g[0][1] + p.gdd[0][1] * w));
+    const double c5a = std::fabs((double)c5);
+    double ns = 1e30;
+    if (c5a > 0.0 && eb > 0.0) {
+      const double nf = std::pow(1e-40 / (2.0 * c5a), 0.4) / (2.0 * eb);
+      const double nm = std::pow(1e-30 / (15.0 * c5a * eb), 2.0 / 3.0) / (2.0 * eb);
+      ns = std::min(nf, nm);
+    }
+    a.nskip = (R)std::min(ns, 1e30);
+  }
   return EGPE_OK;
 }
 

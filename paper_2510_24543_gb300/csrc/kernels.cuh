@@ -39,6 +39,7 @@ template <class R> struct KArgs {
   R d11, d12, d21, d22;      // k-space dipolar coefficients
   R invN;
   int Q, Qm;  // Gauss-Legendre nodes; the first Qm have det eta > 0
+  R nskip;    // LHY terms skipped where n1 + n2 <= nskip (their size is below 1e-30)
   const LhyNode<R>* nodes;
   const C* twx;
   const C* twy;
@@ -101,6 +102,7 @@ template <class R> __device__ __forceinline__ LhyCoef<R> lhy_coef(const KArgs<R>
   c.d11 = a.d11;
   c.d22 = a.d22;
   c.d12 = a.d12;
+  c.nskip = a.nskip;
   return c;
 }
 

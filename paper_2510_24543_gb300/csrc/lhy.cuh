@@ -71,6 +71,14 @@ template <class R, int NP>
 __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, int Q, int Qm, const LhyCoef<R>& c,
                                            const R (&n1)[NP], const R (&n2)[NP], R (&F)[NP], R (&mu1)[NP],
                                            R (&mu2)[NP]) {
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) any |= n1[j] + n2[j] > c.nskip;
+  if (!any) {  // every term below FP64 rounding (see LhyCoef::nskip)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) F[j] = mu1[j] = mu2[j] = R(0);
+    return;
+  }
   LhyPt<R> p[NP];
   R f[NP], S0[NP], S1[NP], T0[NP], T1[NP], T2[NP];
 #pragma unroll
@@ -171,6 +179,14 @@ template <class R, int NP>
 __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int Q, int Qm, const LhyCoef<R>& c,
                                          const R (&n1)[NP], const R (&n2)[NP], const R (&n1p)[NP],
                                          const R (&n2p)[NP], R (&H)[NP]) {
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) any |= n1[j] + n2[j] > c.nskip;
+  if (!any) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) H[j] = R(0);
+    return;
+  }
   LhyPt<R> p[NP];
   R B0[NP], B1[NP], E0[NP], E1[NP], m[NP], mp[NP], h[NP];
 #pragma unroll
@@ -262,6 +278,7 @@ __device__ __forceinline__ void lhy_eta_sums(const LhyNode<R>* __restrict__ nd, 
                                              R n2, R (&o)[7]) {
 #pragma unroll
   for (int k = 0; k < 7; ++k) o[k] = R(0);
+  if (!(n1 + n2 > c.nskip)) return;
   const LhyPt<R> p = lhy_pt(c, n1, n2);
   for (int q = 0; q < Q; ++q) {
     const LhyNode<R>& e = nd[q];
