@@ -113,7 +113,7 @@ template <class R> struct LhyNode {
 // Couplings entering the LHY terms (symmetric: eta12 = eta21).
 template <class R> struct LhyCoef {
   R g11, g22, g12, d11, d22, d12;
-  R nskip;  // points with n1 + n2 <= nskip contribute below FP64 rounding (set per instance)
+  R nskip;  // FP64: points with n1 + n2 <= nskip contribute below FP64 rounding (set per instance)
 };
 
 }  // namespace egpe

@@ -71,13 +71,18 @@ template <class R, int NP>
 __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, int Q, int Qm, const LhyCoef<R>& c,
                                            const R (&n1)[NP], const R (&n2)[NP], R (&F)[NP], R (&mu1)[NP],
                                            R (&mu2)[NP]) {
-  bool any = false;
+  if constexpr (std::is_same<R, double>::value) {
+    // every term below FP64 rounding (see LhyCoef::nskip).  FP64 only: the FP32
+    // transforms leave a round-off floor of ~1e-7 in amplitude everywhere, so
+    // FP32 densities never fall below the threshold and the test only costs.
+    bool any = false;
 #pragma unroll
-  for (int j = 0; j < NP; ++j) any |= n1[j] + n2[j] > c.nskip;
-  if (!any) {  // every term below FP64 rounding (see LhyCoef::nskip)
+    for (int j = 0; j < NP; ++j) any |= n1[j] + n2[j] > c.nskip;
+    if (!any) {
 #pragma unroll
-    for (int j = 0; j < NP; ++j) F[j] = mu1[j] = mu2[j] = R(0);
-    return;
+      for (int j = 0; j < NP; ++j) F[j] = mu1[j] = mu2[j] = R(0);
+      return;
+    }
   }
   LhyPt<R> p[NP];
   R f[NP], S0[NP], S1[NP], T0[NP], T1[NP], T2[NP];
@@ -179,13 +184,15 @@ template <class R, int NP>
 __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int Q, int Qm, const LhyCoef<R>& c,
                                          const R (&n1)[NP], const R (&n2)[NP], const R (&n1p)[NP],
                                          const R (&n2p)[NP], R (&H)[NP]) {
-  bool any = false;
+  if constexpr (std::is_same<R, double>::value) {  // as in lhy_points
+    bool any = false;
 #pragma unroll
-  for (int j = 0; j < NP; ++j) any |= n1[j] + n2[j] > c.nskip;
-  if (!any) {
+    for (int j = 0; j < NP; ++j) any |= n1[j] + n2[j] > c.nskip;
+    if (!any) {
 #pragma unroll
-    for (int j = 0; j < NP; ++j) H[j] = R(0);
-    return;
+      for (int j = 0; j < NP; ++j) H[j] = R(0);
+      return;
+    }
   }
   LhyPt<R> p[NP];
   R B0[NP], B1[NP], E0[NP], E1[NP], m[NP], mp[NP], h[NP];
@@ -278,7 +285,8 @@ __device__ __forceinline__ void lhy_eta_sums(const LhyNode<R>* __restrict__ nd, 
                                              R n2, R (&o)[7]) {
 #pragma unroll
   for (int k = 0; k < 7; ++k) o[k] = R(0);
-  if (!(n1 + n2 > c.nskip)) return;
+  if constexpr (std::is_same<R, double>::value)
+    if (!(n1 + n2 > c.nskip)) return;
   const LhyPt<R> p = lhy_pt(c, n1, n2);
   for (int q = 0; q < Q; ++q) {
     const LhyNode<R>& e = nd[q];
