@@ -92,9 +92,13 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
     f[j] = S0[j] = S1[j] = T0[j] = T1[j] = T2[j] = R(0);
   }
   // nodes [0, Qm): det eta > 0, both branches; [Qm, Q): det eta <= 0, where
-  // V+ V- = 4 n1 n2 det(eta) <= 0 makes max(V-, 0) = 0 at every point
+  // V+ V- = 4 n1 n2 det(eta) <= 0 makes max(V-, 0) = 0 at every point.  With
+  // both branches, one reciprocal square root of V+ gives sqrt(V+) and
+  // sqrt(V-) = gq sqrt(n1 n2) / sqrt(V+) (clamped to sqrt(V+)).
+  R sq[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) sq[j] = sqrt_pos(n1[j] * n2[j]);
   auto node = [&](const LhyNode<R>& e, auto minus) {
-    const R Www = e.Ww * e.w;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       const R A = p[j].A0 + p[j].A1 * e.w;
@@ -103,12 +107,17 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
       const R rs = rsqrt_(s2 + s2_eps<R>());
       const R s = s2 * rs;
       const R vp = fmax(A + s, R(0));
-      const R p32 = vp * sqrt_pos(vp);
-      R m32 = R(0), m52 = R(0);
+      R p32, m32 = R(0), m52 = R(0);
       if constexpr (decltype(minus)::value) {
-        const R vm = fmax(A - s, R(0));
-        m32 = vm * sqrt_pos(vm);
+        const R rp = rsqrt_(vp + s2_eps<R>());
+        const R P1 = vp * rp;
+        const R M1 = fmin(e.gq * sq[j] * rp, P1);
+        const R vm = M1 * M1;
+        p32 = vp * P1;
+        m32 = vm * M1;
         m52 = vm * m32;
+      } else {
+        p32 = vp * sqrt_pos(vp);
       }
       f[j] += e.W * (vp * p32 + m52);
       const R sum32 = p32 + m32;
@@ -117,16 +126,12 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
       S1[j] += e.Ww * sum32;
       T0[j] += e.W * t;
       T1[j] += e.Ww * t;
-      T2[j] += Www * t;
+      T2[j] += e.Www * t;
     }
   };
   if constexpr (std::is_same<R, float>::value) {
-    // FP32: one loop over all nodes; one reciprocal square root of V+ gives
-    // sqrt(V+) and, through V+ V- = 4 n1 n2 det eta, sqrt(V-) = gq sqrt(n1 n2) / sqrt(V+)
-    // (clamped to sqrt(V+), which also makes it 0 where V+ is clamped to 0)
-    R sq[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) sq[j] = sqrt_pos(n1[j] * n2[j]);
+    // FP32: one loop over all nodes with both branches (sqrt(V-) as above; the
+    // clamp also makes it 0 where V+ is clamped to 0)
 #pragma unroll 2
     for (int k = 0; k < Q; ++k) {
       const LhyNode<R>& e = nd[k];
@@ -207,6 +212,9 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
     mp[j] = R(4) * n1p[j] * n2p[j];                   // 4 eta12^2 n1' n2' = eta12^2 mp
     h[j] = R(0);
   }
+  R sq[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) sq[j] = sqrt_pos(n1[j] * n2[j]);
   auto node = [&](const LhyNode<R>& e, auto minus) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
@@ -216,7 +224,13 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
       R rs, s;
       inv_s(s2, rs, s);
       const R vp = fmax(A + s, R(0));
-      const R sp = sqrt_pos(vp);
+      R sp, rp = R(0);
+      if constexpr (decltype(minus)::value) {
+        rp = rsqrt_(vp + s2_eps<R>());  // see lhy_points for sqrt(V-)
+        sp = vp * rp;
+      } else {
+        sp = sqrt_pos(vp);
+      }
       const R A1 = B0[j] + B1[j] * e.w;
       const R d1 = E0[j] + E1[j] * e.w;
       const R t1 = (d * d1 + e.e12sq * m[j]) * rs;
@@ -224,8 +238,8 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
       const R v1p = A1 + t1;
       R acc = R(2) * K * (vp * sp) + R(1.5) * (sp * v1p * v1p);
       if constexpr (decltype(minus)::value) {
-        const R vm = fmax(A - s, R(0));
-        const R sm = sqrt_pos(vm);
+        const R sm = fmin(e.gq * sq[j] * rp, sp);
+        const R vm = sm * sm;
         const R v1m = A1 - t1;
         acc += R(-2) * K * (vm * sm) + R(1.5) * (sm * v1m * v1m);
       }
@@ -238,9 +252,6 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
     //   sum_+- [2 K+- V^{3/2} + 3/2 V^{1/2} V1^2]
     //     = (Q2 - t1^2)/s (P3 - M3) + 3/2 [(P1 + M1)(A1^2 + t1^2) + 2 A1 t1 (P1 - M1)]
     // with K+- = +-(Q2 - t1^2)/(2s), Q2 = delta1^2 + 4 eta12^2 n1' n2'.
-    R sq[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) sq[j] = sqrt_pos(n1[j] * n2[j]);
 #pragma unroll 2
     for (int k = 0; k < Q; ++k) {
       const LhyNode<R>& e = nd[k];
