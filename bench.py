@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-pcstudy", action="store_true", help="skip the preconditioner study")
     ap.add_argument("--no-pgrad", action="store_true", help="skip the parameter-derivative timing")
     ap.add_argument("--fp32-switch", type=float, default=1e-4)
+    ap.add_argument("--table", action="store_true",
+                    help="per-workload table (oracle and GPU) instead of the benchmark line")
     return ap.parse_args()
 
 
@@ -780,8 +782,83 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def config_table(args):
+    """Per-workload figures: the FP64 oracle's seconds per NCG iteration and per
+    ITE step and its time to ground state (single host thread), the GPU's time
+    to ground state at 1e-8 relative energy (plain FP64 and mixed precision),
+    and the FP32 energy/gradient pass against the measured HBM peak.  Oracle
+    times to ground state on the larger workloads are seconds per iteration
+    times the iterations the GPU FP64 solve needed (labelled)."""
+    import torch
+
+    import oracle as O
+    from paper_2510_24543_gb300 import egpe as E
+    from paper_2510_24543_gb300 import inputs as I
+
+    E.load()
+    hbm, _ = peaks()
+    rows = {}
+    for key in ("c1", "c2", "c3", "c3p", "c5"):
+        w = I.PRESETS[key]
+        grid, prm = E.make_grid(w.n, w.L), E.params_from_workload(w)
+        pc = E.PRECOND[w.precond]
+        psi0 = I.gaussian_start(w)
+        psi64 = torch.from_numpy(psi0).to("cuda")
+        h = E.egpe_create([grid], [prm], E.EGPE_MIXED)
+        try:
+            tts = time_to_ground_state(E, h, grid, prm, psi64, pc, args.fp32_switch)
+            prof = E.egpe_profile_attempt(h, 0, 1, psi64.to(torch.complex64), pc, reps=3)
+        finally:
+            E.egpe_destroy(h)
+        eg = prof[-5:]  # the trial energy/gradient pass: x fwd, y, z fused, y, x inv
+        eg_gbs = sum(b for _, _, b in eg) / (sum(t for _, t, _ in eg) * 1e-3) / 1e9
+        g = O.Grid(w.n, w.L)
+        op = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
+        t0 = time.perf_counter()
+        O.evaluate(g, op, psi0)
+        t_eval = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.ncg_solve(g, op, psi0, O.SolveOpts(precond=w.precond, tol_res=0.0, max_iter=1))
+        s_iter = max(time.perf_counter() - t0 - t_eval, 1e-9)
+        row = {"grid": list(w.n), "oracle_s_per_iter": round(s_iter, 3),
+               "gpu_fp64_tts_s": round(tts["fp64"]["seconds"], 4), "gpu_mixed_tts_s": round(tts["mixed"]["seconds"], 4),
+               "gpu_fp64_iters": tts["fp64"]["iters"], "fp32_eg_pass_GBs": round(eg_gbs, 1),
+               "fp32_eg_pass_frac_hbm": round(eg_gbs / hbm, 3)}
+        if key in ("c1", "c2"):
+            t0 = time.perf_counter()
+            O.ite_solve(g, op, psi0, dtau=1e-3, tol_dE=0.0, max_steps=2)
+            row["oracle_s_per_ite_step"] = round((time.perf_counter() - t0 - 2 * t_eval) / 2, 3)
+            t0 = time.perf_counter()
+            _, rep = O.ncg_solve(g, op, psi0, O.SolveOpts(precond=w.precond, tol_res=tts["res_target"]))
+            row["oracle_tts_s"] = round(time.perf_counter() - t0, 2)
+            row["oracle_tts_iters"] = rep["iters"]
+        else:
+            row["oracle_tts_s_extrapolated"] = round(s_iter * tts["fp64"]["iters"] + t_eval, 1)
+        rows[key] = row
+        print(json.dumps({key: row}), flush=True)
+    # the 64-instance scan: oracle seconds per iteration on one sampled instance per grid size
+    scan = I.scan_workloads()
+    c4 = {}
+    for k in (0, 16, 32, 48):
+        w = scan[k]
+        g = O.Grid(w.n, w.L)
+        op = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
+        psi0 = I.gaussian_start(w)
+        t0 = time.perf_counter()
+        O.evaluate(g, op, psi0)
+        t_eval = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.ncg_solve(g, op, psi0, O.SolveOpts(precond=w.precond, tol_res=0.0, max_iter=1))
+        c4[f"{w.n[0]}^3"] = round(max(time.perf_counter() - t0 - t_eval, 1e-9), 3)
+    rows["c4_oracle_s_per_iter_sampled"] = c4
+    print(json.dumps({"table": rows}))
+
+
 def main():
     args = parse()
+    if args.table:
+        config_table(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
