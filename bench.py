@@ -358,32 +358,34 @@ def run_ours(args):
             tts = time_to_ground_state(E, h, grid, prm, psi64, pc, args.fp32_switch)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             tts = {"error": str(ex)[:300]}
+    # single-GPU studies: only in a one-rank run (under torchrun every rank would repeat them)
+    solo = world == 1
     ite = None
-    if not args.no_ite:
+    if solo and not args.no_ite:
         try:
             ite = ncg_vs_ite(E, tune=not args.no_tune)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             ite = {"error": str(ex)[:300]}
     scan = None
-    if not args.no_scan:
+    if solo and not args.no_scan:
         try:
             scan = scan_benchmark(E, tune=not args.no_tune)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             scan = {"error": str(ex)[:300]}
     pgrad = None
-    if not args.no_pgrad:
+    if solo and not args.no_pgrad:
         try:
             pgrad = param_grad_timing(E)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             pgrad = {"error": str(ex)[:300]}
     pcs = None
-    if not args.no_pcstudy:
+    if solo and not args.no_pcstudy:
         try:
             pcs = precond_study(E)
         except Exception as ex:  # reported, not fatal for the iteration numbers
             pcs = {"error": str(ex)[:300]}
     cont = None
-    if not args.no_cont:
+    if solo and not args.no_cont:
         try:
             cont = continuation_benchmark(E, tune=not args.no_tune)
         except Exception as ex:  # reported, not fatal for the iteration numbers
