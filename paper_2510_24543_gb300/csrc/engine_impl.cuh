@@ -664,8 +664,8 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   const int block = M * TPL;
   const int other = (Op::AXIS == 1) ? nz : ny;
   const int tiles = (nx / M) * other * a.nf;
-  const size_t smem_tma =
-      2 * (size_t)M * L * sizeof(C) + L * sizeof(C) + 2 * sizeof(uint64_t) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const size_t smem_tma = (size_t)kColStages * M * L * sizeof(C) + L * sizeof(C) + kColStages * sizeof(uint64_t) +
+                          (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const size_t smem_plain = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   bool tma = tm && use_tma_;
   if (tma && !tune_.empty()) {

@@ -213,6 +213,13 @@ __global__ void __launch_bounds__(MaxThreads<Op>::v, MinBlocks<Op>::v)
   xpass_body<Op>(kb.k[blockIdx.y]);
 }
 
+#ifndef EGPE_COL_STAGES
+#define EGPE_COL_STAGES 3
+#endif
+// Tiles in flight per block of a TMA-fed column pass (one transformed, the
+// rest loading).
+constexpr int kColStages = EGPE_COL_STAGES;
+
 // Threads per block of a column pass: at most max(128 B / element, 32 / (L/8))
 // columns times L/8 threads.  The power-of-two lengths keep the 512 bound they
 // were tuned with; the mixed-radix lengths give the compiler the exact bound.
@@ -291,20 +298,21 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
   using C = C2<R>;
   constexpr int L = Op::L, NS = Op::NS;
   constexpr int NSR = NS > 0 ? NS : 1;
+  constexpr int NST = kColStages;
   if (!gate_open(a)) return;
   extern __shared__ __align__(128) unsigned char smraw_tma[];
   const int tileC = a.M * L;
-  C* tiles = reinterpret_cast<C*>(smraw_tma);  // two tiles
-  C* tw = tiles + 2 * tileC;
+  C* tiles = reinterpret_cast<C*>(smraw_tma);  // NST tiles
+  C* tw = tiles + NST * tileC;
   uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
-  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(bar + 2);
+  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(bar + NST);
   const int tid = threadIdx.x;
   const int m = tid % a.M, t = tid / a.M;
   const C* twsrc = (Op::AXIS == 1) ? a.twy : a.twz;
   for (int i = tid; i < L; i += blockDim.x) tw[i] = twsrc[i];
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+#pragma unroll
+    for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
     fence_barrier_init();
   }
   __syncthreads();
@@ -329,15 +337,22 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     mbar_expect_tx(&bar[b], bytes);
     tma_load_3d(tiles + b * tileC, tm, c0, c1, c2, &bar[b]);
   };
-  if (tid == 0 && (int)blockIdx.x < tiles_n) issue(blockIdx.x, 0);
-  bool timed_out = false, next_pending = false;
+  // iteration q of this block handles tile blockIdx.x + q gridDim.x in buffer q % NST;
+  // the copies of the next NST - 1 iterations are in flight while one is transformed
+  auto tile_of = [&](int q) { return (int)blockIdx.x + q * (int)gridDim.x; };
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NST - 1; ++q)
+      if (tile_of(q) < tiles_n) issue(tile_of(q), q);
+  }
+  bool timed_out = false;
   int it = 0;
   for (int tile = blockIdx.x; tile < tiles_n; tile += gridDim.x, ++it) {
-    const int b = it & 1;
-    const int next = tile + gridDim.x;
-    next_pending = next < tiles_n;
-    if (tid == 0 && next_pending) issue(next, b ^ 1);
-    const bool ok = mbar_wait(&bar[b], (uint32_t)((it >> 1) & 1), kTmaWaitPolls);
+    const int b = it % NST;
+    const int ahead = tile_of(it + NST - 1);
+    // its buffer was last used by iteration it - 1, which ended with a barrier
+    if (tid == 0 && ahead < tiles_n) issue(ahead, (it + NST - 1) % NST);
+    const bool ok = mbar_wait(&bar[b], (uint32_t)((it / NST) & 1), kTmaWaitPolls);
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
@@ -357,8 +372,9 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     __syncthreads();  // buffer b may be refilled from the next iteration on
   }
   if (timed_out) {
-    // let the copy already issued for the next tile land (bounded) before exiting
-    if (next_pending) mbar_wait(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kTmaWaitPolls);
+    // let every copy already issued land (each wait bounded) before exiting
+    for (int q = it; q < it + NST; ++q)
+      if (tile_of(q) < tiles_n) mbar_wait(&bar[q % NST], (uint32_t)((q / NST) & 1), kTmaWaitPolls);
     if (tid == 0) {
       a.st->status = 7;  // EGPE_ERR_TIMEOUT
       a.st->phase = PH_DONE;
