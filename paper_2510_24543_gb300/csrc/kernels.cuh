@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(MaxThreads<Op>::v, MinBlocks<Op>::v)
 }
 
 #ifndef EGPE_COL_STAGES
-#define EGPE_COL_STAGES 3
+#define EGPE_COL_STAGES 2
 #endif
 // Tiles in flight per block of a TMA-fed column pass (one transformed, the
 // rest loading).
