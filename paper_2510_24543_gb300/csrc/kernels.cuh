@@ -223,10 +223,16 @@ constexpr int kColStages = EGPE_COL_STAGES;
 // Threads per block of a column pass: at most max(128 B / element, 32 / (L/8))
 // columns times L/8 threads.  The power-of-two lengths keep the 512 bound they
 // were tuned with; the mixed-radix lengths give the compiler the exact bound.
+#ifndef EGPE_COL_MINB
+#define EGPE_COL_MINB 1
+#endif
 template <class Op> struct ColMaxThreads {
   static constexpr int TPL = Op::L / 8;
   static constexpr int MC = (int)(128 / sizeof(C2<typename Op::R>));
-  static constexpr int v = IsPow2<Op::L>::v ? 512 : (MC > 32 / TPL ? MC : 32 / TPL) * TPL;
+  static constexpr int exact = (MC > 32 / TPL ? MC : 32 / TPL) * TPL;
+  static constexpr int v = (IsPow2<Op::L>::v && EGPE_COL_MINB == 1) ? 512 : exact;
+  // resident blocks per SM the compiler is asked to allow for (caps registers)
+  static constexpr int minb = (EGPE_COL_MINB > 1 && exact <= 256) ? EGPE_COL_MINB : 1;
 };
 
 // ----------------------------------------------------------------------------
@@ -276,11 +282,13 @@ template <class Op> __device__ __forceinline__ void colpass_body(const KArgs<typ
     }
   }
 }
-template <class Op> __global__ void __launch_bounds__(ColMaxThreads<Op>::v) colpass_kernel(KArgs<typename Op::R> a) {
+template <class Op>
+__global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb) colpass_kernel(KArgs<typename Op::R> a) {
   colpass_body<Op>(a);
 }
 template <class Op>
-__global__ void __launch_bounds__(ColMaxThreads<Op>::v) colpass_kernel_b(const __grid_constant__ KBatch<typename Op::R> kb) {
+__global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
+    colpass_kernel_b(const __grid_constant__ KBatch<typename Op::R> kb) {
   colpass_body<Op>(kb.k[blockIdx.y]);
 }
 
@@ -390,12 +398,12 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
   }
 }
 template <class Op>
-__global__ void __launch_bounds__(ColMaxThreads<Op>::v)
+__global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
     colpass_tma_kernel(const __grid_constant__ CUtensorMap tm, KArgs<typename Op::R> a) {
   colpass_tma_body<Op>(&tm, a);
 }
 template <class Op>
-__global__ void __launch_bounds__(ColMaxThreads<Op>::v)
+__global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
     colpass_tma_kernel_b(const __grid_constant__ KBatch<typename Op::R> kb) {
   colpass_tma_body<Op>(&kb.tm[blockIdx.y], kb.k[blockIdx.y]);
 }
