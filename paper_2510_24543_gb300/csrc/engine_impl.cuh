@@ -50,10 +50,16 @@ static TmaEncodeFn tma_encode_fn() {
   return fn;
 }
 
-// Columns per tile of the strided passes: 128-byte rows, at least one warp.
+// Columns per tile of the strided passes: EGPE_COL_BYTES-wide rows (128 B:
+// one cache line) and at least one warp; the power-of-two lengths, whose
+// kernels are bound to 512 threads, may take wider rows.
 template <class C> static inline int col_tile_width(int L, int nx) {
   const int TPL = L / 8;
-  return std::min(std::max((int)(128 / sizeof(C)), 32 / TPL), nx);
+  const bool pow2 = (L & (L - 1)) == 0;
+  int M = pow2 ? std::min((int)(EGPE_COL_BYTES / sizeof(C)), 512 / TPL) : (int)(128 / sizeof(C));
+  M = std::min(std::max(M, 32 / TPL), nx);
+  while (M > 1 && nx % M != 0) M /= 2;  // whole tiles across x
+  return M;
 }
 
 // Tensor map of `nfields` consecutive complex fields (nx, ny, nz), box = one

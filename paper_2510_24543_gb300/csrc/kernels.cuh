@@ -226,6 +226,10 @@ constexpr int kColStages = EGPE_COL_STAGES;
 #ifndef EGPE_COL_MINB
 #define EGPE_COL_MINB 1
 #endif
+#ifndef EGPE_COL_BYTES
+#define EGPE_COL_BYTES 128  // row width of a column-pass tile (see col_tile_width)
+#endif
+static_assert(EGPE_COL_MINB == 1 || EGPE_COL_BYTES == 128, "exact column bounds assume 128-byte tile rows");
 template <class Op> struct ColMaxThreads {
   static constexpr int TPL = Op::L / 8;
   static constexpr int MC = (int)(128 / sizeof(C2<typename Op::R>));
