@@ -85,11 +85,11 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
     }
   }
   LhyPt<R> p[NP];
-  R f[NP], S0[NP], S1[NP], T0[NP], T1[NP], T2[NP];
+  R S0[NP], S1[NP], T0[NP], T1[NP], T2[NP];
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
     p[j] = lhy_pt(c, n1[j], n2[j]);
-    f[j] = S0[j] = S1[j] = T0[j] = T1[j] = T2[j] = R(0);
+    S0[j] = S1[j] = T0[j] = T1[j] = T2[j] = R(0);
   }
   // nodes [0, Qm): det eta > 0, both branches; [Qm, Q): det eta <= 0, where
   // V+ V- = 4 n1 n2 det(eta) <= 0 makes max(V-, 0) = 0 at every point.  With
@@ -107,19 +107,16 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
       const R rs = rsqrt_(s2 + s2_eps<R>());
       const R s = s2 * rs;
       const R vp = fmax(A + s, R(0));
-      R p32, m32 = R(0), m52 = R(0);
+      R p32, m32 = R(0);
       if constexpr (decltype(minus)::value) {
         const R rp = rsqrt_(vp + s2_eps<R>());
         const R P1 = vp * rp;
         const R M1 = fmin(e.gq * sq[j] * rp, P1);
-        const R vm = M1 * M1;
         p32 = vp * P1;
-        m32 = vm * M1;
-        m52 = vm * m32;
+        m32 = M1 * M1 * M1;
       } else {
         p32 = vp * sqrt_pos(vp);
       }
-      f[j] += e.W * (vp * p32 + m52);
       const R sum32 = p32 + m32;
       const R t = (p32 - m32) * rs;
       S0[j] += e.W * sum32;
@@ -145,9 +142,7 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
         const R rp = rsqrt_(vp + s2_eps<R>());
         const R P1 = vp * rp;
         const R M1 = fmin(e.gq * sq[j] * rp, P1);
-        const R vm = M1 * M1;
-        const R p32 = vp * P1, m32 = vm * M1;
-        f[j] += e.W * (vp * p32 + vm * m32);
+        const R p32 = vp * P1, m32 = M1 * M1 * M1;
         const R sum32 = p32 + m32;
         const R t = (p32 - m32) * rs;
         S0[j] += e.W * sum32;
@@ -173,9 +168,11 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
     const R s20 = -c.g22 * p[j].D0 + n1x2 * c.g12 * c.g12;
     const R s21 = -c.g22 * p[j].D1 - c.d22 * p[j].D0 + R(2) * n1x2 * c.g12 * c.d12;
     const R s22 = -c.d22 * p[j].D1 + n1x2 * c.d12 * c.d12;
-    F[j] = f[j];
     mu1[j] = R(2.5) * (c.g11 * S0[j] + c.d11 * S1[j] + s10 * T0[j] + s11 * T1[j] + s12 * T2[j]);
     mu2[j] = R(2.5) * (c.g22 * S0[j] + c.d22 * S1[j] + s20 * T0[j] + s21 * T1[j] + s22 * T2[j]);
+    // V+- are homogeneous of degree 1 in (n1, n2), so F is of degree 5/2 and
+    // Euler's theorem gives F = (2/5)(n1 mu1 + n2 mu2) exactly
+    F[j] = R(0.4) * (n1[j] * mu1[j] + n2[j] * mu2[j]);
   }
 }
 
