@@ -20,6 +20,8 @@
 // interface with a mixed-radix plan (radix 8, then 3/5 and 2/4 passes in
 // shared memory) and natural entry/exit layouts; see fft_mixed.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace egpe {
@@ -69,6 +71,16 @@ template <int L> struct Plan<L, true> {
     return t + (e / r) * TPL + (e % r) * (L / r);
   }
 };
+
+struct ColIdx;
+// Synchronisation of one transform's exchange buffer.  A row line's L/8
+// threads are consecutive and, for the power-of-two lengths (L/8 <= 32
+// dividing 32), inside one warp with a buffer of their own: a warp barrier
+// suffices.  Column lines spread over the block and need the block barrier.
+template <class SI> __device__ __forceinline__ void line_sync() {
+  if constexpr (std::is_same<SI, ColIdx>::value) __syncthreads();
+  else __syncwarp();
+}
 
 template <class C> __device__ __forceinline__ C mul_i(C a) { return cmk<C>(-a.y, a.x); }
 template <class C> __device__ __forceinline__ C mul_mi(C a) { return cmk<C>(a.y, -a.x); }
@@ -198,7 +210,7 @@ __device__ __forceinline__ void fft_passes(C (&v)[NF][8], C* sm, int fstride, co
         for (int f = 0; f < NF; ++f) sm[f * fstride + o] = v[f][b * r + q];
       }
     }
-    __syncthreads();
+    line_sync<SI>();
     constexpr int r2 = PL::rad(INV, p + 1);
     constexpr int NB2 = 8 / r2;
 #pragma unroll
@@ -211,7 +223,7 @@ __device__ __forceinline__ void fft_passes(C (&v)[NF][8], C* sm, int fstride, co
         for (int f = 0; f < NF; ++f) v[f][b * r2 + q] = sm[f * fstride + o];
       }
     }
-    __syncthreads();
+    line_sync<SI>();
     fft_passes<C, L, INV, NF, p + 1, SI>(v, sm, fstride, tw, t, si);
   }
 }

@@ -178,7 +178,10 @@ template <class Op> __device__ __forceinline__ void xpass_body(const KArgs<typen
 #pragma unroll
         for (int e = 0; e < 8; ++e) sm[f * a.MX * LP + si(Plan<L>::exit_pos(Op::INV, t, e))] = v[f][e];
       Op::store_staged(a, u, row, valid, t, sm, a.MX * LP, acc, nodes);
-      __syncthreads();  // the next row group's exchanges reuse the buffer
+      // the next row group's exchanges reuse the buffer (a warp's own rows when
+      // the length is a power of two, else rows that may straddle warps)
+      if constexpr (IsPow2<L>::v) __syncwarp();
+      else __syncthreads();
     } else {
       Op::store(a, u, row, valid, t, v, acc, nodes);
     }
