@@ -229,9 +229,6 @@ constexpr int kColStages = EGPE_COL_STAGES;
 #ifndef EGPE_COL_MINB
 #define EGPE_COL_MINB 1
 #endif
-#ifndef EGPE_COL_WARP
-#define EGPE_COL_WARP 1  // TMA column passes with each line inside one warp (see colpass_tma_body)
-#endif
 #ifndef EGPE_COL_BYTES
 #define EGPE_COL_BYTES 128  // row width of a column-pass tile (see col_tile_width)
 #endif
@@ -311,7 +308,7 @@ __global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
 // memory from registers.
 // ----------------------------------------------------------------------------
 template <class Op>
-__device__ __forceinline__ void colpass_tma_body_block(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
+__device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
   using R = typename Op::R;
   using C = C2<R>;
   constexpr int L = Op::L, NS = Op::NS;
@@ -407,133 +404,6 @@ __device__ __forceinline__ void colpass_tma_body_block(const CUtensorMap* tm, co
     }
   }
 }
-
-// Element (pos, c) of a tile of 128-byte rows written by TMA with the 128-byte
-// swizzle: the 16-byte chunk index within a row is XORed with the row index
-// modulo 8 (tile base aligned to 1024 bytes).
-template <class C> __device__ __forceinline__ const C& swizzled(const C* tile, int pos, int c) {
-  const int byte = c * (int)sizeof(C);
-  const int off = pos * 128 + ((((byte >> 4) ^ (pos & 7)) << 4) | (byte & 15));
-  return *reinterpret_cast<const C*>(reinterpret_cast<const char*>(tile) + off);
-}
-
-// Column pass with each line's L/8 threads inside one warp (power-of-two
-// lengths, 128-byte tile rows): the transform exchanges go through a padded
-// line buffer private to the warp and synchronise per warp; one block barrier
-// per tile remains, before its TMA buffer is refilled.  The tile arrives with
-// the 128-byte swizzle, so reading it column by column is free of bank
-// conflicts.
-template <class Op>
-__device__ __forceinline__ void colpass_tma_body_warp(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
-  using R = typename Op::R;
-  using C = C2<R>;
-  constexpr int L = Op::L, NS = Op::NS, TPL = L / 8;
-  constexpr int NSR = NS > 0 ? NS : 1;
-  constexpr int NST = kColStages;
-  constexpr int LP = row_len_padded<R, L>();
-  if (!gate_open(a)) return;
-  extern __shared__ __align__(128) unsigned char smraw_tma[];
-  unsigned char* base_sm = smraw_tma + ((1024u - (smem_u32(smraw_tma) & 1023u)) & 1023u);
-  const int tileC = a.M * L;
-  C* tiles = reinterpret_cast<C*>(base_sm);  // NST swizzled tiles
-  C* exch = tiles + NST * tileC;              // one padded line per column
-  C* tw = exch + a.M * LP;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
-  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(bar + NST);
-  const int tid = threadIdx.x;
-  const int c = tid / TPL, t = tid - c * TPL;
-  const C* twsrc = (Op::AXIS == 1) ? a.twy : a.twz;
-  for (int i = tid; i < L; i += blockDim.x) tw[i] = twsrc[i];
-  if (tid == 0) {
-#pragma unroll
-    for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
-    fence_barrier_init();
-  }
-  __syncthreads();
-  typename Op::Uni u;
-  Op::uniform(a, u);
-  PAcc<R> acc[NSR];
-  const int xb_n = a.nx / a.M;
-  const int other_n = (Op::AXIS == 1) ? a.nz : a.ny;
-  const int tiles_n = xb_n * other_n * a.nf;
-  const size_t lstride = (Op::AXIS == 1) ? (size_t)a.nx : (size_t)a.nx * a.ny;
-  const uint32_t bytes = (uint32_t)(tileC * sizeof(C));
-  constexpr int ESZ = (int)(sizeof(C) / 8);
-  auto issue = [&](int tile, int b) {
-    const int xb = tile % xb_n;
-    const int rest = tile / xb_n;
-    const int o = rest % other_n;
-    const int f = a.f0 + rest / other_n;
-    const int c0 = xb * a.M * ESZ;
-    const int c1 = (Op::AXIS == 1) ? 0 : o;
-    const int c2 = (Op::AXIS == 1) ? f * a.nz + o : f * a.nz;
-    fence_proxy_async();
-    mbar_expect_tx(&bar[b], bytes);
-    tma_load_3d(tiles + b * tileC, tm, c0, c1, c2, &bar[b]);
-  };
-  auto tile_of = [&](int q) { return (int)blockIdx.x + q * (int)gridDim.x; };
-  if (tid == 0) {
-#pragma unroll
-    for (int q = 0; q < NST - 1; ++q)
-      if (tile_of(q) < tiles_n) issue(tile_of(q), q);
-  }
-  bool timed_out = false;
-  int it = 0;
-  for (int tile = blockIdx.x; tile < tiles_n; tile += gridDim.x, ++it) {
-    const int b = it % NST;
-    const int ahead = tile_of(it + NST - 1);
-    if (tid == 0 && ahead < tiles_n) issue(ahead, (it + NST - 1) % NST);
-    const bool ok = mbar_wait(&bar[b], (uint32_t)((it / NST) & 1), kTmaWaitPolls);
-    if (__syncthreads_or(!ok)) {
-      timed_out = true;
-      break;
-    }
-    const C* tb = tiles + b * tileC;
-    C v[1][8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[0][e] = swizzled(tb, Plan<L>::entry_pos(Op::FIRST_INV, t, e), c);
-    const int xb = tile % xb_n;
-    const int rest = tile / xb_n;
-    const int o = rest % other_n;
-    const int f = a.f0 + rest / other_n;
-    const int x = xb * a.M + c;
-    const size_t base = (size_t)f * a.N + (Op::AXIS == 1 ? (size_t)o * a.nx * a.ny : (size_t)o * a.nx) + x;
-    Op::process(a, u, f, x, o, base, lstride, t, v, exch + c * LP, tw, RowIdx<PadShift<R>::v>{}, acc);
-    __syncthreads();  // buffer b may be refilled from the next iteration on
-  }
-  if (timed_out) {
-    for (int q = it; q < it + NST; ++q)
-      if (tile_of(q) < tiles_n) mbar_wait(&bar[q % NST], (uint32_t)((q / NST) & 1), kTmaWaitPolls);
-    if (tid == 0) {
-      a.st->status = 7;  // EGPE_ERR_TIMEOUT
-      a.st->phase = PH_DONE;
-    }
-  }
-  if constexpr (NS > 0) {
-    double dacc[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) dacc[s] = acc[s].get();
-    if (reduce_blocks<NS>(dacc, a.partials, a.counter, Op::out(a, u), *red)) {
-      if (threadIdx.x == 0) Op::finish(a, u);
-    }
-  }
-}
-
-// Whether a TMA column pass uses the warp layout (host and device agree).
-template <class C> __host__ __device__ constexpr bool col_warp_layout(int L, int M) {
-  return EGPE_COL_WARP && (L & (L - 1)) == 0 && M * (int)sizeof(C) == 128;
-}
-
-template <class Op>
-__device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
-  if constexpr (IsPow2<Op::L>::v && EGPE_COL_WARP) {
-    if (col_warp_layout<C2<typename Op::R>>(Op::L, a.M)) {
-      colpass_tma_body_warp<Op>(tm, a);
-      return;
-    }
-  }
-  colpass_tma_body_block<Op>(tm, a);
-}
 template <class Op>
 __global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
     colpass_tma_kernel(const __grid_constant__ CUtensorMap tm, KArgs<typename Op::R> a) {
@@ -585,9 +455,8 @@ template <class R_, int L_, int AXIS_, bool INV_> struct ColPlain {
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
   static constexpr bool FIRST_INV = INV_;
   static __device__ const C* src(const KArgs<R>& a) { return a.gin; }
-  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int, int, int, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, const SI& si, PAcc<R>*) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
     fft_line<C, L, INV, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.gout[base + (size_t)Plan<L>::exit_pos(INV, t, e) * ls] = v[0][e];
@@ -706,9 +575,8 @@ template <class R_, int L_> struct ZEg {
   }
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
-  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, const SI& si, PAcc<R>* acc) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>* acc) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -995,9 +863,8 @@ template <class R_, int L_> struct ZPc {
   }
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
-  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni& u, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, const SI& si, PAcc<R>*) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -1234,9 +1101,8 @@ template <class R_, int L_> struct ZLc {
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
-  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, const SI& si, PAcc<R>* acc) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>* acc) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -1433,9 +1299,8 @@ template <class R_, int L_> struct ZKin {
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
-  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, const SI& si, PAcc<R>*) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R exy = a.kin_tab[x] * a.kin_tab[a.nx + y] * a.invN;
 #pragma unroll
@@ -1556,9 +1421,8 @@ template <class R_, int L_> struct ZPg {
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
-  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, const SI& si, PAcc<R>*) {
+                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
