@@ -59,7 +59,7 @@ template <class Op> cudaError_t noalloc_launch_x(egpe::KArgs<double> a, int rows
   int mx = std::max(1, 32 / TPL);
   while ((mx * 2) * TPL <= 256 && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
   a.MX = mx;
-  const size_t smem = L * sizeof(double2) + (Op::USES_LHY ? (size_t)a.Q * sizeof(LhyNode<double>) : 0) +
+  const size_t smem = L * sizeof(double2) + (Op::USES_LHY ? lhy_stage_bytes<double>(a.Q) : 0) +
                       mx * rowbytes + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const int groups = (rows + mx - 1) / mx;
   const int grid = std::min(groups, (int)kNoAllocBlocks);

@@ -630,7 +630,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   a.MX = mx;
   const int block = mx * TPL;
   const size_t smem_fixed =
-      L * sizeof(C) + (Op::USES_LHY ? (size_t)a.Q * sizeof(LhyNode<R>) : 0) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+      L * sizeof(C) + (Op::USES_LHY ? lhy_stage_bytes<R>(a.Q) : 0) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const size_t smem = smem_fixed + mx * rowbytes;
   const int rows = ny * nz;
   const int groups = (rows + mx - 1) / mx;

@@ -149,13 +149,12 @@ template <class Op> __device__ __forceinline__ void xpass_body(const KArgs<typen
   extern __shared__ __align__(16) unsigned char smraw[];
   C* tw = reinterpret_cast<C*>(smraw);
   LhyNode<R>* nodes = reinterpret_cast<LhyNode<R>*>(tw + L);
-  C* buf = reinterpret_cast<C*>(nodes + (Op::USES_LHY ? a.Q : 0));
+  C* buf = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(nodes) + (Op::USES_LHY ? lhy_stage_bytes<R>(a.Q) : 0));
   RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(buf + NF * a.MX * LP);
   const int tid = threadIdx.x;
   const int mrow = tid / TPL, t = tid - mrow * TPL;
   for (int i = tid; i < L; i += blockDim.x) tw[i] = a.twx[i];
-  if (Op::USES_LHY)
-    for (int i = tid; i < a.Q; i += blockDim.x) nodes[i] = a.nodes[i];
+  if (Op::USES_LHY) stage_lhy_nodes(nodes, a.nodes, a.Q);
   __syncthreads();
   typename Op::Uni u;
   Op::uniform(a, u);
@@ -1554,9 +1553,10 @@ template <class R> __device__ __forceinline__ void eg_point_body(const KArgs<R>&
   using C = C2<R>;
   constexpr int NP = 2;
   if (!gate_open(a)) return;
-  __shared__ LhyNode<R> nodes[64];
+  __shared__ __align__(16) unsigned char nodes_raw[lhy_stage_bytes<R>(64)];
+  LhyNode<R>* nodes = reinterpret_cast<LhyNode<R>*>(nodes_raw);
   __shared__ RedSmem<EG_NS> red;
-  for (int i = threadIdx.x; i < a.Q; i += blockDim.x) nodes[i] = a.nodes[i];
+  stage_lhy_nodes(nodes, a.nodes, a.Q);
   __syncthreads();
   EgUni<R> u;
   XFwdEG<R, 16>::uniform(a, u);
@@ -1630,9 +1630,10 @@ template <class R> __device__ __forceinline__ void lc_point_body(const KArgs<R>&
   using C = C2<R>;
   constexpr int NP = 2;
   if (!gate_open(a)) return;
-  __shared__ LhyNode<R> nodes[64];
+  __shared__ __align__(16) unsigned char nodes_raw[lhy_stage_bytes<R>(64)];
+  LhyNode<R>* nodes = reinterpret_cast<LhyNode<R>*>(nodes_raw);
   __shared__ RedSmem<LC_NS> red;
-  for (int i = threadIdx.x; i < a.Q; i += blockDim.x) nodes[i] = a.nodes[i];
+  stage_lhy_nodes(nodes, a.nodes, a.Q);
   __syncthreads();
   LcUni<R> u;
   lc_uniform(a, u);

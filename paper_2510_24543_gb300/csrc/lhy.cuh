@@ -45,6 +45,88 @@ template <class R> __device__ __forceinline__ R s2_eps();
 template <> __device__ __forceinline__ double s2_eps<double>() { return 1e-300; }
 template <> __device__ __forceinline__ float s2_eps<float>() { return 1e-30f; }
 
+// Two FP32 values in one 64-bit register pair, operated on by the packed FP32
+// instructions (add/sub/mul/fma .f32x2: both lanes in one issue slot, each
+// rounded like its scalar counterpart, denormals flushed like the rest of the
+// FP32 path).  The FP32 node loops below are bound by instruction issue and
+// evaluate two grid points per instruction with them; square roots, min and
+// max stay scalar.
+struct f32x2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {  // a b + c
+  f32x2 r;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 rsqrt2(f32x2 a) {
+  float x, y;
+  upk2(a, x, y);
+  return pk2(rsqrtf(x), rsqrtf(y));
+}
+__device__ __forceinline__ f32x2 max0_2(f32x2 a) {
+  float x, y;
+  upk2(a, x, y);
+  return pk2(fmaxf(x, 0.f), fmaxf(y, 0.f));
+}
+__device__ __forceinline__ f32x2 min2(f32x2 a, f32x2 b) {
+  float x, y, u, v;
+  upk2(a, x, y);
+  upk2(b, u, v);
+  return pk2(fminf(x, u), fminf(y, v));
+}
+
+// A quadrature node with every value in both lanes, for the packed loops.
+struct __align__(16) LhyNodeP {
+  f32x2 w, W, Ww, e12sq, gq, Www, pad0, pad1;
+};
+
+// Shared-memory staging of the node table: the LhyNode<R> entries, followed
+// for FP32 by the same nodes in packed form (the FP32 node loops read them at
+// nd + Q).  The staged table must start on a 16-byte boundary.
+template <class R> __host__ __device__ constexpr size_t lhy_stage_bytes(int Q) {
+  return (size_t)Q * sizeof(LhyNode<R>) + (std::is_same<R, float>::value ? (size_t)Q * sizeof(LhyNodeP) : 0);
+}
+template <class R> __device__ __forceinline__ void stage_lhy_nodes(LhyNode<R>* dst, const LhyNode<R>* src, int Q) {
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+    const LhyNode<R> e = src[i];
+    dst[i] = e;
+    if constexpr (std::is_same<R, float>::value) {
+      LhyNodeP& q = reinterpret_cast<LhyNodeP*>(dst + Q)[i];
+      q.w = pk2(e.w, e.w);
+      q.W = pk2(e.W, e.W);
+      q.Ww = pk2(e.Ww, e.Ww);
+      q.e12sq = pk2(e.e12sq, e.e12sq);
+      q.gq = pk2(e.gq, e.gq);
+      q.Www = pk2(e.Www, e.Www);
+      q.pad0 = q.pad1 = pk2(0.f, 0.f);
+    }
+  }
+}
+
 // Per-point coefficients.
 template <class R> struct LhyPt {
   R A0, A1, D0, D1, q4;  // q4 = 4 n1 n2
@@ -128,29 +210,53 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
   };
   if constexpr (std::is_same<R, float>::value) {
     // FP32: one loop over all nodes with both branches (sqrt(V-) as above; the
-    // clamp also makes it 0 where V+ is clamped to 0)
+    // clamp also makes it 0 where V+ is clamped to 0), points j = 2h, 2h + 1 in
+    // the two lanes
+    static_assert(NP % 2 == 0, "the packed FP32 loop takes points in pairs");
+    constexpr int NH = NP / 2;
+    const LhyNodeP* np = reinterpret_cast<const LhyNodeP*>(nd + Q);
+    f32x2 A0[NH], A1[NH], D0[NH], D1[NH], q4[NH], sq2[NH], s0[NH], s1[NH], t0[NH], t1[NH], t2[NH];
+    const f32x2 eps = pk2(s2_eps<float>(), s2_eps<float>()), zero = pk2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      A0[h] = pk2(p[2 * h].A0, p[2 * h + 1].A0);
+      A1[h] = pk2(p[2 * h].A1, p[2 * h + 1].A1);
+      D0[h] = pk2(p[2 * h].D0, p[2 * h + 1].D0);
+      D1[h] = pk2(p[2 * h].D1, p[2 * h + 1].D1);
+      q4[h] = pk2(p[2 * h].q4, p[2 * h + 1].q4);
+      sq2[h] = pk2(sq[2 * h], sq[2 * h + 1]);
+      s0[h] = s1[h] = t0[h] = t1[h] = t2[h] = zero;
+    }
 #pragma unroll 2
     for (int k = 0; k < Q; ++k) {
-      const LhyNode<R>& e = nd[k];
+      const LhyNodeP e = np[k];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        const R A = p[j].A0 + p[j].A1 * e.w;
-        const R d = p[j].D0 + p[j].D1 * e.w;
-        const R s2 = d * d + e.e12sq * p[j].q4;
-        const R rs = rsqrt_(s2 + s2_eps<R>());
-        const R vp = fmax(A + s2 * rs, R(0));
-        const R rp = rsqrt_(vp + s2_eps<R>());
-        const R P1 = vp * rp;
-        const R M1 = fmin(e.gq * sq[j] * rp, P1);
-        const R p32 = vp * P1, m32 = M1 * M1 * M1;
-        const R sum32 = p32 + m32;
-        const R t = (p32 - m32) * rs;
-        S0[j] += e.W * sum32;
-        S1[j] += e.Ww * sum32;
-        T0[j] += e.W * t;
-        T1[j] += e.Ww * t;
-        T2[j] += e.Www * t;
+      for (int h = 0; h < NH; ++h) {
+        const f32x2 A = fma2(A1[h], e.w, A0[h]);
+        const f32x2 d = fma2(D1[h], e.w, D0[h]);
+        const f32x2 s2 = fma2(d, d, mul2(e.e12sq, q4[h]));
+        const f32x2 rs = rsqrt2(add2(s2, eps));
+        const f32x2 vp = max0_2(fma2(s2, rs, A));
+        const f32x2 rp = rsqrt2(add2(vp, eps));
+        const f32x2 P1 = mul2(vp, rp);
+        const f32x2 M1 = min2(mul2(mul2(e.gq, sq2[h]), rp), P1);
+        const f32x2 p32 = mul2(vp, P1), m32 = mul2(mul2(M1, M1), M1);
+        const f32x2 sum32 = add2(p32, m32);
+        const f32x2 t = mul2(sub2(p32, m32), rs);
+        s0[h] = fma2(e.W, sum32, s0[h]);
+        s1[h] = fma2(e.Ww, sum32, s1[h]);
+        t0[h] = fma2(e.W, t, t0[h]);
+        t1[h] = fma2(e.Ww, t, t1[h]);
+        t2[h] = fma2(e.Www, t, t2[h]);
       }
+    }
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      upk2(s0[h], S0[2 * h], S0[2 * h + 1]);
+      upk2(s1[h], S1[2 * h], S1[2 * h + 1]);
+      upk2(t0[h], T0[2 * h], T0[2 * h + 1]);
+      upk2(t1[h], T1[2 * h], T1[2 * h + 1]);
+      upk2(t2[h], T2[2 * h], T2[2 * h + 1]);
     }
   } else {
 #pragma unroll 2
@@ -249,28 +355,55 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
     //   sum_+- [2 K+- V^{3/2} + 3/2 V^{1/2} V1^2]
     //     = (Q2 - t1^2)/s (P3 - M3) + 3/2 [(P1 + M1)(A1^2 + t1^2) + 2 A1 t1 (P1 - M1)]
     // with K+- = +-(Q2 - t1^2)/(2s), Q2 = delta1^2 + 4 eta12^2 n1' n2'.
+    // Points j = 2i, 2i + 1 in the two lanes of the packed instructions.
+    static_assert(NP % 2 == 0, "the packed FP32 loop takes points in pairs");
+    constexpr int NH = NP / 2;
+    const LhyNodeP* np = reinterpret_cast<const LhyNodeP*>(nd + Q);
+    f32x2 A0[NH], A1c[NH], D0[NH], D1[NH], q4[NH], sq2[NH], b0[NH], b1[NH], e0[NH], e1[NH], m2[NH], mp2[NH],
+        hh[NH];
+    const f32x2 eps = pk2(s2_eps<float>(), s2_eps<float>()), c15 = pk2(1.5f, 1.5f);
+#pragma unroll
+    for (int i = 0; i < NH; ++i) {
+      const int j0 = 2 * i, j1 = 2 * i + 1;
+      A0[i] = pk2(p[j0].A0, p[j1].A0);
+      A1c[i] = pk2(p[j0].A1, p[j1].A1);
+      D0[i] = pk2(p[j0].D0, p[j1].D0);
+      D1[i] = pk2(p[j0].D1, p[j1].D1);
+      q4[i] = pk2(p[j0].q4, p[j1].q4);
+      sq2[i] = pk2(sq[j0], sq[j1]);
+      b0[i] = pk2(B0[j0], B0[j1]);
+      b1[i] = pk2(B1[j0], B1[j1]);
+      e0[i] = pk2(E0[j0], E0[j1]);
+      e1[i] = pk2(E1[j0], E1[j1]);
+      m2[i] = pk2(m[j0], m[j1]);
+      mp2[i] = pk2(mp[j0], mp[j1]);
+      hh[i] = pk2(0.f, 0.f);
+    }
 #pragma unroll 2
     for (int k = 0; k < Q; ++k) {
-      const LhyNode<R>& e = nd[k];
+      const LhyNodeP e = np[k];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        const R A = p[j].A0 + p[j].A1 * e.w;
-        const R d = p[j].D0 + p[j].D1 * e.w;
-        const R s2 = d * d + e.e12sq * p[j].q4;
-        const R rs = rsqrt_(s2 + s2_eps<R>());
-        const R vp = fmax(A + s2 * rs, R(0));
-        const R rp = rsqrt_(vp + s2_eps<R>());
-        const R P1 = vp * rp;
-        const R M1 = fmin(e.gq * sq[j] * rp, P1);
-        const R dP3 = vp * P1 - M1 * M1 * M1;
-        const R A1 = B0[j] + B1[j] * e.w;
-        const R d1 = E0[j] + E1[j] * e.w;
-        const R t1 = (d * d1 + e.e12sq * m[j]) * rs;
-        const R K2 = (d1 * d1 + e.e12sq * mp[j] - t1 * t1) * rs;
-        const R br = (P1 + M1) * (A1 * A1 + t1 * t1) + R(2) * A1 * t1 * (P1 - M1);
-        h[j] += e.W * (K2 * dP3 + R(1.5) * br);
+      for (int i = 0; i < NH; ++i) {
+        const f32x2 A = fma2(A1c[i], e.w, A0[i]);
+        const f32x2 d = fma2(D1[i], e.w, D0[i]);
+        const f32x2 s2 = fma2(d, d, mul2(e.e12sq, q4[i]));
+        const f32x2 rs = rsqrt2(add2(s2, eps));
+        const f32x2 vp = max0_2(fma2(s2, rs, A));
+        const f32x2 rp = rsqrt2(add2(vp, eps));
+        const f32x2 P1 = mul2(vp, rp);
+        const f32x2 M1 = min2(mul2(mul2(e.gq, sq2[i]), rp), P1);
+        const f32x2 dP3 = sub2(mul2(vp, P1), mul2(mul2(M1, M1), M1));
+        const f32x2 a1 = fma2(b1[i], e.w, b0[i]);
+        const f32x2 d1 = fma2(e1[i], e.w, e0[i]);
+        const f32x2 t1 = mul2(fma2(d, d1, mul2(e.e12sq, m2[i])), rs);
+        const f32x2 tt = mul2(t1, t1);
+        const f32x2 K2 = mul2(sub2(fma2(d1, d1, mul2(e.e12sq, mp2[i])), tt), rs);
+        const f32x2 br = fma2(add2(P1, M1), fma2(a1, a1, tt), mul2(mul2(add2(a1, a1), t1), sub2(P1, M1)));
+        hh[i] = fma2(e.W, fma2(c15, br, mul2(K2, dP3)), hh[i]);
       }
     }
+#pragma unroll
+    for (int i = 0; i < NH; ++i) upk2(hh[i], h[2 * i], h[2 * i + 1]);
   } else {
 #pragma unroll 2
     for (int k = 0; k < Qm; ++k) node(nd[k], std::true_type{});
