@@ -89,9 +89,10 @@ template <class R> struct ChunkW;
 template <> struct ChunkW<float> { static constexpr int v = 4; };
 template <> struct ChunkW<double> { static constexpr int v = 2; };
 
-// Grid points evaluated together in the LHY node loops (independent chains).
+// Grid points evaluated together in the LHY node loops (independent chains;
+// FP32: two pairs of packed lanes).
 template <class R> struct LhyNP;
-template <> struct LhyNP<float> { static constexpr int v = 2; };
+template <> struct LhyNP<float> { static constexpr int v = 4; };
 template <> struct LhyNP<double> { static constexpr int v = 2; };
 
 template <class R> __device__ __forceinline__ LhyCoef<R> lhy_coef(const KArgs<R>& a) {
