@@ -89,23 +89,6 @@ template <class R> struct ChunkW;
 template <> struct ChunkW<float> { static constexpr int v = 4; };
 template <> struct ChunkW<double> { static constexpr int v = 2; };
 
-// Row passes whose epilogue reads other fields at the transformed row first
-// prefetch those rows into L2 from their prologue, so the reads after the
-// transform find them there: field i of `rows` is prefetched by thread i of the
-// row's L/8 (a row is nx complex values, a multiple of 16 bytes).
-#ifndef EGPE_EPI_PREFETCH
-#define EGPE_EPI_PREFETCH 2  // 0: none, 1: preconditioner pass only, 2: all epilogue passes
-#endif
-template <int TPL, int NR, class C, class RowPtr>
-__device__ __forceinline__ void prefetch_rows(RowPtr row_ptr, int nr, int nx, int t) {
-#pragma unroll
-  for (int i = 0; i < NR; ++i) {
-    if (i % TPL != t || i >= nr) continue;
-    const C* p = row_ptr(i);
-    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) prefetch_l2(p, (uint32_t)(nx * sizeof(C)));
-  }
-}
-
 // Grid points evaluated together in the LHY node loops (independent chains;
 // FP32: two pairs of packed lanes).
 template <class R> struct LhyNP;
@@ -632,11 +615,7 @@ template <class R_, int L_> struct XInvEG {
   static constexpr bool INV = true, USES_LHY = true;
   using Uni = EgUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { XFwdEG<R, L>::uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*) {
-    if (EGPE_EPI_PREFETCH >= 2 && valid) {  // psi
-      const size_t o = (size_t)row * a.nx;
-      prefetch_rows<L / 8, 2, C>([&](int i) -> const C* { return a.psi[u.slot] + (i ? a.N : 0) + o; }, 2, a.nx, t);
-    }
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*) {
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
@@ -913,18 +892,7 @@ template <class R_, int L_> struct XInvPC {
   static constexpr bool INV = true, USES_LHY = false;
   using Uni = PcUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { pc_uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*) {
-    if (EGPE_EPI_PREFETCH >= 1 && valid) {
-      // r, r_prev, d_prev, psi (both components) and, blended, mu_LHY
-      const size_t o = (size_t)row * a.nx;
-      prefetch_rows<L / 8, 9, C>(
-          [&](int i) -> const C* {
-            const C* b = i < 2 ? a.rb[u.nsel] : i < 4 ? a.rb[u.nsel ^ 1] : i < 6 ? a.pb[u.nsel ^ 1]
-                       : i < 8 ? a.psi[u.cur] : a.ax[u.cur] + a.N;
-            return b + ((i & 1) && i < 8 ? a.N : 0) + o;
-          },
-          a.blend ? 9 : 8, a.nx, t);
-    }
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*) {
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
@@ -1173,16 +1141,7 @@ template <class R_, int L_> struct XInvLC {
   static constexpr bool INV = true, USES_LHY = true;
   using Uni = LcUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { lc_uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*) {
-    if (EGPE_EPI_PREFETCH >= 2 && valid) {  // psi, p, H psi, (Phi, mu_LHY)
-      const size_t o = (size_t)row * a.nx;
-      prefetch_rows<L / 8, 8, C>(
-          [&](int i) -> const C* {
-            const C* b = i < 2 ? a.psi[u.cur] : i < 4 ? a.pb[u.nsel] : i < 6 ? a.hp[u.cur] : a.ax[u.cur];
-            return b + ((i & 1) ? a.N : 0) + o;
-          },
-          8, a.nx, t);
-    }
+  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*) {
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       v[0][e] = valid ? a.W[(size_t)2 * a.N + (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e)] : cmk<C>(0, 0);

@@ -39,12 +39,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
-// Asynchronous prefetch of [p, p + bytes) from global memory into L2 (address
-// and size multiples of 16 bytes); nothing waits for it.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // Waits for phase `parity` of the barrier to complete; false after `limit` polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const uint32_t a = smem_u32(bar);
