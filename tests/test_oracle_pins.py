@@ -197,6 +197,20 @@ def test_lhy_mu_is_derivative_of_density():
     assert np.max(np.abs(fd2 - m2)) < 1e-7 * np.max(np.abs(m2))
 
 
+def test_lhy_euler_identity():
+    """V_+- are homogeneous of degree 1 in (n1, n2), so the LHY density F is of
+    degree 5/2 and n1 mu1 + n2 mu2 = (5/2) F exactly (Euler's theorem), also where
+    det eta(u) < 0 at some nodes (one branch clamped) and at zero density."""
+    rng = np.random.default_rng(11)
+    n1 = np.concatenate([rng.uniform(0.0, 0.3, 60), [0.0, 0.2, 0.0]])
+    n2 = np.concatenate([rng.uniform(0.0, 0.3, 60), [0.0, 0.0, 0.15]])
+    for g12, gdd12 in ((280.0, 400.0), (340.0, 150.0), (120.0, 60.0)):
+        prm = _prm(g=((300, g12), (g12, 310)), gdd=((420, gdd12), (gdd12, 380)), kappa=40.0, eta_s=610.0)
+        F, m1, m2 = O.lhy_density_and_mu(prm, n1, n2)
+        assert np.max(np.abs(n1 * m1 + n2 * m2 - 2.5 * F)) < 1e-13 * np.max(np.abs(F))
+        assert F[-3] == 0.0 and m1[-3] == 0.0 and m2[-3] == 0.0
+
+
 def test_lhy_quadrature_against_adaptive_integral():
     """For smooth integrands (all V > 0) the 32-node rule matches scipy.quad."""
     from scipy.integrate import quad
