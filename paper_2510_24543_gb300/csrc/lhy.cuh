@@ -39,9 +39,8 @@ template <class R> __device__ __forceinline__ void inv_s(R s2, R& rs, R& s) {
   s = s2 * rs;
 }
 
-// 1/s with a tiny offset (the packed FP32 loops: a floor) instead of a branch:
-// where s^2 is 0 the quantities multiplied by it, (V+^{3/2} - V-^{3/2}), vanish
-// with it.  The same guard keeps 1/sqrt(V+) finite where V+ is clamped to 0.
+// 1/s with a tiny offset instead of a branch: where s^2 is 0 the quantities
+// multiplied by it, (V+^{3/2} - V-^{3/2}), vanish with it.
 template <class R> __device__ __forceinline__ R s2_eps();
 template <> __device__ __forceinline__ double s2_eps<double>() { return 1e-300; }
 template <> __device__ __forceinline__ float s2_eps<float>() { return 1e-30f; }
@@ -87,12 +86,6 @@ __device__ __forceinline__ f32x2 rsqrt2(f32x2 a) {
   float x, y;
   upk2(a, x, y);
   return pk2(rsqrtf(x), rsqrtf(y));
-}
-// 1/sqrt(max(a, lo)) per lane: the floor on the ALU pipe, not the FMA pipe
-__device__ __forceinline__ f32x2 rsqrt_floor2(f32x2 a, float lo) {
-  float x, y;
-  upk2(a, x, y);
-  return pk2(rsqrtf(fmaxf(x, lo)), rsqrtf(fmaxf(y, lo)));
 }
 __device__ __forceinline__ f32x2 max0_2(f32x2 a) {
   float x, y;
@@ -223,7 +216,7 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
     constexpr int NH = NP / 2;
     const LhyNodeP* np = reinterpret_cast<const LhyNodeP*>(nd + Q);
     f32x2 A0[NH], A1[NH], D0[NH], D1[NH], q4[NH], sq2[NH], s0[NH], s1[NH], t0[NH], t1[NH], t2[NH];
-    const f32x2 zero = pk2(0.f, 0.f);
+    const f32x2 eps = pk2(s2_eps<float>(), s2_eps<float>()), zero = pk2(0.f, 0.f);
 #pragma unroll
     for (int h = 0; h < NH; ++h) {
       A0[h] = pk2(p[2 * h].A0, p[2 * h + 1].A0);
@@ -242,9 +235,9 @@ __device__ __forceinline__ void lhy_points(const LhyNode<R>* __restrict__ nd, in
         const f32x2 A = fma2(A1[h], e.w, A0[h]);
         const f32x2 d = fma2(D1[h], e.w, D0[h]);
         const f32x2 s2 = fma2(d, d, mul2(e.e12sq, q4[h]));
-        const f32x2 rs = rsqrt_floor2(s2, s2_eps<float>());
+        const f32x2 rs = rsqrt2(add2(s2, eps));
         const f32x2 vp = max0_2(fma2(s2, rs, A));
-        const f32x2 rp = rsqrt_floor2(vp, s2_eps<float>());
+        const f32x2 rp = rsqrt2(add2(vp, eps));
         const f32x2 P1 = mul2(vp, rp);
         const f32x2 M1 = min2(mul2(mul2(e.gq, sq2[h]), rp), P1);
         const f32x2 p32 = mul2(vp, P1), m32 = mul2(mul2(M1, M1), M1);
@@ -368,7 +361,7 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
     const LhyNodeP* np = reinterpret_cast<const LhyNodeP*>(nd + Q);
     f32x2 A0[NH], A1c[NH], D0[NH], D1[NH], q4[NH], sq2[NH], b0[NH], b1[NH], e0[NH], e1[NH], m2[NH], mp2[NH],
         hh[NH];
-    const f32x2 c15 = pk2(1.5f, 1.5f);
+    const f32x2 eps = pk2(s2_eps<float>(), s2_eps<float>()), c15 = pk2(1.5f, 1.5f);
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
       const int j0 = 2 * i, j1 = 2 * i + 1;
@@ -394,9 +387,9 @@ __device__ __forceinline__ void lhy_hess(const LhyNode<R>* __restrict__ nd, int 
         const f32x2 A = fma2(A1c[i], e.w, A0[i]);
         const f32x2 d = fma2(D1[i], e.w, D0[i]);
         const f32x2 s2 = fma2(d, d, mul2(e.e12sq, q4[i]));
-        const f32x2 rs = rsqrt_floor2(s2, s2_eps<float>());
+        const f32x2 rs = rsqrt2(add2(s2, eps));
         const f32x2 vp = max0_2(fma2(s2, rs, A));
-        const f32x2 rp = rsqrt_floor2(vp, s2_eps<float>());
+        const f32x2 rp = rsqrt2(add2(vp, eps));
         const f32x2 P1 = mul2(vp, rp);
         const f32x2 M1 = min2(mul2(mul2(e.gq, sq2[i]), rp), P1);
         const f32x2 dP3 = sub2(mul2(vp, P1), mul2(mul2(M1, M1), M1));
