@@ -76,9 +76,7 @@ static bool make_col_map(CUtensorMap& tm, const void* base, int nx, int ny, int 
   cuuint32_t box[3] = {(cuuint32_t)(M * esz), axis == 1 ? (cuuint32_t)L : 1u, axis == 1 ? 1u : (cuuint32_t)L};
   cuuint32_t es[3] = {1, 1, 1};
   return fn(&tm, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE,
-            col_warp_layout<C>(axis, L, M) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -672,10 +670,8 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   const int block = M * TPL;
   const int other = (Op::AXIS == 1) ? nz : ny;
   const int tiles = (nx / M) * other * a.nf;
-  // the warp layout adds one padded line per column and 1024 bytes to align the swizzled tiles
   const size_t smem_tma = (size_t)kColStages * M * L * sizeof(C) + L * sizeof(C) + kColStages * sizeof(uint64_t) +
-                          (NS > 0 ? sizeof(RedSmem<NS>) : 0) +
-                          (col_warp_layout<C>(Op::AXIS, L, M) ? 1024 + (size_t)M * row_len_padded<R, L>() * sizeof(C) : 0);
+                          (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const size_t smem_plain = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   bool tma = tm && use_tma_;
   if (tma && !tune_.empty()) {

@@ -229,9 +229,6 @@ constexpr int kColStages = EGPE_COL_STAGES;
 #ifndef EGPE_COL_MINB
 #define EGPE_COL_MINB 1
 #endif
-#ifndef EGPE_COL_WARP
-#define EGPE_COL_WARP 1  // y passes: each line inside one warp (see colpass_tma_body_warp)
-#endif
 #ifndef EGPE_COL_BYTES
 #define EGPE_COL_BYTES 128  // row width of a column-pass tile (see col_tile_width)
 #endif
@@ -311,7 +308,7 @@ __global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
 // memory from registers.
 // ----------------------------------------------------------------------------
 template <class Op>
-__device__ __forceinline__ void colpass_tma_body_block(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
+__device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
   using R = typename Op::R;
   using C = C2<R>;
   constexpr int L = Op::L, NS = Op::NS;
@@ -407,127 +404,6 @@ __device__ __forceinline__ void colpass_tma_body_block(const CUtensorMap* tm, co
     }
   }
 }
-// Whether a TMA column pass uses the warp layout below (host and device
-// agree): plain y transforms of power-of-two length over 128-byte tile rows;
-// their tensor maps carry the 128-byte swizzle.
-template <class C> __host__ __device__ constexpr bool col_warp_layout(int axis, int L, int M) {
-  return EGPE_COL_WARP && axis == 1 && (L & (L - 1)) == 0 && M * (int)sizeof(C) == 128;
-}
-
-// Byte offset of element (pos, c) in a tile of 128-byte rows written by TMA
-// with the 128-byte swizzle (16-byte chunk index XOR row index mod 8; tile
-// base on a 1024-byte boundary).
-template <class C> __device__ __forceinline__ int swz_off(int pos, int c) {
-  const int byte = c * (int)sizeof(C);
-  return pos * 128 + ((((byte >> 4) ^ (pos & 7)) << 4) | (byte & 15));
-}
-
-// Plain y transform with each line's L/8 threads inside one warp: the
-// exchanges of the transform go through a padded line buffer of the warp's own
-// and synchronise per warp.  The line is read from the swizzled TMA tile and
-// its result written back to the same tile slots (each warp touches only its
-// own columns, so no block barrier is needed in between); the block then
-// writes the tile out in whole 128-byte rows.  Two block barriers per tile.
-template <class Op>
-__device__ __forceinline__ void colpass_tma_body_warp(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
-  using R = typename Op::R;
-  using C = C2<R>;
-  constexpr int L = Op::L, TPL = L / 8;
-  constexpr int NST = kColStages;
-  constexpr int LP = row_len_padded<R, L>();
-  static_assert(Op::NS == 0 && Op::AXIS == 1, "the warp layout serves the plain y transforms");
-  if (!gate_open(a)) return;
-  extern __shared__ __align__(128) unsigned char smraw_tma[];
-  unsigned char* base_sm = smraw_tma + ((1024u - (smem_u32(smraw_tma) & 1023u)) & 1023u);
-  const int M = a.M;
-  const int tileC = M * L;
-  C* tiles = reinterpret_cast<C*>(base_sm);  // NST swizzled tiles, each a multiple of 1024 bytes
-  C* exch = tiles + NST * tileC;              // one padded line per column
-  C* tw = exch + M * LP;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
-  const int tid = threadIdx.x;
-  const int c = tid / TPL, t = tid - c * TPL;                          // transform: column c, thread t of its line
-  const int m = tid % M, prow = tid / M, prows = (int)blockDim.x / M;  // copy-out: column m, rows prow + k prows
-  for (int i = tid; i < L; i += blockDim.x) tw[i] = a.twy[i];
-  if (tid == 0) {
-#pragma unroll
-    for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
-    fence_barrier_init();
-  }
-  __syncthreads();
-  const int xb_n = a.nx / M;
-  const int tiles_n = xb_n * a.nz * a.nf;
-  const size_t lstride = (size_t)a.nx;
-  const uint32_t bytes = (uint32_t)(tileC * sizeof(C));
-  constexpr int ESZ = (int)(sizeof(C) / 8);
-  auto issue = [&](int tile, int b) {
-    const int xb = tile % xb_n;
-    const int rest = tile / xb_n;
-    const int o = rest % a.nz;
-    const int f = a.f0 + rest / a.nz;
-    fence_proxy_async();
-    mbar_expect_tx(&bar[b], bytes);
-    tma_load_3d(tiles + b * tileC, tm, xb * M * ESZ, 0, f * a.nz + o, &bar[b]);
-  };
-  auto tile_of = [&](int q) { return (int)blockIdx.x + q * (int)gridDim.x; };
-  if (tid == 0) {
-#pragma unroll
-    for (int q = 0; q < NST - 1; ++q)
-      if (tile_of(q) < tiles_n) issue(tile_of(q), q);
-  }
-  bool timed_out = false;
-  int it = 0;
-  for (int tile = blockIdx.x; tile < tiles_n; tile += gridDim.x, ++it) {
-    const int b = it % NST;
-    const int ahead = tile_of(it + NST - 1);
-    // its buffer was last used by iteration it - 1, which ended with a barrier
-    if (tid == 0 && ahead < tiles_n) issue(ahead, (it + NST - 1) % NST);
-    const bool ok = mbar_wait(&bar[b], (uint32_t)((it / NST) & 1), kTmaWaitPolls);
-    if (__syncthreads_or(!ok)) {
-      timed_out = true;
-      break;
-    }
-    unsigned char* tb = reinterpret_cast<unsigned char*>(tiles + b * tileC);
-    C v[1][8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      v[0][e] = *reinterpret_cast<const C*>(tb + swz_off<C>(Plan<L>::entry_pos(Op::INV, t, e), c));
-    fft_line<C, L, Op::INV, 1>(v, exch + c * LP, 0, tw, t, RowIdx<PadShift<R>::v>{});
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      *reinterpret_cast<C*>(tb + swz_off<C>(Plan<L>::exit_pos(Op::INV, t, e), c)) = v[0][e];
-    __syncthreads();  // the whole tile is transformed
-    const int xb = tile % xb_n;
-    const int rest = tile / xb_n;
-    const int o = rest % a.nz;
-    const int f = a.f0 + rest / a.nz;
-    C* dst = a.gout + (size_t)f * a.N + (size_t)o * a.nx * a.ny + (size_t)xb * M + m;
-    for (int pos = prow; pos < L; pos += prows)
-      dst[(size_t)pos * lstride] = *reinterpret_cast<const C*>(tb + swz_off<C>(pos, m));
-    __syncthreads();  // buffer b may be refilled from the next iteration on
-  }
-  if (timed_out) {
-    // let every copy already issued land (each wait bounded) before exiting
-    for (int q = it; q < it + NST; ++q)
-      if (tile_of(q) < tiles_n) mbar_wait(&bar[q % NST], (uint32_t)((q / NST) & 1), kTmaWaitPolls);
-    if (tid == 0) {
-      a.st->status = 7;  // EGPE_ERR_TIMEOUT
-      a.st->phase = PH_DONE;
-    }
-  }
-}
-
-template <class Op>
-__device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
-  if constexpr (Op::AXIS == 1 && Op::NS == 0 && IsPow2<Op::L>::v && EGPE_COL_WARP) {
-    if (col_warp_layout<C2<typename Op::R>>(1, Op::L, a.M)) {
-      colpass_tma_body_warp<Op>(tm, a);
-      return;
-    }
-  }
-  colpass_tma_body_block<Op>(tm, a);
-}
-
 template <class Op>
 __global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
     colpass_tma_kernel(const __grid_constant__ CUtensorMap tm, KArgs<typename Op::R> a) {
