@@ -420,7 +420,11 @@ def time_to_ground_state(E, h, grid, prm, psi64, pc, fp32_switch):
     """Wall time of egpe_ncg_solve from the seeded start until |E - E_ref| <=
     1e-8 |E_ref|, mixed (FP32 phase then FP64 polish) against FP64 only.
     E_ref: FP64 solve to ||r|| <= 1e-10.  The residual target r* is the
-    residual of the reference run at its first point within the accuracy."""
+    residual of the reference run at its first point within the accuracy.
+    Both timed solves run on handles that have solved once already (the FP64
+    one ran the reference, the mixed one an untimed solve from the same start),
+    so neither pays graph capture or first-launch set-up; the mixed handle's
+    first solve is reported as seconds_cold."""
     o = E.egpe_default_solve_opts()
     o.precond = pc
     o.tol_res = 1e-10
@@ -444,11 +448,14 @@ def time_to_ground_state(E, h, grid, prm, psi64, pc, fp32_switch):
         t64 = r64[0]
         o.tol_fp32_switch = fp32_switch
         x = psi64.clone()
+        st, rc, _ = E.egpe_ncg_solve(h, [x], o, 1)
+        x = psi64.clone()
         st, rm, _ = E.egpe_ncg_solve(h, [x], o, 1)
         tm = rm[0]
         return {"E_ref": Eref, "ref_iters": reps[0]["iters"], "ref_status": reps[0]["status"], "res_target": rstar,
                 "fp64": {"seconds": t64["seconds"], "iters": t64["iters"], "rel_err": abs(t64["E"] - Eref) / abs(Eref)},
-                "mixed": {"seconds": tm["seconds"], "iters": tm["iters"], "iters_fp32": tm["iters_fp32"],
+                "mixed": {"seconds": tm["seconds"], "seconds_cold": rc[0]["seconds"], "iters": tm["iters"],
+                          "iters_fp32": tm["iters_fp32"],
                           "rel_err": abs(tm["E"] - Eref) / abs(Eref), "fp32_switch": fp32_switch},
                 "speedup": t64["seconds"] / tm["seconds"]}
     finally:
