@@ -821,6 +821,13 @@ def config_table(args):
             E.egpe_destroy(h)
         eg = prof[-5:]  # the trial energy/gradient pass: x fwd, y, z fused, y, x inv
         eg_gbs = sum(b for _, _, b in eg) / (sum(t for _, t, _ in eg) * 1e-3) / 1e9
+        if args.no_cpu:  # GPU columns only
+            rows[key] = {"grid": list(w.n), "gpu_fp64_tts_s": round(tts["fp64"]["seconds"], 4),
+                         "gpu_mixed_tts_s": round(tts["mixed"]["seconds"], 4),
+                         "gpu_mixed_tts_cold_s": round(tts["mixed"]["seconds_cold"], 4),
+                         "gpu_fp64_iters": tts["fp64"]["iters"], "fp32_eg_pass_frac_hbm": round(eg_gbs / hbm, 3)}
+            print(json.dumps({key: rows[key]}), flush=True)
+            continue
         g = O.Grid(w.n, w.L)
         op = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
         t0 = time.perf_counter()
@@ -845,6 +852,9 @@ def config_table(args):
             row["oracle_tts_s_extrapolated"] = round(s_iter * tts["fp64"]["iters"] + t_eval, 1)
         rows[key] = row
         print(json.dumps({key: row}), flush=True)
+    if args.no_cpu:
+        print(json.dumps({"table": rows}))
+        return
     # the 64-instance scan: oracle seconds per iteration on one sampled instance per grid size
     scan = I.scan_workloads()
     c4 = {}
