@@ -45,7 +45,9 @@ def _digest() -> str:
             if name.endswith((".cu", ".cuh", ".h")):
                 with open(os.path.join(d, name), "rb") as f:
                     h.update(name.encode() + f.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # flags without the machine-specific include path, so the digest names the
+    # sources and options alone (it stamps profiles taken on another machine)
+    h.update(" ".join(ARCH + [f for f in FLAGS if not f.startswith("-I")]).encode())
     h.update(repr(sorted(UNIT_FLAGS.items())).encode())
     return h.hexdigest()
 
