@@ -31,7 +31,6 @@
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvW3>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XFwdPC>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvPC>(int, const KArgs<R>&);                        \
-  template egpe_status Engine<R>::dispatch_x_##SFX<XInvPCz>(int, const KArgs<R>&);                       \
   template egpe_status Engine<R>::dispatch_x_##SFX<XFwdLC>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvLC>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvW1F2>(int, const KArgs<R>&);                      \

@@ -825,12 +825,7 @@ template <class R> egpe_status Engine<R>::enq_pc(int mode, int gate, int ctrl, i
     EGPE_TRY(dispatch_col<ZPc>(nz, a, tmz()));
     EGPE_TRY(plain_col(1, 1, y, tmy()));
     a.ctrl = ctrl;
-    if (!EGPE_SPLIT_PC) return dispatch_x<XInvPC>(nx, a);
-    a.ctrl = 0;
-    EGPE_TRY(dispatch_x<XInvPCz>(nx, a));
-    a.ctrl = ctrl;
-    return launch_point(pc_sums_kernel<R>, pc_sums_kernel_b<R>, "precond sums", 10.0 * N * sizeof(C), a,
-                        (long long)((N + 511) / 512));
+    return dispatch_x<XInvPC>(nx, a);
   }
   a.ctrl = ctrl;
   return launch_point(pc_point_kernel<R>, pc_point_kernel_b<R>, "pointwise precond sums",

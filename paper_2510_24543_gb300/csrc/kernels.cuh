@@ -951,123 +951,6 @@ template <class R_, int L_> struct XInvPC {
   }
 };
 
-// Split form of the preconditioner's last pass: the x inverse stores z alone
-// (blended with P_V where asked), and a pointwise kernel forms the sums.  The
-// fused epilogue holds 167 registers a thread and waits on its ten field reads
-// at three resident 128-thread blocks per SM; the pointwise kernel streams them
-// with 32 resident warps per SM.
-#ifndef EGPE_SPLIT_PC
-#define EGPE_SPLIT_PC 1
-#endif
-template <class R_, int L_> struct XInvPCz {
-  using R = R_;
-  using C = C2<R>;
-  static constexpr const char* NAME = "x-inv precond";
-  static double alg_bytes(const KArgs<R>& a) { return (a.blend ? 9.0 : 4.0) * a.N * sizeof(C); }
-  static constexpr int L = L_, NF = 2, NS = 0;
-  static constexpr bool INV = true, USES_LHY = false;
-  using Uni = PcUni<R>;
-  static __device__ void uniform(const KArgs<R>& a, Uni& u) { pc_uniform(a, u); }
-  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*) {
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
-      v[0][e] = valid ? a.W[idx] : cmk<C>(0, 0);
-      v[1][e] = valid ? a.W[(size_t)a.N + idx] : cmk<C>(0, 0);
-    }
-  }
-  static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], PAcc<R>*,
-                               const LhyNode<R>*) {
-    if (!valid) return;
-    const size_t N = a.N;
-    const int yy = row % a.ny, zz = row / a.ny;
-    const R Yc = -a.Ly + (R)yy * a.hy, Zc = -a.Lz + (R)zz * a.hz;
-    const R vyz = a.vy * Yc * Yc + a.vz * Zc * Zc;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int x = Plan<L>::exit_pos(true, t, e);
-      const size_t idx = (size_t)row * a.nx + x;
-      C z1 = v[0][e], z2 = v[1][e];
-      if (a.blend) {  // z = (1 - w) P_Delta^{-1} r + w P_V^{-1} r, as in XInvPC
-        const C r1 = a.rb[u.nsel][idx], r2 = a.rb[u.nsel][N + idx];
-        const C p1 = a.psi[u.cur][idx], p2 = a.psi[u.cur][N + idx];
-        const C ml = a.ax[u.cur][N + idx];
-        const R X = -a.Lx + (R)x * a.hx;
-        const R V = a.vx * X * X + vyz;
-        const R n1 = cabs2(p1), n2 = cabs2(p2);
-        R P1 = u.shift[0] + V + a.g11 * n1 + a.g12 * n2 + ml.x;
-        R P2 = u.shift[1] + V + a.g21 * n1 + a.g22 * n2 + ml.y;
-        P1 = P1 > u.floor_[0] ? P1 : u.floor_[0];
-        P2 = P2 > u.floor_[1] ? P2 : u.floor_[1];
-        const R wd = R(1) - u.wv, w1 = u.wv / P1, w2 = u.wv / P2;
-        z1 = cmk<C>(wd * z1.x + w1 * r1.x, wd * z1.y + w1 * r1.y);
-        z2 = cmk<C>(wd * z2.x + w2 * r2.x, wd * z2.y + w2 * r2.y);
-      }
-      a.z[idx] = z1;
-      a.z[N + idx] = z2;
-    }
-  }
-  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
-  static __device__ void finish(const KArgs<R>&, Uni&) {}
-};
-
-// The preconditioner sums over z already stored (second half of the split
-// pass; with ctrl, the controller step after the transform preconditioner).
-template <class R> __device__ __forceinline__ void pc_sums_body(const KArgs<R>& a) {
-  using C = C2<R>;
-  if (!gate_open(a)) return;
-  __shared__ RedSmem<PC_NS> red;
-  PcUni<R> u;
-  pc_uniform(a, u);
-  PAcc<R> acc[PC_NS];
-  const size_t N = a.N;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  constexpr int U = 1;  // points per thread and iteration (more spill at the register bound below)
-  for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += U * stride) {
-    PcSumIn<R> in[U];
-    C z1[U], z2[U];
-    bool ok[U];
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const size_t idx = i0 + (size_t)j * stride;
-      ok[j] = idx < N;
-      const size_t id = ok[j] ? idx : 0;
-      pc_sum_load<R>(a, u, id, in[j]);
-      z1[j] = a.z[id];
-      z2[j] = a.z[N + id];
-    }
-    R s[PC_NS];
-#pragma unroll
-    for (int q = 0; q < PC_NS; ++q) s[q] = 0;
-#pragma unroll
-    for (int j = 0; j < U; ++j)
-      if (ok[j]) pc_sum_add<R>(in[j], z1[j], z2[j], s);
-#pragma unroll
-    for (int q = 0; q < PC_NS; ++q) acc[q].add(s[q]);
-  }
-  double dacc[PC_NS];
-#pragma unroll
-  for (int q = 0; q < PC_NS; ++q) dacc[q] = acc[q].get();
-  if (reduce_blocks<PC_NS>(dacc, a.partials, a.counter, a.st->pc, red)) {
-    if (threadIdx.x == 0 && a.ctrl) {
-      a.st->ffts += 4;
-      ctrl_after_pc(a.st);
-    }
-  }
-}
-// resident blocks per SM the sums kernel is compiled for (FP32: 64 registers
-// a thread, 32 warps per SM, no spills)
-template <class R> struct PcSumsMinB {
-  static constexpr int v = sizeof(R) == 4 ? 4 : 2;
-};
-template <class R> __global__ void __launch_bounds__(256, PcSumsMinB<R>::v) pc_sums_kernel(KArgs<R> a) {
-  pc_sums_body(a);
-}
-template <class R>
-__global__ void __launch_bounds__(256, PcSumsMinB<R>::v) pc_sums_kernel_b(const __grid_constant__ KBatch<R> kb) {
-  pc_sums_body(kb.k[blockIdx.y]);
-}
-
 // Pointwise preconditioner (modes none and diagonal): one pass, no transform.
 template <class R>
 __device__ __forceinline__ void pc_point_body(const KArgs<R>& a) {
