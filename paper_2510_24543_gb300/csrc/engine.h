@@ -185,8 +185,6 @@ template <class R> class Engine {
   };
   std::vector<KTime> tlog_;
   bool timing_ = false;
-  // LHY epilogues as separate pointwise kernels (true) or fused into the last x pass
-  bool split_lhy_ = false;
   // strided passes fed by TMA (tensor maps over the workspace W)
   bool use_tma_ = true;
   bool have_maps_ = false;

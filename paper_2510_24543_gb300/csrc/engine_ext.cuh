@@ -28,12 +28,10 @@
   namespace egpe {                                                                                       \
   template egpe_status Engine<R>::dispatch_x_##SFX<XFwdEG>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvEG>(int, const KArgs<R>&);                        \
-  template egpe_status Engine<R>::dispatch_x_##SFX<XInvW3>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XFwdPC>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvPC>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XFwdLC>(int, const KArgs<R>&);                        \
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvLC>(int, const KArgs<R>&);                        \
-  template egpe_status Engine<R>::dispatch_x_##SFX<XInvW1F2>(int, const KArgs<R>&);                      \
   template egpe_status Engine<R>::dispatch_x_##SFX<XFwdKin>(int, const KArgs<R>&);                       \
   template egpe_status Engine<R>::dispatch_x_##SFX<XInvKin>(int, const KArgs<R>&);                       \
   template egpe_status Engine<R>::dispatch_x_##SFX<XFwdPG>(int, const KArgs<R>&);                        \

@@ -798,12 +798,7 @@ template <class R> egpe_status Engine<R>::enq_eg(int trial, int gate, int ctrl) 
   EGPE_TRY(dispatch_col<ZEg>(nz, a, tmz()));
   EGPE_TRY(plain_col(1, 1, y, tmy()));
   a.ctrl = ctrl;
-  if (!split_lhy_) return dispatch_x<XInvEG>(nx, a);
-  a.ctrl = 0;
-  EGPE_TRY(dispatch_x<XInvW3>(nx, a));
-  a.ctrl = ctrl;
-  return launch_point(eg_point_kernel<R>, eg_point_kernel_b<R>, "energy+LHY pointwise", 9.0 * N * sizeof(C), a,
-                      (long long)((N + 511) / 512));
+  return dispatch_x<XInvEG>(nx, a);
 }
 
 // Preconditioner pipeline: 4 transforms for the kinetic modes, none otherwise.
@@ -850,12 +845,7 @@ template <class R> egpe_status Engine<R>::enq_lc(int gate, int ctrl, int pgiven)
   y.f0 = 2;
   EGPE_TRY(plain_col(1, 1, y, tmy()));
   a.ctrl = ctrl;
-  if (!split_lhy_) return dispatch_x<XInvLC>(nx, a);
-  a.ctrl = 0;
-  EGPE_TRY(dispatch_x<XInvW1F2>(nx, a));
-  a.ctrl = ctrl;
-  return launch_point(lc_point_kernel<R>, lc_point_kernel_b<R>, "line sums+LHY pointwise", 9.0 * N * sizeof(C), a,
-                      (long long)((N + 511) / 512));
+  return dispatch_x<XInvLC>(nx, a);
 }
 
 template <class R> egpe_status Engine<R>::enq_attempt(int mode) {

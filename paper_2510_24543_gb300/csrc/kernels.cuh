@@ -1501,205 +1501,6 @@ template <class R_, int L_> struct XInvPG {
 };
 
 // ----------------------------------------------------------------------------
-// Split epilogues: the last x pass only inverts the workspace in place, and a
-// pointwise kernel with high occupancy evaluates the LHY quadrature, H psi and
-// the sums.  (Same arithmetic as the fused XInvEG / XInvLC epilogues; the LHY
-// node loop is issue-bound, and out of the transform kernel it runs with four
-// times the resident warps.)
-// ----------------------------------------------------------------------------
-template <class R_, int L_, int NF_, int F0_> struct XInvW {
-  using R = R_;
-  using C = C2<R>;
-  static constexpr int L = L_, NF = NF_, NS = 0;
-  static constexpr bool INV = true, USES_LHY = false;
-  static constexpr const char* NAME = NF_ == 3 ? "x-inv workspace (3 fields)" : "x-inv workspace (1 field)";
-  static double alg_bytes(const KArgs<R>& a) { return 2.0 * NF * a.N * sizeof(C); }
-  using Uni = NoUni;
-  static __device__ void uniform(const KArgs<R>&, Uni&) {}
-  static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[NF][8], PAcc<R>*) {
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const size_t idx = (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) v[f][e] = valid ? a.W[(size_t)(F0_ + f) * a.N + idx] : cmk<C>(0, 0);
-    }
-  }
-  static __device__ void store(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[NF][8], PAcc<R>*,
-                               const LhyNode<R>*) {
-    if (!valid) return;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) a.W[(size_t)(F0_ + f) * a.N + idx] = v[f][e];
-    }
-  }
-  static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
-  static __device__ void finish(const KArgs<R>&, Uni&) {}
-};
-template <class R, int L> using XInvW3 = XInvW<R, L, 3, 0>;
-template <class R, int L> using XInvW1F2 = XInvW<R, L, 1, 2>;
-
-template <class R> __device__ __forceinline__ R trap_at(const KArgs<R>& a, size_t idx) {
-  const int x = (int)(idx % a.nx);
-  const size_t r = idx / a.nx;
-  const int y = (int)(r % a.ny), z = (int)(r / a.ny);
-  const R X = -a.Lx + (R)x * a.hx, Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
-  return a.vx * X * X + a.vy * Y * Y + a.vz * Z * Z;
-}
-
-// Energy/gradient epilogue, pointwise: W fields 0, 1 hold T psi_1, T psi_2 and
-// field 2 holds Phi_1 + i Phi_2 (already inverse transformed).
-template <class R> __device__ __forceinline__ void eg_point_body(const KArgs<R>& a) {
-  using C = C2<R>;
-  constexpr int NP = 2;
-  if (!gate_open(a)) return;
-  __shared__ __align__(16) unsigned char nodes_raw[lhy_stage_bytes<R>(64)];
-  LhyNode<R>* nodes = reinterpret_cast<LhyNode<R>*>(nodes_raw);
-  __shared__ RedSmem<EG_NS> red;
-  stage_lhy_nodes(nodes, a.nodes, a.Q);
-  __syncthreads();
-  EgUni<R> u;
-  XFwdEG<R, 16>::uniform(a, u);
-  const C* ps = a.psi[u.slot];
-  C* hp = a.hp[u.slot];
-  C* ax = a.ax[u.slot];
-  const size_t N = a.N;
-  const LhyCoef<R> cf = lhy_coef(a);
-  double acc[EG_NS];
-  R s[EG_NS];  // field-precision partials over this thread's points
-#pragma unroll
-  for (int k = 0; k < EG_NS; ++k) s[k] = 0;
-  const size_t span = (size_t)blockDim.x * NP;
-  for (size_t base = (size_t)blockIdx.x * span; base < N; base += (size_t)gridDim.x * span) {
-    R n1[NP], n2[NP], F[NP], m1[NP], m2[NP];
-    C p1[NP], p2[NP];
-    bool ok[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      const size_t idx = base + threadIdx.x + (size_t)j * blockDim.x;
-      ok[j] = idx < N;
-      const size_t id = ok[j] ? idx : 0;
-      p1[j] = ps[id];
-      p2[j] = ps[N + id];
-      n1[j] = ok[j] ? cabs2(p1[j]) : R(0);
-      n2[j] = ok[j] ? cabs2(p2[j]) : R(0);
-    }
-    lhy_points<R, NP>(nodes, a.Q, a.Qm, cf, n1, n2, F, m1, m2);
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      if (!ok[j]) continue;
-      const size_t idx = base + threadIdx.x + (size_t)j * blockDim.x;
-      const C t1 = a.W[idx], t2 = a.W[N + idx], phi = a.W[2 * N + idx];
-      const R V = trap_at(a, idx);
-      const R U1 = V + a.g11 * n1[j] + a.g12 * n2[j] + phi.x + m1[j];
-      const R U2 = V + a.g21 * n1[j] + a.g22 * n2[j] + phi.y + m2[j];
-      const C H1 = cmk<C>(t1.x + U1 * p1[j].x, t1.y + U1 * p1[j].y);
-      const C H2 = cmk<C>(t2.x + U2 * p2[j].x, t2.y + U2 * p2[j].y);
-      hp[idx] = H1;
-      hp[N + idx] = H2;
-      ax[idx] = phi;
-      ax[N + idx] = cmk<C>(m1[j], m2[j]);
-      s[EG_TRAP] += V * (n1[j] + n2[j]);
-      s[EG_CONTACT] += R(0.5) * (a.g11 * n1[j] * n1[j] + (a.g12 + a.g21) * n1[j] * n2[j] + a.g22 * n2[j] * n2[j]);
-      s[EG_DIPOLAR] += R(0.5) * (n1[j] * phi.x + n2[j] * phi.y);
-      s[EG_LHY] += F[j];
-      s[EG_MU1] += cdot(p1[j], H1);
-      s[EG_MU2] += cdot(p2[j], H2);
-      s[EG_NPHI1] += n1[j] * phi.x;
-      s[EG_NPHI2] += n2[j] * phi.y;
-      s[EG_NMUL1] += n1[j] * m1[j];
-      s[EG_NMUL2] += n2[j] * m2[j];
-      s[EG_NORM1] += n1[j];
-      s[EG_NORM2] += n2[j];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < EG_NS; ++k) acc[k] = (double)s[k];
-  if (reduce_blocks<EG_NS>(acc, a.partials, a.counter, a.st->eg[u.slot], red)) {
-    if (threadIdx.x == 0) eg_ctrl(a);
-  }
-}
-template <class R> __global__ void __launch_bounds__(256) eg_point_kernel(KArgs<R> a) { eg_point_body(a); }
-template <class R> __global__ void __launch_bounds__(256) eg_point_kernel_b(const __grid_constant__ KBatch<R> kb) {
-  eg_point_body(kb.k[blockIdx.y]);
-}
-
-
-// Line-search epilogue, pointwise: W field 2 holds Phi[rho] (inverse transformed).
-template <class R> __device__ __forceinline__ void lc_point_body(const KArgs<R>& a) {
-  using C = C2<R>;
-  constexpr int NP = 2;
-  if (!gate_open(a)) return;
-  __shared__ __align__(16) unsigned char nodes_raw[lhy_stage_bytes<R>(64)];
-  LhyNode<R>* nodes = reinterpret_cast<LhyNode<R>*>(nodes_raw);
-  __shared__ RedSmem<LC_NS> red;
-  stage_lhy_nodes(nodes, a.nodes, a.Q);
-  __syncthreads();
-  LcUni<R> u;
-  lc_uniform(a, u);
-  const size_t N = a.N;
-  const C* ps = a.psi[u.cur];
-  const C* pd = a.pb[u.nsel];
-  const C* hp = a.hp[u.cur];
-  const C* ax = a.ax[u.cur];
-  const LhyCoef<R> cf = lhy_coef(a);
-  double acc[LC_NS];
-  R s[LC_NS];  // field-precision partials over this thread's points
-#pragma unroll
-  for (int k = 0; k < LC_NS; ++k) s[k] = 0;
-  const size_t span = (size_t)blockDim.x * NP;
-  for (size_t base = (size_t)blockIdx.x * span; base < N; base += (size_t)gridDim.x * span) {
-    R n1[NP], n2[NP], n1p[NP], n2p[NP], Hh[NP];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      const size_t idx = base + threadIdx.x + (size_t)j * blockDim.x;
-      n1[j] = n2[j] = n1p[j] = n2p[j] = R(0);
-      if (idx >= N) continue;
-      const C p1 = ps[idx], p2 = ps[N + idx];
-      const C q1 = pd[idx], q2 = pd[N + idx];
-      const C h1 = hp[idx], h2 = hp[N + idx];
-      const C phi = ax[idx], ml = ax[N + idx];
-      const C phr = a.W[2 * N + idx];
-      n1[j] = cabs2(p1);
-      n2[j] = cabs2(p2);
-      const R a1 = cabs2(q1), a2 = cabs2(q2);
-      const R rho1 = cdot(p1, q1), rho2 = cdot(p2, q2);
-      n1p[j] = R(2) * rho1;
-      n2p[j] = R(2) * rho2;
-      const R V = trap_at(a, idx);
-      const R U1 = V + a.g11 * n1[j] + a.g12 * n2[j] + phi.x + ml.x;
-      const R U2 = V + a.g21 * n1[j] + a.g22 * n2[j] + phi.y + ml.y;
-      s[LC_P1] += a1;
-      s[LC_P2] += a2;
-      s[LC_PSIP1] += rho1;
-      s[LC_PSIP2] += rho2;
-      s[LC_PH1] += cdot(q1, h1);
-      s[LC_PH2] += cdot(q2, h2);
-      s[LC_UPP1] += U1 * a1;
-      s[LC_UPP2] += U2 * a2;
-      s[LC_SRHO] += rho1 * (a.g11 * rho1 + a.g12 * rho2 + phr.x) + rho2 * (a.g21 * rho1 + a.g22 * rho2 + phr.y);
-    }
-    lhy_hess<R, NP>(nodes, a.Q, a.Qm, cf, n1, n2, n1p, n2p, Hh);
-#pragma unroll
-    for (int j = 0; j < NP; ++j) s[LC_HLHY] += Hh[j];
-  }
-#pragma unroll
-  for (int k = 0; k < LC_NS; ++k) acc[k] = (double)s[k];
-  if (reduce_blocks<LC_NS>(acc, a.partials, a.counter, a.st->lc, red)) {
-    if (threadIdx.x == 0 && a.ctrl) {
-      a.st->ffts += 4;
-      ctrl_after_lc(a.st);
-    }
-  }
-}
-template <class R> __global__ void __launch_bounds__(256) lc_point_kernel(KArgs<R> a) { lc_point_body(a); }
-template <class R> __global__ void __launch_bounds__(256) lc_point_kernel_b(const __grid_constant__ KBatch<R> kb) {
-  lc_point_body(kb.k[blockIdx.y]);
-}
-
-
-// ----------------------------------------------------------------------------
 // Small pointwise kernels: retraction sums and apply, residual norm, casts.
 // ----------------------------------------------------------------------------
 // sums over (psi = gin, p = gout-as-input) for the standalone retraction
