@@ -800,10 +800,11 @@ def config_table(args):
     times the iterations the GPU FP64 solve needed (labelled)."""
     import torch
 
-    import oracle as O
     from paper_2510_24543_gb300 import egpe as E
     from paper_2510_24543_gb300 import inputs as I
 
+    if not args.no_cpu:
+        import oracle as O  # the CPU baseline columns only
     E.load()
     hbm, _ = peaks()
     rows = {}
