@@ -95,3 +95,13 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             mod.load(str(tmp_path / "missing.so"))
     finally:
         mod._lib = saved
+
+
+def test_source_digest_ignores_the_machine_include_path(monkeypatch):
+    """The digest that stamps builds and committed profiles names the sources
+    and compiler options, not where the repository sits on a machine."""
+    d0 = B._digest()
+    monkeypatch.setattr(B, "FLAGS", [f if not f.startswith("-I") else "-I/elsewhere/include" for f in B.FLAGS])
+    assert B._digest() == d0
+    monkeypatch.setattr(B, "FLAGS", B.FLAGS + ["-DEXTRA"])
+    assert B._digest() != d0
