@@ -15,7 +15,8 @@ paper is silent or garbled are named in each docstring.  All functions are
 pinned by tests against closed forms, invariants, brute force or library
 routines (``tests/test_oracle_pins.py``).  Parity status per function:
 
-* energy/gradient, Hamiltonian, LHY, dipolar term, kinetic term: pinned
+* energy/gradient, Hamiltonian, LHY, dipolar term, kinetic term: pinned (LHY
+  also by Euler's identity n1 mu1 + n2 mu2 = 5/2 F of its degree-5/2 density)
 * line-search coefficients E', E'': pinned (finite differences along the exact
   geodesic)
 * preconditioners, beta, projection, retraction, NCG loop: pinned (invariants,
