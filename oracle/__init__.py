@@ -19,7 +19,12 @@ routines (``tests/test_oracle_pins.py``).  Parity status per function:
   also by Euler's identity n1 mu1 + n2 mu2 = 5/2 F of its degree-5/2 density)
 * line-search coefficients E', E'': pinned (finite differences along the exact
   geodesic)
-* preconditioners, beta, projection, retraction, NCG loop: pinned (invariants,
+* preconditioner shift alpha_i and P_V: pinned (harmonic closed form; a
+  single-component plane-wave state whose kinetic, dipolar and LHY terms have
+  closed forms)
+* beta (HS+ and PR+): pinned (hand-built fields with exactly known inner
+  products: values, the max(., 0) clamp, zero-denominator restarts)
+* P_Delta, projection, retraction, NCG loop: pinned (plane waves, invariants,
   harmonic closed form, descent, symmetry, agreement with ITE)
 * ITE reference: pinned (harmonic closed form, agreement with NCG)
 * parameter derivatives dE/d(g, g_dd, kappa, eta_s, trap): pinned (central
@@ -31,6 +36,6 @@ from .egpe import (  # noqa: F401
     Grid, Params, SolveOpts, Evaluation,
     gauss_legendre_01, inner, kinetic_apply, trap_potential, dipolar_potentials,
     lhy_density_and_mu, evaluate, energy_grad, line_coeffs, line_coeffs_detail,
-    preconditioner_shift, precondition, project, retract, ncg_solve, ite_solve,
+    preconditioner_shift, precondition, project, retract, cg_beta, ncg_solve, ite_solve,
     lhy_eta_derivatives, param_grad, PARAM_NAMES, PRECOND_MODES,
 )

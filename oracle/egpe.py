@@ -459,6 +459,31 @@ def retract(grid: Grid, psi: np.ndarray, p: np.ndarray, theta) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Preconditioned nonlinear CG on the product of spheres (Algorithm 1)
 # ----------------------------------------------------------------------------
+def cg_beta(grid: Grid, r: np.ndarray, z: np.ndarray, r_prev: np.ndarray, p_prev: np.ndarray,
+            rz_prev: Optional[float], rule: str = "HS"):
+    """Conjugacy coefficient of the preconditioned NCG direction (Sec. IV.C).
+
+    With z = P^{-1} r and sums over both components (one global beta; Algorithm 1
+    carries no component index on beta):
+      HS+: beta = max( sum_i Re<r_i - r_prev_i, z_i> / sum_i Re<r_i - r_prev_i, p_prev_i>, 0 )
+      PR+: beta = max( sum_i Re<r_i - r_prev_i, z_i> / rz_prev, 0 ),
+           rz_prev = sum_i Re<r_prev_i, z_prev_i>
+    Readings: the HS denominator takes the previous direction p^{n-1} (the printed
+    p^{(n)} would be circular); the PR denominator is the stored value of the
+    previous iteration, i.e. with the preconditioner of iteration n-1.
+    Returns (beta, ok); ok is False when the denominator is zero or either sum is
+    not finite, which the solver treats as a restart (beta = 0).
+    """
+    num = sum(inner(grid, r[i] - r_prev[i], z[i]).real for i in range(2))
+    if rule == "PR":
+        den = rz_prev
+    else:
+        den = sum(inner(grid, r[i] - r_prev[i], p_prev[i]).real for i in range(2))
+    if den is None or den == 0.0 or not np.isfinite(den) or not np.isfinite(num):
+        return 0.0, False
+    return max(num / den, 0.0), True
+
+
 @dataclass
 class SolveOpts:
     precond: str = "kinetic"
@@ -527,17 +552,8 @@ def ncg_solve(grid: Grid, prm: Params, psi0: np.ndarray, opts: SolveOpts = Solve
         beta = 0.0
         rz = sum(inner(grid, r[i], z[i]).real for i in range(2))
         if not restart:
-            num = sum(inner(grid, r[i] - r_prev[i], z[i]).real for i in range(2))
-            if opts.beta_rule == "PR":
-                # PR+: Re<r^n - r^{n-1}, P^{-1} r^n> / Re<r^{n-1}, P^{-1} r^{n-1}> (Sec. IV.C);
-                # reading: the denominator uses the preconditioner of iteration n-1
-                den = rz_prev
-            else:
-                den = sum(inner(grid, r[i] - r_prev[i], p_prev[i]).real for i in range(2))
-            if den == 0.0 or not np.isfinite(den) or not np.isfinite(num):
-                restart = True
-            else:
-                beta = max(num / den, 0.0)
+            beta, ok = cg_beta(grid, r, z, r_prev, p_prev, rz_prev, opts.beta_rule)
+            restart = not ok
         d = -z + beta * p_prev if beta != 0.0 else -z
         p = project(grid, psi, d)
         descent = sum(inner(grid, r[i], p[i]).real for i in range(2))

@@ -338,6 +338,151 @@ def test_preconditioners_are_positive():
         assert np.max(np.abs(z[i] - wave / (alpha[i] + 0.5 * k * k))) < 1e-13
 
 
+def test_preconditioner_shift_and_pv_harmonic_closed_form():
+    """g = g_dd = kappa = 0 at the harmonic ground state: alpha_i = mu_i =
+    (lx+ly+lz)/2 exactly, P_V,i = alpha_i + V pointwise, so the diagonal mode is
+    z = r/(alpha_i + V); the kinetic mode with that alpha acts on a plane wave
+    as 1/(alpha + |k|^2/2); the composed mode is P_Delta^{-1}(P_V^{-1} r) (Sec. IV.B)."""
+    trap = (1.0, 1.5, 2.0)
+    g = O.Grid((32, 32, 40), (7.0, 7.0, 6.0))
+    psi = _harmonic_gs(g, trap)
+    prm = _prm(trap=trap)
+    ev = O.evaluate(g, prm, psi)
+    alpha = O.preconditioner_shift(g, ev, psi)
+    assert np.allclose(alpha, sum(trap) / 2.0, atol=1e-12, rtol=0)
+    X = [g.x[0][None, None, :], g.x[1][None, :, None], g.x[2][:, None, None]]
+    V = 0.5 * sum(trap[a] ** 2 * X[a] ** 2 for a in range(3))
+    r = I.random_fields(psi.shape, 31)
+    z = O.precondition(g, prm, ev, psi, r, "diagonal")
+    for i in range(2):
+        assert np.max(np.abs(z[i] - r[i] / (sum(trap) / 2.0 + V))) < 1e-13 * np.max(np.abs(r[i]))
+    k = math.pi / g.L[0] * 4
+    wave = np.exp(1j * k * X[0]) * np.ones(g.shape)
+    zk = O.precondition(g, prm, ev, psi, np.stack([wave, 2 * wave]), "kinetic")
+    for i in range(2):
+        assert np.max(np.abs(zk[i] - (i + 1) * wave / (sum(trap) / 2.0 + 0.5 * k * k))) < 1e-13
+    zkd = O.precondition(g, prm, ev, psi, r, "kinetic+diagonal")
+    assert np.max(np.abs(zkd - O.precondition(g, prm, ev, psi, z, "kinetic"))) < 1e-14 * np.max(np.abs(zkd))
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_preconditioner_shift_and_pv_plane_wave_closed_form(comp):
+    """One occupied component psi_c = a + b cos(k z) (the other zero) with every
+    coupling on.  Its terms have closed forms: T psi_c = b k^2/2 cos(kz); the
+    density has modes 0, k, 2k along z, so Phi_c = 2 gdd_cc (density minus its
+    mean) (kernel +2 g_dd along the dipoles, 0 at k = 0); with the other
+    density zero the LHY chemical potential is the single-component
+    mu_LHY = (5/2) kappa eta_s^{-5/2} (2 g_cc)^{5/2} n^{3/2} Q5(gdd_cc/g_cc).  Hence
+    alpha_c = <psi,T psi> + int (V + g_cc n + mu_LHY) n (the dipolar energy
+    excluded) and P_V,c = max(|alpha_c| + V + g_cc n + mu_LHY, 1e-2 |alpha_c|).
+    Adding Phi to P_V, dropping mu_LHY or V, or taking mu_c for alpha_c fails."""
+    g = O.Grid((8, 10, 16), (3.0, 3.5, 4.0))
+    trap = (0.7, 0.9, 1.3)
+    gm = np.array([[310.0, 140.0], [140.0, 260.0]])
+    gdd = np.array([[220.0, 90.0], [90.0, 180.0]])
+    prm = _prm(g=gm, gdd=gdd, kappa=21.0, eta_s=570.0, nodes=32, trap=trap)
+    X = [g.x[0][None, None, :], g.x[1][None, :, None], g.x[2][:, None, None]]
+    vol = 8.0 * g.L[0] * g.L[1] * g.L[2]
+    k = math.pi / g.L[2] * 2
+    a = 1.0 / math.sqrt(vol * (1.0 + 0.3 ** 2 / 2))
+    b = 0.3 * a
+    phi = (a + b * np.cos(k * X[2])) * np.ones(g.shape)
+    psi = np.zeros((2,) + g.shape, dtype=np.complex128)
+    psi[comp] = phi
+    ev = O.evaluate(g, prm, psi)
+    n = phi ** 2
+    V = 0.5 * sum(trap[ax] ** 2 * X[ax] ** 2 for ax in range(3))
+    gc, dc = gm[comp, comp], gdd[comp, comp]
+    muL = 2.5 * prm.kappa * prm.eta_s ** -2.5 * (2 * gc) ** 2.5 * n ** 1.5 * _q5_closed_form(dc / gc)
+    kin = vol * b * b * k * k / 4.0
+    alpha = kin + g.dV * np.sum((V + gc * n + muL) * n)
+    phi_dd = 2.0 * dc * (n - (a * a + b * b / 2.0))
+    mu = alpha + g.dV * np.sum(phi_dd * n)
+    assert abs(ev.mu[comp] - mu) < 1e-12 * abs(mu)
+    sh = O.preconditioner_shift(g, ev, psi)
+    assert abs(sh[comp] - alpha) < 1e-12 * abs(alpha)
+    assert abs(alpha - mu) > 1e-3 * abs(alpha)  # the dipolar part is not negligible here
+    r = I.random_fields(psi.shape, 32)
+    z = O.precondition(g, prm, ev, psi, r, "diagonal")
+    PV = np.maximum(abs(alpha) + V + gc * n + muL, 1e-2 * abs(alpha))
+    assert np.max(np.abs(z[comp] - r[comp] / PV)) < 1e-12 * np.max(np.abs(r[comp] / PV))
+
+
+def test_preconditioner_pv_floor_binds():
+    """Where alpha + V + sum_j g_ij n_j + mu_LHY falls below 1e-2 |alpha| (an
+    attractive contact coupling), P_V is the floor 1e-2 |alpha| (Sec. IV.B's
+    small positive shift); elsewhere it is the unfloored value."""
+    g = O.Grid((8, 8, 16), (3.0, 3.0, 4.0))
+    prm = _prm(g=((-500.0, 0.0), (0.0, 100.0)), trap=(0.0, 0.0, 0.0))
+    X = g.x[2][:, None, None]
+    vol = 8.0 * g.L[0] * g.L[1] * g.L[2]
+    k = math.pi / g.L[2] * 2
+    a = 1.0 / math.sqrt(vol * (1.0 + 0.9 ** 2 / 2))
+    phi = (a + 0.9 * a * np.cos(k * X)) * np.ones(g.shape)
+    psi = np.stack([phi, phi]).astype(np.complex128)
+    ev = O.evaluate(g, prm, psi)
+    n = phi ** 2
+    alpha = abs(O.preconditioner_shift(g, ev, psi)[0])
+    raw = alpha + (-500.0) * n
+    assert np.any(raw < 1e-2 * alpha) and np.any(raw > 1e-2 * alpha)
+    r = I.random_fields(psi.shape, 33)
+    z = O.precondition(g, prm, ev, psi, r, "diagonal")
+    assert np.max(np.abs(z[0] - r[0] / np.maximum(raw, 1e-2 * alpha))) < 1e-12 * np.max(np.abs(z[0]))
+
+
+def _beta_fields():
+    """Hand-built fields on a grid with dV = 1, nonzero only at three points,
+    so every inner product is an exact small rational:
+      d = r - r_prev: comp 1 at A = 2, comp 2 at B = 1 - i
+      z:              comp 1 at A = 3/2, comp 2 at B = 2 + 3i
+      p_prev:         comp 1 at A = 1/4, comp 1 at C = 7, comp 2 at B = -i
+      Re<d, z>      = 2 * 3/2 + Re((1 + i)(2 + 3i)) = 3 - 1 = 2
+      Re<d, p_prev> = 2 * 1/4 + Re((1 + i)(-i))     = 1/2 + 1 = 3/2
+    """
+    g = O.Grid((4, 4, 4), (2.0, 2.0, 2.0))
+    assert g.dV == 1.0
+    A, B, C = (0, 1, 2), (3, 0, 1), (2, 2, 2)
+    z0 = np.zeros((2,) + g.shape, dtype=np.complex128)
+    r_prev, r, z, p_prev = z0.copy(), z0.copy(), z0.copy(), z0.copy()
+    r_prev[0][A], r_prev[1][B] = 1.0, 2j
+    r[0][A], r[1][B] = 3.0, 1.0 + 1j
+    z[0][A], z[1][B] = 1.5, 2.0 + 3j
+    p_prev[0][A], p_prev[0][C], p_prev[1][B] = 0.25, 7.0, -1j
+    return g, r, z, r_prev, p_prev
+
+
+def test_beta_hs_and_pr_hand_computed():
+    """HS+ = 2 / (3/2) = 4/3; PR+ with Re<r_prev, z_prev> = 4/5 is 2 / (4/5) = 5/2
+    (Sec. IV.C; sums over both components).  Component 1 alone would give 3/(1/2)
+    = 6, a missing conjugate 8/(3/2), r in place of r - r_prev 19/2 / ..."""
+    g, r, z, r_prev, p_prev = _beta_fields()
+    b, ok = O.cg_beta(g, r, z, r_prev, p_prev, 0.8, "HS")
+    assert ok and abs(b - 4.0 / 3.0) < 1e-15
+    b, ok = O.cg_beta(g, r, z, r_prev, p_prev, 0.8, "PR")
+    assert ok and abs(b - 2.5) < 1e-15
+
+
+def test_beta_clamp_and_restarts():
+    """max(., 0): with z at A negated the numerator is -3 - 1 = -4, so both
+    rules give 0 without a restart; a zero or non-finite denominator is a
+    restart (beta = 0, ok False)."""
+    g, r, z, r_prev, p_prev = _beta_fields()
+    zn = z.copy()
+    zn[0][0, 1, 2] = -1.5
+    for rule in ("HS", "PR"):
+        b, ok = O.cg_beta(g, r, zn, r_prev, p_prev, 0.8, rule)
+        assert ok and b == 0.0
+    b, ok = O.cg_beta(g, r, z, r_prev, np.zeros_like(p_prev), 0.8, "HS")
+    assert not ok and b == 0.0
+    b, ok = O.cg_beta(g, r, z, r_prev, p_prev, 0.0, "PR")
+    assert not ok and b == 0.0
+    rn = r.copy()
+    rn[1][3, 0, 1] = np.nan
+    for rule in ("HS", "PR"):
+        b, ok = O.cg_beta(g, rn, z, r_prev, p_prev, 0.8, rule)
+        assert not ok and b == 0.0
+
+
 # ---------------------------------------------------------------- solver invariants
 @pytest.fixture(scope="module")
 def c1_small():
@@ -384,6 +529,20 @@ def test_pr_plus_reaches_the_same_minimum(c1_small):
     assert any(t["beta"] > 0 for t in tr)
     tau = opts.accept_rtol * abs(tr[0]["E"])
     assert all(t["E_new"] <= t["E"] + tau for t in tr)
+
+
+def test_periodic_restart(c1_small):
+    """beta = 0 exactly at n mod K_r = 0 (short periodic restarts, Sec. IV.C), and
+    the conjugate coefficient is used in between."""
+    g, prm, psi0 = c1_small
+    tr = []
+    O.ncg_solve(g, prm, psi0, O.SolveOpts(precond="kinetic", tol_res=1e-9, restart_period=4, max_iter=14), trace=tr)
+    acc = [t for t in tr if t["accepted"]]
+    assert len(acc) >= 13
+    for t in acc:
+        if t["n"] % 4 == 0:
+            assert t["beta"] == 0.0, t["n"]
+    assert sum(t["beta"] > 0 for t in acc if t["n"] % 4) >= 6
 
 
 def test_symmetric_mixture_keeps_components_equal():
