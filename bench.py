@@ -92,6 +92,17 @@ class Clocks:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def snapshot(self):
+        """Median SM clock of the samples taken so far (None if none)."""
+        sm = []
+        for ln in list(self.lines):
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[1]))
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm)} if sm else None
+
     def stop(self):
         if not self.proc:
             return None
@@ -128,9 +139,11 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# FP32 CUDA-core peak from unit counts and the maximum SM clock: 152 SMs x 128
-# FP32 lanes x 2 operations per fused multiply-add x 2070 MHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+def alu_peaks(sm_count, sm_mhz):
+    """CUDA-core peaks from the unit counts of this GPU (Blackwell SM: 128 FP32
+    lanes, 2 FP64 FMA lanes per clock on GB300) at a given SM clock, 2
+    operations per fused multiply-add, in TFLOP/s."""
+    return {"fp32": sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12, "fp64": sm_count * 2 * 2 * sm_mhz * 1e6 / 1e12}
 
 
 def kernel_flops(name, N, Q, L):
@@ -312,11 +325,16 @@ def run_ours(args):
                            "peak_kind": peak_kind + " (burst copy)"},
               "attempt": attempt,
               "kernels": [{"name": n, "ms": round(t, 5), "GBs": round(b / (t * 1e-3) / 1e9, 1)} for n, t, b in prof32]}
+    props = torch.cuda.get_device_properties(local)
+    clk_mid = clocks.snapshot()
+    sm_mhz = (clk_mid or {}).get("sm_mhz") or 2070.0
+    pk = alu_peaks(props.multi_processor_count, sm_mhz)
     if fl is not None:
         tf = fl / (dom[1] * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": round(tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                    "frac": round(tf / FP32_PEAK_TFLOPS, 4),
-                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+        roofline = {"bound": "alu", "achieved": round(tf, 2), "peak": round(pk["fp32"], 1), "unit": "TFLOP/s",
+                    "frac": round(tf / pk["fp32"], 4),
+                    "peak_kind": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz "
+                                 "(median SM clock sampled so far)",
                     "algorithmic_flops": fl, **common}
     else:
         roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
@@ -393,9 +411,15 @@ def run_ours(args):
     clk = clocks.stop()
     E.egpe_destroy(h)
 
-    cpu = None
+    # the CPU leg: the oracle timed on the host, and the oracle's evaluation of
+    # the mixed-precision results (rank 0 of a one-GPU run only)
+    cpu = macc = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w)
+        try:
+            macc = mixed_accuracy(E, w0, pc, args.fp32_switch)
+        except Exception as ex:  # reported, not fatal for the iteration numbers
+            macc = {"error": str(ex)[:300]}
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -408,7 +432,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2: ~25 complex64 fields of 16.8 MB resident per instance",
                            "step": "one NCG attempt (precondition + line coefficients + trial E/grad + controller)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launch32,
-                "clocks": clk, "fp64": fp64, "time_to_ground_state": tts, "ncg_vs_ite": ite,
+                "clocks": clk, "fp64": fp64, "time_to_ground_state": tts, "mixed_accuracy": macc,
+                "ncg_vs_ite": ite,
                 "scan": scan, "continuation": cont,
                 "precond_study": pcs, "param_grad": pgrad, "autotune": tuning}
         print(json.dumps(line))
@@ -417,23 +442,30 @@ def run_ours(args):
 
 
 def time_to_ground_state(E, h, grid, prm, psi64, pc, fp32_switch):
-    """Wall time of egpe_ncg_solve from the seeded start until |E - E_ref| <=
-    1e-8 |E_ref|, mixed (FP32 phase then FP64 polish) against FP64 only.
-    E_ref: FP64 solve to ||r|| <= 1e-10.  The residual target r* is the
-    residual of the reference run at its first point within the accuracy.
-    Both timed solves run on handles that have solved once already (the FP64
-    one ran the reference, the mixed one an untimed solve from the same start),
-    so neither pays graph capture or first-launch set-up; the mixed handle's
-    first solve is reported as seconds_cold."""
+    """Wall time of egpe_ncg_solve from the seeded start, FP64 fields against
+    FP32 fields, to two targets; every returned state is re-evaluated by the
+    GPU FP64 engine (egpe_energy_grad on an FP64 handle), and its relative
+    energy error is taken against E_ref, the FP64 energy of a solve to
+    ||r|| <= 1e-11:
+      * "energy_1e-8": both stop at the residual r* at which the FP64 run first
+        came within 1e-8 of E_ref (FP64 fields vs FP32 fields alone);
+      * "residual_1e-8": both stop at ||r|| <= 1e-8, FP64 alone against mixed
+        precision (FP32 fields until ||r|| < fp32_switch, then the FP64 polish).
+    Timed solves run on handles that have solved once already, so none pays
+    graph capture or first-launch set-up; the mixed handle's first solve is
+    reported as seconds_cold."""
+    import torch
     o = E.egpe_default_solve_opts()
     o.precond = pc
-    o.tol_res = 1e-10
+    o.tol_res = 1e-11
     o.max_iter = 5000
+    o.max_iter_fp32 = 5000
     ref = psi64.clone()
     hd = E.egpe_create([grid], [prm], E.EGPE_FP64)
+    h32 = E.egpe_create([grid], [prm], E.EGPE_FP32)
     try:
         st, reps, tr = E.egpe_ncg_solve(hd, [ref], o, 1, trace_cap=8000)
-        Eref = reps[0]["E"]
+        Eref = E.egpe_energy_grad(hd, 0, ref)[0]
         rstar = None
         acc = [t for t in tr if t["flags"] & 1]
         for k, t in enumerate(acc):
@@ -442,24 +474,87 @@ def time_to_ground_state(E, h, grid, prm, psi64, pc, fp32_switch):
                 break
         if rstar is None:
             raise RuntimeError("reference never reached the accuracy")
-        o.tol_res = rstar
-        x = psi64.clone()
-        st, r64, _ = E.egpe_ncg_solve(hd, [x], o, 1)
-        t64 = r64[0]
-        o.tol_fp32_switch = fp32_switch
-        x = psi64.clone()
-        st, rc, _ = E.egpe_ncg_solve(h, [x], o, 1)
-        x = psi64.clone()
-        st, rm, _ = E.egpe_ncg_solve(h, [x], o, 1)
-        tm = rm[0]
-        return {"E_ref": Eref, "ref_iters": reps[0]["iters"], "ref_status": reps[0]["status"], "res_target": rstar,
-                "fp64": {"seconds": t64["seconds"], "iters": t64["iters"], "rel_err": abs(t64["E"] - Eref) / abs(Eref)},
-                "mixed": {"seconds": tm["seconds"], "seconds_cold": rc[0]["seconds"], "iters": tm["iters"],
-                          "iters_fp32": tm["iters_fp32"],
-                          "rel_err": abs(tm["E"] - Eref) / abs(Eref), "fp32_switch": fp32_switch},
-                "speedup": t64["seconds"] / tm["seconds"]}
+
+        def fp64_error(x):
+            e64 = E.egpe_energy_grad(hd, 0, x.to(torch.complex128))[0]
+            return abs(e64 - Eref) / abs(Eref)
+
+        def run(handle, tol, switch=None, dtype=torch.complex128):
+            o.tol_res = tol
+            if switch is not None:
+                o.tol_fp32_switch = switch
+            x = psi64.clone().to(dtype)
+            st, r, _ = E.egpe_ncg_solve(handle, [x], o, 1)
+            r = r[0]
+            return {"seconds": r["seconds"], "iters": r["iters"], "iters_fp32": r["iters_fp32"], "status": r["status"],
+                    "res": r["res"], "rel_err_fp64_eval": fp64_error(x)}
+
+        run(hd, rstar)  # warm-up of the FP64 handle at this tolerance (graphs by max_iter)
+        run(h32, rstar, dtype=torch.complex64)  # warm-up: graph capture, first launches
+        e_fp64 = run(hd, rstar)
+        e_fp32 = run(h32, rstar, dtype=torch.complex64)
+        cold = run(h, 1e-8, fp32_switch)  # the mixed handle's first solve
+        r_fp64 = run(hd, 1e-8)
+        r_mixed = run(h, 1e-8, fp32_switch)
+        r_mixed["seconds_cold"] = cold["seconds"]
+        r_mixed["fp32_switch"] = fp32_switch
+        return {"E_ref": Eref, "ref_iters": reps[0]["iters"], "ref_status": reps[0]["status"],
+                "energy_1e-8": {"res_target": rstar, "fp64": e_fp64, "fp32_fields": e_fp32,
+                                "speedup": e_fp64["seconds"] / e_fp32["seconds"]},
+                "residual_1e-8": {"fp64": r_fp64, "mixed": r_mixed,
+                                  "speedup": r_fp64["seconds"] / r_mixed["seconds"]}}
     finally:
         E.egpe_destroy(hd)
+        E.egpe_destroy(h32)
+
+
+def mixed_accuracy(E, w, pc, fp32_switch=1e-4, tol_polish=1e-10):
+    """Mixed-precision accuracy against the FP64 oracle: the state after the
+    FP32 phase (FP32 fields to ||r|| < fp32_switch), the state after the FP64
+    polish (||r|| < tol_polish) and an FP64 reference (||r|| <= 1e-11) are each
+    evaluated by the oracle (the CPU-baseline leg may call it); reported are
+    |E - E_ref|/|E_ref| and |mu_i - mu_ref,i| with E_ref, mu_ref the oracle's
+    evaluation of the reference, and the GPU's own reported values against the
+    oracle's evaluation of the same state."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_2510_24543_gb300 import inputs as I
+
+    g = O.Grid(w.n, w.L)
+    op = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
+    grid, prm = E.make_grid(w.n, w.L), E.params_from_workload(w)
+    psi0 = torch.from_numpy(I.gaussian_start(w)).to("cuda")
+    states = {}
+    for name, prec, tol in (("reference_fp64", E.EGPE_FP64, 1e-11), ("after_fp32_phase", E.EGPE_FP32, fp32_switch),
+                            ("after_fp64_polish", E.EGPE_MIXED, tol_polish)):
+        h = E.egpe_create([grid], [prm], prec)
+        try:
+            o = E.egpe_default_solve_opts()
+            o.precond = pc
+            o.tol_res = tol
+            o.tol_fp32_switch = fp32_switch
+            o.max_iter = 5000
+            o.max_iter_fp32 = 5000
+            x = psi0.clone() if prec != E.EGPE_FP32 else psi0.to(torch.complex64)
+            st, reps, _ = E.egpe_ncg_solve(h, [x], o, 1)
+            states[name] = (reps[0], x.to(torch.complex128).cpu().numpy())
+        finally:
+            E.egpe_destroy(h)
+    evs = {k: O.evaluate(g, op, v[1]) for k, v in states.items()}
+    ref = evs["reference_fp64"]
+    out = {"workload": w.name, "E_ref_oracle": ref.E, "mu_ref_oracle": list(ref.mu)}
+    for k in ("after_fp32_phase", "after_fp64_polish"):
+        rep, psi = states[k]
+        ev = evs[k]
+        r = np.stack([ev.Hpsi[i] - ev.mu[i] * psi[i] for i in range(2)])
+        out[k] = {"iters": rep["iters"], "iters_fp32": rep["iters_fp32"], "status": rep["status"],
+                  "rel_err_E": abs(ev.E - ref.E) / abs(ref.E),
+                  "abs_err_mu": [abs(ev.mu[i] - ref.mu[i]) for i in range(2)],
+                  "res_oracle": float(np.sqrt(sum(O.inner(g, r[i], r[i]).real for i in range(2)))),
+                  "reported_vs_oracle_rel_E": abs(rep["E"] - ev.E) / abs(ev.E)}
+    return out
 
 
 def ncg_vs_ite(E, tune=True):
@@ -729,17 +824,36 @@ def continuation_benchmark(E, tol_res=1e-6, tune=True):
     return out
 
 
+def host_cpu():
+    """Core count and CPU model of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
 def cpu_baseline(w):
     """The FP64 oracle as it stands on this host: one NCG iteration (precondition,
-    line coefficients, trial evaluation) of the same 128^3 workload."""
+    line coefficients, trial evaluation) of the same 128^3 workload, its
+    transforms on every host core (scipy.fft workers), its pointwise NumPy code
+    on one."""
     import numpy as np  # noqa: F401
 
     import oracle as O
     from paper_2510_24543_gb300 import inputs as I
 
+    cores, model = host_cpu()
+    O.egpe.set_fft_workers(cores)
     g = O.Grid(w.n, w.L)
     prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
     psi = I.gaussian_start(w)
+    O.evaluate(g, prm, psi)  # warm-up: imports, transform plans, page-in
     t0 = time.perf_counter()
     O.evaluate(g, prm, psi)
     t_eval = time.perf_counter() - t0
@@ -748,10 +862,11 @@ def cpu_baseline(w):
                                                    max_iter=1, tol_res=0.0))
     t_solve = time.perf_counter() - t0
     t_it = max(t_solve - t_eval, 1e-9)
-    return {"value": round(1.0 / t_it, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+    O.egpe.set_fft_workers(None)
+    return {"value": round(1.0 / t_it, 5), "unit": UNIT, "cores": cores, "cpu_model": model, "kind": "oracle",
             "sample": f"one oracle NCG iteration on the full {w.n[0]}x{w.n[1]}x{w.n[2]} workload "
                       f"({t_it:.1f} s; its initial evaluation, {t_eval:.1f} s, timed separately and excluded); "
-                      "NumPy FFT and pointwise code, single thread"}
+                      f"transforms on {cores} threads (scipy.fft), pointwise NumPy code on one"}
 
 
 # ---------------------------------------------------------------------------
@@ -764,10 +879,13 @@ def run_reference(args):
     from paper_2510_24543_gb300 import inputs as I
 
     w = I.PRESETS[args.workload]
+    cores, model = host_cpu()
+    O.egpe.set_fft_workers(cores)
     g = O.Grid(w.n, w.L)
     prm = O.Params(w.g, w.gdd, w.kappa, w.eta_s, w.lhy_nodes, w.trap)
     psi = I.gaussian_start(w)
     budget = 150.0
+    O.evaluate(g, prm, psi)  # warm-up: imports, transform plans, page-in
     t0 = time.perf_counter()
     ev = O.evaluate(g, prm, psi)
     t_eval = time.perf_counter() - t0
@@ -784,9 +902,11 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Gaussian + 1% noise start)", "impl": "reference",
             "config": {"workload": w.name, "grid": list(w.n), "precond": args.precond},
-            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "cpu_model": model,
+                             "kind": "oracle",
                              "sample": f"first {done} oracle NCG iterations on the full workload (bounded to "
-                                       f"~{int(budget)} s), initial evaluation excluded"},
+                                       f"~{int(budget)} s), initial evaluation excluded; transforms on {cores} "
+                                       "threads (scipy.fft), pointwise NumPy code on one"},
             "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -822,11 +942,19 @@ def config_table(args):
             E.egpe_destroy(h)
         eg = prof[-5:]  # the trial energy/gradient pass: x fwd, y, z fused, y, x inv
         eg_gbs = sum(b for _, _, b in eg) / (sum(t for _, t, _ in eg) * 1e-3) / 1e9
+        en, rs = tts["energy_1e-8"], tts["residual_1e-8"]
+        gpu_cols = {"grid": list(w.n),
+                    "gpu_fp64_tts_energy_s": round(en["fp64"]["seconds"], 4),
+                    "gpu_fp32_tts_energy_s": round(en["fp32_fields"]["seconds"], 4),
+                    "fp32_energy_err_fp64_eval": en["fp32_fields"]["rel_err_fp64_eval"],
+                    "gpu_fp64_tts_res_s": round(rs["fp64"]["seconds"], 4),
+                    "gpu_mixed_tts_res_s": round(rs["mixed"]["seconds"], 4),
+                    "gpu_mixed_iters": [rs["mixed"]["iters_fp32"], rs["mixed"]["iters"]],
+                    "gpu_fp64_iters": rs["fp64"]["iters"], "fp32_eg_pass_frac_hbm": round(eg_gbs / hbm, 3)}
+        if key in ("c3", "c3p") and not args.no_cpu:
+            gpu_cols["mixed_accuracy"] = mixed_accuracy(E, w, pc, args.fp32_switch)
         if args.no_cpu:  # GPU columns only
-            rows[key] = {"grid": list(w.n), "gpu_fp64_tts_s": round(tts["fp64"]["seconds"], 4),
-                         "gpu_mixed_tts_s": round(tts["mixed"]["seconds"], 4),
-                         "gpu_mixed_tts_cold_s": round(tts["mixed"]["seconds_cold"], 4),
-                         "gpu_fp64_iters": tts["fp64"]["iters"], "fp32_eg_pass_frac_hbm": round(eg_gbs / hbm, 3)}
+            rows[key] = gpu_cols
             print(json.dumps({key: rows[key]}), flush=True)
             continue
         g = O.Grid(w.n, w.L)
@@ -837,20 +965,17 @@ def config_table(args):
         t0 = time.perf_counter()
         O.ncg_solve(g, op, psi0, O.SolveOpts(precond=w.precond, tol_res=0.0, max_iter=1))
         s_iter = max(time.perf_counter() - t0 - t_eval, 1e-9)
-        row = {"grid": list(w.n), "oracle_s_per_iter": round(s_iter, 3),
-               "gpu_fp64_tts_s": round(tts["fp64"]["seconds"], 4), "gpu_mixed_tts_s": round(tts["mixed"]["seconds"], 4),
-               "gpu_fp64_iters": tts["fp64"]["iters"], "fp32_eg_pass_GBs": round(eg_gbs, 1),
-               "fp32_eg_pass_frac_hbm": round(eg_gbs / hbm, 3)}
+        row = {"oracle_s_per_iter": round(s_iter, 3), "fp32_eg_pass_GBs": round(eg_gbs, 1), **gpu_cols}
         if key in ("c1", "c2"):
             t0 = time.perf_counter()
             O.ite_solve(g, op, psi0, dtau=1e-3, tol_dE=0.0, max_steps=2)
             row["oracle_s_per_ite_step"] = round((time.perf_counter() - t0 - 2 * t_eval) / 2, 3)
             t0 = time.perf_counter()
-            _, rep = O.ncg_solve(g, op, psi0, O.SolveOpts(precond=w.precond, tol_res=tts["res_target"]))
+            _, rep = O.ncg_solve(g, op, psi0, O.SolveOpts(precond=w.precond, tol_res=en["res_target"]))
             row["oracle_tts_s"] = round(time.perf_counter() - t0, 2)
             row["oracle_tts_iters"] = rep["iters"]
         else:
-            row["oracle_tts_s_extrapolated"] = round(s_iter * tts["fp64"]["iters"] + t_eval, 1)
+            row["oracle_tts_s_extrapolated"] = round(s_iter * en["fp64"]["iters"] + t_eval, 1)
         rows[key] = row
         print(json.dumps({key: row}), flush=True)
     if args.no_cpu:

@@ -205,10 +205,15 @@ egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n
  * EGPE_ERR_INVALID_ARG with the reason in egpe_last_error().
  * Workspace: one fixed 4 MiB device array inside the library, held on every
  * GPU that loads the library until the process exits.  The first call on a
- * device looks up that array's device address; make that first call before
- * any stream capture begins.  Every call shares the array and it keeps the
- * last call's contents (what must start at zero is cleared by each call):
- * calls whose work overlaps on the GPU race on it and must be serialised. */
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before any stream capture begins.  A device
+ * reset (cudaDeviceReset) invalidates the cached address for the rest of the
+ * process.  Every call shares the array and it keeps the last call's contents
+ * (what must start at zero is cleared by each call): calls whose work overlaps
+ * on the GPU race on it and must be serialised.  The call is synchronous: it
+ * returns after E and mu are on the host.  The library cannot check the size
+ * or element type of psi and grad: a buffer smaller than 2*nx*ny*nz complex128
+ * values is read or written out of bounds. */
 egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egpe_params* params, const void* psi,
                                      double* E, double mu[2], void* grad, void* cuda_stream);
 
@@ -294,6 +299,16 @@ egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi,
  * build, device and grid.  Entries whose key the engine never launches are
  * ignored; out-of-range choices fall back to the untuned shape. */
 egpe_status egpe_set_tuning(egpe_handle* h, int inst, int engine, const egpe_tuning* t, int count);
+
+/* Poll budget of the device-side waits of every engine of the handle (the
+ * TMA tile loads of the column passes; default 2^20 polls, roughly a second).
+ * No counterpart in the paper: a guard of this implementation.  A wait that
+ * runs out of its budget lets the copies already issued land, marks the run
+ * and returns; the call that launched it then reports EGPE_ERR_TIMEOUT (a
+ * solve, in its report and return value), and the handle stays usable.  0
+ * gives up before the first poll, which tests use to reach that path.
+ * Captured graphs are rebuilt.  Errors: INVALID_ARG (NULL handle, polls < 0). */
+egpe_status egpe_set_wait_limit(egpe_handle* h, long long polls);
 
 /* Ground state by preconditioned NCG (Algorithm 1).  psi_inout[i] is the start
  * and receives the result for instance i (device pointers unless
@@ -383,7 +398,7 @@ const char* egpe_status_string(egpe_status s);
 /* Message of the last CUDA error seen by this thread's calls ("" if none). */
 const char* egpe_last_error(void);
 
-/* ABI version (major * 100 + minor). */
+/* ABI version (major * 100 + minor): 101. */
 int egpe_version(void);
 
 #ifdef __cplusplus

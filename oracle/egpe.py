@@ -84,11 +84,29 @@ def inner(grid: Grid, a: np.ndarray, b: np.ndarray) -> complex:
     return grid.dV * np.sum(np.conj(a) * b)
 
 
+# Transform backend: numpy.fft (pocketfft, one thread) unless set_fft_workers
+# chose scipy.fft (the same pocketfft algorithm) with several threads, which
+# only the host-baseline timing does.  The arithmetic is the same either way.
+_FFT_WORKERS = None
+
+
+def set_fft_workers(n: Optional[int]) -> None:
+    """Run the oracle's transforms on n host threads (None: numpy.fft, one thread)."""
+    global _FFT_WORKERS
+    _FFT_WORKERS = int(n) if n else None
+
+
 def dft(f):
+    if _FFT_WORKERS:
+        import scipy.fft
+        return scipy.fft.fftn(f, workers=_FFT_WORKERS)
     return np.fft.fftn(f)
 
 
 def idft(F):
+    if _FFT_WORKERS:
+        import scipy.fft
+        return scipy.fft.ifftn(F, workers=_FFT_WORKERS)
     return np.fft.ifftn(F)
 
 

@@ -108,7 +108,7 @@ egpe_status sync_and_check(egpe_handle* h) {
 
 extern "C" {
 
-int egpe_version(void) { return 100; }
+int egpe_version(void) { return 101; }
 
 const char* egpe_last_error(void) { return egpe::g_last_error.c_str(); }
 
@@ -336,6 +336,13 @@ egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi,
     t.ms_default = res[k].ms_default;
   }
   if (count) *count = n;
+  return EGPE_OK;
+}
+
+egpe_status egpe_set_wait_limit(egpe_handle* h, long long polls) {
+  if (!h || polls < 0) return EGPE_ERR_INVALID_ARG;
+  for (auto* e : h->e64) e->set_wait_limit(polls);
+  for (auto* e : h->e32) e->set_wait_limit(polls);
   return EGPE_OK;
 }
 

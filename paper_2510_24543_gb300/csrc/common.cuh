@@ -85,7 +85,7 @@ struct DevState {
   // flow control
   int phase, status, n, attempts, restarts, armijo_total, armijo_k, kind;
   int cur, fallback, trace_len, restart_flag;
-  int rgiven, pgiven, pad0, pad1;
+  int rgiven, pgiven, timeout, pad1;  // timeout: a device wait ran out of its poll budget
   SolveOptsDev opt;
   // current point (slot cur)
   double E, mu[2], shift[2], nmuL[2], norm2[2];

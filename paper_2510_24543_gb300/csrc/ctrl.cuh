@@ -93,6 +93,15 @@ __device__ inline void set_retraction(DevState* st) {
   }
 }
 
+// A device wait that ran out of its budget ends the run with EGPE_ERR_TIMEOUT
+// whatever the controller step would decide from the (incomplete) sums.
+__device__ inline bool ctrl_timed_out(DevState* st) {
+  if (!st->timeout) return false;
+  st->status = 7;  // EGPE_ERR_TIMEOUT
+  st->phase = PH_DONE;
+  return true;
+}
+
 __device__ inline void load_point(DevState* st, int slot) {
   EnergyOut o;
   finalize_energy(st->eg[slot], st->egz[slot], st->dV, st->invN, o);
@@ -108,6 +117,7 @@ __device__ inline void load_point(DevState* st, int slot) {
 // After an energy/gradient evaluation.  mode 0: evaluation of the current
 // point (start of a solve, or a standalone call); mode 1: trial point.
 __device__ inline void ctrl_after_eg(DevState* st, int mode, TraceDev* trace) {
+  if (ctrl_timed_out(st)) return;
   if (mode == 0) {
     load_point(st, st->cur);
     st->phase = finite_(st->E) ? PH_NEW_ITER : PH_DONE;
@@ -177,6 +187,7 @@ __device__ inline void ctrl_after_eg(DevState* st, int mode, TraceDev* trace) {
 // End of one imaginary-time step: the energy of the renormalised state, the
 // |E^{k+1} - E^k| < tol_dE stopping rule of the ITE comparison (Sec. VI.A).
 __device__ inline void ctrl_after_ite(DevState* st) {
+  if (ctrl_timed_out(st)) return;
   const double Eold = st->E;
   load_point(st, st->cur);
   st->dE_last = st->E - Eold;
@@ -196,6 +207,7 @@ __device__ inline void ctrl_after_ite(DevState* st) {
 // After the preconditioned residual and its sums: convergence test, beta,
 // projection coefficients, restart rules.
 __device__ inline void ctrl_after_pc(DevState* st) {
+  if (ctrl_timed_out(st)) return;
   const double* pc = st->pc;
   const double dV = st->dV;
   const SolveOptsDev& op = st->opt;
@@ -265,6 +277,7 @@ __device__ inline void ctrl_after_pc(DevState* st) {
 
 // After the line-search sums: E', E'', alpha, theta, retraction coefficients.
 __device__ inline void ctrl_after_lc(DevState* st) {
+  if (ctrl_timed_out(st)) return;
   LineOut o;
   finalize_line(st->lc, st->lcz, st->mu, st->dV, st->invN, o);
   st->Ep = o.Ep;

@@ -115,6 +115,9 @@ template <class R> class Engine {
     tune_.clear();
     drop_graphs();
   }
+  // Poll budget of the device-side TMA waits (default kTmaWaitPolls; 0 gives
+  // up before the first poll, which tests use to reach the timeout path).
+  void set_wait_limit(long long polls);
   // Captured graphs hold launch shapes: drop them when the shapes change.
   void drop_graphs();
   // Records (instead of launching) the kernels of one solver attempt.
@@ -138,7 +141,7 @@ template <class R> class Engine {
   egpe_status enq_ite_step(int gate);
   egpe_status reset_state(const egpe_solve_opts* o, int fp32_phase, int max_iter, double tol_res,
                           double accept_rtol);
-  egpe_status read_state(DevState& hs);
+  egpe_status read_state(DevState& hs, bool report_timeout = true);
   template <class Op> egpe_status launch_x(KArgs<R> a);
   egpe_status launch_point(void (*kern)(KArgs<R>), void (*kern_b)(KBatch<R>), const char* name, double bytes,
                            const KArgs<R>& a, long long units);

@@ -18,14 +18,20 @@ template egpe_status egpe::batch_solve<double>(const std::vector<egpe::Engine<do
 // one file-scope device array of fixed size.
 //
 // The array lives for as long as the library is loaded, on every GPU that
-// loads it.  Its address is looked up once per device (cudaGetSymbolAddress)
-// on the first call made with that device current; make that first call
-// before any stream capture begins.  All calls share the array: two calls
-// whose work overlaps on the GPU (different streams, or different host
-// threads on one device) race on it and must be serialised by the caller.
+// loads it.  Host code cannot hand the array's name to a kernel (in host code
+// it names a host-side stand-in), so its device address is looked up with
+// cudaGetSymbolAddress once per device, on the first call made with that
+// device current, and cached (under a mutex) for later calls; make that first
+// call before any stream capture begins.  The cached address stays valid until
+// the device is reset (cudaDeviceReset), which invalidates this entry point for
+// the rest of the process.  All calls share the array: two calls whose work
+// overlaps on the GPU (different streams, or different host threads on one
+// device) race on it and must be serialised by the caller.  Each call is
+// synchronous: it returns after E and mu have reached the host.
 // ---------------------------------------------------------------------------
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 namespace {
 
@@ -50,6 +56,21 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 static unsigned char* g_scratch_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_scratch_mutex;
+
+// Device address of the scratch array on the current device (looked up once).
+cudaError_t noalloc_scratch(int dev, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (ce != cudaSuccess) return ce;
+    if (!ptr) return cudaErrorInvalidSymbol;
+    g_scratch_ptr[dev] = (unsigned char*)ptr;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
 
 template <class Op> cudaError_t noalloc_launch_x(egpe::KArgs<double> a, int rows, cudaStream_t s) {
   using namespace egpe;
@@ -124,6 +145,12 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
       return EGPE_ERR_INVALID_ARG;
     }
   }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (!std::isfinite(p.g[i][j]) || !std::isfinite(p.gdd[i][j])) {
+        set_error_msg("egpe_energy_grad_noalloc: couplings must be finite");
+        return EGPE_ERR_INVALID_ARG;
+      }
   if (p.g[0][1] != p.g[1][0] || p.gdd[0][1] != p.gdd[1][0] || p.lhy_nodes < 1 || p.lhy_nodes > 64 ||
       !(p.lhy_eta_scale > 0.0) || !std::isfinite(p.lhy_kappa)) {
     set_error_msg("egpe_energy_grad_noalloc: couplings must be symmetric, lhy_nodes in [1,64], eta_s > 0");
@@ -140,76 +167,21 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
     set_error_msg("egpe_energy_grad_noalloc: device ordinal out of range");
     return EGPE_ERR_INVALID_ARG;
   }
-  if (!g_scratch_ptr[dev]) {
-    void* ptr = nullptr;
-    ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (ce != cudaSuccess || !ptr) {
-      set_error("cudaGetSymbolAddress", ce);
-      return EGPE_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = (unsigned char*)ptr;
+  unsigned char* base = nullptr;
+  ce = noalloc_scratch(dev, &base);
+  if (ce != cudaSuccess) {
+    set_error("cudaGetSymbolAddress", ce);
+    return EGPE_ERR_CUDA;
   }
-  unsigned char* base = g_scratch_ptr[dev];
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const size_t N = (size_t)nx * ny * nz;
 
-  // constant tables (host long double), staged through fixed host arrays
+  // constant tables (host long double, shared with the handle path), staged
+  // through fixed host arrays
   double2 tw[3][kNoAllocMaxN];
-  const long double pi = 3.141592653589793238462643383279502884L;
-  for (int ax = 0; ax < 3; ++ax)
-    for (int m = 0; m < g.n[ax]; ++m) {
-      const long double ang = 2.0L * pi * (long double)m / (long double)g.n[ax];
-      tw[ax][m] = make_double2((double)cosl(ang), (double)(-sinl(ang)));
-    }
-  LhyNode<double> nodes[64], nneg[64];
-  int qm = 0, qn = 0;
-  {
-    const int Q = p.lhy_nodes;
-    const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
-    for (int q = 0; q < Q; ++q) {
-      // Gauss-Legendre node q on [0,1] by Newton iteration on P_Q
-      long double x = cosl(pi * (q + 0.75L) / (Q + 0.5L)), dp = 1.0L;
-      for (int it = 0; it < 100; ++it) {
-        long double p0 = 1.0L, p1 = x;
-        for (int k = 2; k <= Q; ++k) {
-          const long double p2 = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
-          p0 = p1;
-          p1 = p2;
-        }
-        dp = Q * (x * p1 - p0) / (x * x - 1.0L);
-        const long double dx = p1 / dp;
-        x -= dx;
-        if (fabsl(dx) < 1e-19L) break;
-      }
-      {
-        long double p0 = 1.0L, p1 = x;
-        for (int k = 2; k <= Q; ++k) {
-          const long double p2 = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
-          p0 = p1;
-          p1 = p2;
-        }
-        dp = Q * (x * p1 - p0) / (x * x - 1.0L);
-      }
-      const long double u = 0.5L * (1.0L + x), w = 1.0L / ((1.0L - x * x) * dp * dp);
-      const long double sdd = 3.0L * u * u - 1.0L;
-      const long double e12 = p.g[0][1] + p.gdd[0][1] * sdd;
-      const long double det = (p.g[0][0] + p.gdd[0][0] * sdd) * (p.g[1][1] + p.gdd[1][1] * sdd) - e12 * e12;
-      LhyNode<double> nd;
-      nd.w = (double)sdd;
-      nd.W = (double)(c5 * w);
-      nd.Ww = (double)(c5 * w * sdd);
-      nd.e12sq = (double)(e12 * e12);
-      nd.gq = (double)(det > 0.0L ? 2.0L * sqrtl(det) : 0.0L);
-      nd.Www = (double)(c5 * w * sdd * sdd);
-      nd.pad0 = nd.pad1 = 0.0;
-      if (det > 0.0L) {
-        nodes[qm++] = nd;
-      } else {
-        nneg[qn++] = nd;
-      }
-    }
-    for (int q = 0; q < qn; ++q) nodes[qm + q] = nneg[q];
-  }
+  for (int ax = 0; ax < 3; ++ax) twiddle_table<double>(g.n[ax], tw[ax]);
+  LhyNode<double> nodes[64];
+  const int qm = lhy_node_table<double>(p, nodes);
   double2* twd = (double2*)(base + kOffTw);
   for (int ax = 0; ax < 3; ++ax) {
     ce = cudaMemcpyAsync(twd + ax * kNoAllocMaxN, tw[ax], g.n[ax] * sizeof(double2), cudaMemcpyHostToDevice, s);
@@ -257,6 +229,7 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
   a.invN = 1.0 / (double)N;
   a.Q = p.lhy_nodes;
   a.Qm = qm;
+  a.nskip = lhy_skip_threshold(p);
   a.nodes = (const LhyNode<double>*)(base + kOffNodes);
   a.twx = twd;
   a.twy = twd + kNoAllocMaxN;
@@ -269,6 +242,7 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
   a.counter = (unsigned*)(base + kOffCnt);
   a.st = (DevState*)(base + kOffSt);
   a.trace = nullptr;
+  a.wait_polls = kTmaWaitPolls;  // (the passes here load tiles without TMA)
   a.gate = GATE_ALWAYS;
   a.flag = 0;
   a.ctrl = 0;

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "host_tables.h"
 #include "kernels.cuh"
 
 namespace egpe {
@@ -84,75 +85,14 @@ static inline bool supported_len(int n) {
   return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 48 || n == 80 || n == 96;
 }
 
-// Gauss-Legendre rule on [0,1] by Newton iteration on P_Q (long double).
-static void gauss_legendre01(int Q, std::vector<long double>& u, std::vector<long double>& w) {
-  u.resize(Q);
-  w.resize(Q);
-  const long double pi = 3.141592653589793238462643383279502884L;
-  for (int i = 0; i < Q; ++i) {
-    long double x = cosl(pi * (i + 0.75L) / (Q + 0.5L));
-    long double dp = 1.0L;
-    for (int it = 0; it < 100; ++it) {
-      long double p0 = 1.0L, p1 = x;
-      for (int k = 2; k <= Q; ++k) {
-        const long double p2 = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      if (Q == 1) {
-        p1 = x;
-        p0 = 1.0L;
-      }
-      dp = Q * (x * p1 - p0) / (x * x - 1.0L);
-      const long double dx = p1 / dp;
-      x -= dx;
-      if (fabsl(dx) < 1e-19L) break;
-    }
-    {
-      long double p0 = 1.0L, p1 = x;
-      for (int k = 2; k <= Q; ++k) {
-        const long double p2 = ((2.0L * k - 1.0L) * x * p1 - (k - 1.0L) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      if (Q == 1) {
-        p1 = x;
-        p0 = 1.0L;
-      }
-      dp = Q * (x * p1 - p0) / (x * x - 1.0L);
-    }
-    u[i] = 0.5L * (1.0L + x);
-    w[i] = 1.0L / ((1.0L - x * x) * dp * dp);  // (2/((1-x^2) P'^2)) / 2
-  }
-}
-
 // Couplings, trap and LHY node table of the instance (at create, and again
 // when the parameters change: egpe_set_params).  The node table keeps its
 // nodes with det eta > 0 first (Qm_ of them).
 template <class R> egpe_status Engine<R>::apply_params(const egpe_params& p) {
   prm_ = p;
   const int Q = p.lhy_nodes;
-  std::vector<long double> u, w;
-  gauss_legendre01(Q, u, w);
-  std::vector<LhyNode<R>> h;
-  std::vector<LhyNode<R>> hneg;
-  const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
-  for (int q = 0; q < Q; ++q) {
-    const long double s = 3.0L * u[q] * u[q] - 1.0L;
-    const long double e12 = p.g[0][1] + p.gdd[0][1] * s;
-    const long double det = (p.g[0][0] + p.gdd[0][0] * s) * (p.g[1][1] + p.gdd[1][1] * s) - e12 * e12;
-    LhyNode<R> nd;
-    nd.w = (R)s;
-    nd.W = (R)(c5 * w[q]);
-    nd.Ww = (R)(c5 * w[q] * s);
-    nd.e12sq = (R)(e12 * e12);
-    nd.gq = (R)(det > 0.0L ? 2.0L * sqrtl(det) : 0.0L);
-    nd.Www = (R)(c5 * w[q] * s * s);
-    nd.pad0 = nd.pad1 = (R)0;
-    (det > 0.0L ? h : hneg).push_back(nd);
-  }
-  Qm_ = (int)h.size();
-  h.insert(h.end(), hneg.begin(), hneg.end());
+  std::vector<LhyNode<R>> h(Q);
+  Qm_ = lhy_node_table<R>(p, h.data());
   // kernels still reading the old table finish first
   EGPE_CUDA(cudaStreamSynchronize(stream));
   if (nodes_ && nodes_q_ != Q) {
@@ -179,23 +119,7 @@ template <class R> egpe_status Engine<R>::apply_params(const egpe_params& p) {
   a.Q = Q;
   a.Qm = Qm_;
   a.nodes = nodes_;
-  // LHY skip threshold: with eb = max over u of |eta11| + |eta22| + |eta12| every branch
-  // potential obeys V <= 2 eb n (n = n1 + n2), so F <= 2 c5 (2 eb n)^{5/2} and
-  // mu_LHY <= 15 c5 eb (2 eb n)^{3/2}; below nskip these are under 1e-40 and 1e-30.
-  {
-    double eb = 0.0;
-    for (double w : {-1.0, 2.0})
-      eb = std::max(eb, std::fabs(p.g[0][0] + p.gdd[0][0] * w) + std::fabs(p.g[1][1] + p.gdd[1][1] * w) +
-                            std::fabs(p.g[0][1] + p.gdd[0][1] * w));
-    const double c5a = std::fabs((double)c5);
-    double ns = 1e30;
-    if (c5a > 0.0 && eb > 0.0) {
-      const double nf = std::pow(1e-40 / (2.0 * c5a), 0.4) / (2.0 * eb);
-      const double nm = std::pow(1e-30 / (15.0 * c5a * eb), 2.0 / 3.0) / (2.0 * eb);
-      ns = std::min(nf, nm);
-    }
-    a.nskip = (R)std::min(ns, 1e30);
-  }
+  a.nskip = (R)lhy_skip_threshold(p);
   return EGPE_OK;
 }
 
@@ -277,11 +201,7 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   for (int ax = 0; ax < 3; ++ax) {
     const int L = g.n[ax];
     std::vector<C> h(L);
-    const long double pi = 3.141592653589793238462643383279502884L;
-    for (int m = 0; m < L; ++m) {
-      const long double ang = 2.0L * pi * (long double)m / (long double)L;
-      h[m] = cmk<C>((R)cosl(ang), (R)(-sinl(ang)));
-    }
+    twiddle_table<R>(L, h.data());
     EGPE_CUDA(cudaMalloc(tws[ax], L * sizeof(C)));
     EGPE_CUDA(cudaMemcpy(*tws[ax], h.data(), L * sizeof(C), cudaMemcpyHostToDevice));
   }
@@ -318,9 +238,15 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   a.st = st_;
   a.trace = nullptr;
   a.kin_tab = kin_tab_;
+  a.wait_polls = kTmaWaitPolls;
   a.gate = GATE_ALWAYS;
   have_maps_ = make_col_map<C>(tmW_y_, a.W, nx, ny, nz, 3, 1) && make_col_map<C>(tmW_z_, a.W, nx, ny, nz, 3, 2);
   return reset_state(nullptr, 0, 0, 0.0, 0.0);
+}
+
+template <class R> void Engine<R>::set_wait_limit(long long polls) {
+  base_->wait_polls = polls;
+  drop_graphs();  // captured launches hold the old budget
 }
 
 template <class R> void Engine<R>::drop_graphs() {
@@ -890,10 +816,14 @@ egpe_status Engine<R>::reset_state(const egpe_solve_opts* o, int fp32_phase, int
   return EGPE_OK;
 }
 
-template <class R> egpe_status Engine<R>::read_state(DevState& hs) {
+template <class R> egpe_status Engine<R>::read_state(DevState& hs, bool report_timeout) {
   EGPE_CUDA(cudaMemcpyAsync(st_host_, st_, sizeof(DevState), cudaMemcpyDeviceToHost, stream));
   EGPE_CUDA(cudaStreamSynchronize(stream));
   hs = *st_host_;
+  if (report_timeout && hs.timeout) {
+    set_error_msg("a device-side wait ran out of its poll budget");
+    return EGPE_ERR_TIMEOUT;
+  }
   return EGPE_OK;
 }
 
@@ -1214,8 +1144,9 @@ egpe_status Engine<R>::solve_finish(SolveRun& run, egpe_trace_entry* trace_out, 
     EGPE_CUDA(cudaGetLastError());
   }
   DevState hs;
-  EGPE_TRY(read_state(hs));
+  EGPE_TRY(read_state(hs, false));
   run.status = (hs.phase == PH_DONE) ? hs.status : EGPE_ERR_NOT_CONVERGED;
+  if (hs.timeout) run.status = EGPE_ERR_TIMEOUT;
   run.n = hs.n;
   run.attempts = hs.attempts;
   run.restarts = hs.restarts;

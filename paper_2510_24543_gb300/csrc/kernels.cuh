@@ -64,6 +64,7 @@ template <class R> struct KArgs {
   int ctrl;                  // run the controller step in the last block
   int diag;                  // P_V part of the preconditioner
   int blend;                 // weighted P_V / P_Delta combination (mode 4)
+  long long wait_polls;      // poll budget of a TMA tile wait before the pass reports a timeout
 };
 
 template <class R> __device__ __forceinline__ bool gate_open(const KArgs<R>& a) {
@@ -367,7 +368,7 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     const int ahead = tile_of(it + NST - 1);
     // its buffer was last used by iteration it - 1, which ended with a barrier
     if (tid == 0 && ahead < tiles_n) issue(ahead, (it + NST - 1) % NST);
-    const bool ok = mbar_wait(&bar[b], (uint32_t)((it / NST) & 1), kTmaWaitPolls);
+    const bool ok = mbar_wait(&bar[b], (uint32_t)((it / NST) & 1), a.wait_polls);
     if (__syncthreads_or(!ok)) {
       timed_out = true;
       break;
@@ -387,11 +388,14 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     __syncthreads();  // buffer b may be refilled from the next iteration on
   }
   if (timed_out) {
-    // let every copy already issued land (each wait bounded) before exiting
+    // let every copy already issued land before exiting: these waits keep the
+    // full budget whatever a.wait_polls says, so no copy can still write into
+    // shared memory once the block has left
     for (int q = it; q < it + NST; ++q)
       if (tile_of(q) < tiles_n) mbar_wait(&bar[q % NST], (uint32_t)((q / NST) & 1), kTmaWaitPolls);
     if (tid == 0) {
-      a.st->status = 7;  // EGPE_ERR_TIMEOUT
+      a.st->timeout = 1;  // sticky: every later controller step ends the run
+      a.st->status = 7;   // EGPE_ERR_TIMEOUT
       a.st->phase = PH_DONE;
     }
   }

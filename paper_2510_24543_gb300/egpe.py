@@ -111,6 +111,7 @@ _SIGS = {
     "egpe_autotune": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p, ct.c_int, ct.c_int,
                                  ct.POINTER(egpe_tuning), ct.c_int, ct.POINTER(ct.c_int)]),
     "egpe_set_tuning": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(egpe_tuning), ct.c_int]),
+    "egpe_set_wait_limit": (ct.c_int, [ct.c_void_p, ct.c_longlong]),
     "egpe_default_solve_opts": (None, [ct.POINTER(egpe_solve_opts)]),
     "egpe_status_string": (ct.c_char_p, [ct.c_int]),
     "egpe_last_error": (ct.c_char_p, []),
@@ -215,9 +216,31 @@ def egpe_energy_grad(h: int, inst: int, psi, grad=None):
     return E.value, (mu[0], mu[1])
 
 
+def _check_field(name: str, t, grid: egpe_grid, dtype_name: str):
+    """Host-side check that a field tensor matches the grid it is used with:
+    a CUDA tensor of the given complex dtype, contiguous, with 2*nx*ny*nz
+    elements.  The C entry points receive bare pointers and cannot check this."""
+    if not hasattr(t, "data_ptr") or not hasattr(t, "is_cuda"):
+        raise ValueError(f"{name} must be a torch CUDA tensor, not {type(t).__name__}")
+    want = 2 * grid.n[0] * grid.n[1] * grid.n[2]
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise ValueError(f"{name} must be {dtype_name}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != want:
+        raise ValueError(f"{name} has {t.numel()} elements; the grid needs 2*nx*ny*nz = {want}")
+
+
 def egpe_energy_grad_noalloc(grid: egpe_grid, params: egpe_params, psi, grad=None, stream: int = 0):
     """Energy and gradient with the library's fixed workspace (no device
-    allocation; at most 32 points per axis).  Returns (E, (mu1, mu2))."""
+    allocation; at most 32 points per axis).  psi (and grad, if given) must be
+    contiguous complex128 CUDA tensors of 2*nx*ny*nz elements: checked here,
+    before the call, since the library only sees pointers.  Returns (E, (mu1, mu2))."""
+    _check_field("psi", psi, grid, "complex128")
+    if grad is not None:
+        _check_field("grad", grad, grid, "complex128")
     E = ct.c_double()
     mu = (ct.c_double * 2)()
     _check("egpe_energy_grad_noalloc",
@@ -359,6 +382,11 @@ def egpe_set_tuning(h: int, inst: int, engine: int, entries) -> None:
         arr[k].key = e["key"].encode()[:159]
         arr[k].choice = int(e["choice"])
     _check("egpe_set_tuning", load().egpe_set_tuning(ct.c_void_p(h), inst, engine, arr, len(entries)))
+
+
+def egpe_set_wait_limit(h: int, polls: int) -> None:
+    """Poll budget of the device-side TMA waits of every engine of the handle."""
+    _check("egpe_set_wait_limit", load().egpe_set_wait_limit(ct.c_void_p(h), int(polls)))
 
 
 def _report_dict(r) -> dict:

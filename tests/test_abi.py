@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert E.egpe_version() == 100
+    assert E.egpe_version() == 101
     for s in range(9):
         assert E.egpe_status_string(s)
     assert E.egpe_status_string(99) == "unknown status"
@@ -105,3 +105,20 @@ def test_source_digest_ignores_the_machine_include_path(monkeypatch):
     assert B._digest() == d0
     monkeypatch.setattr(B, "FLAGS", B.FLAGS + ["-DEXTRA"])
     assert B._digest() != d0
+
+
+def test_wait_limit_rejects_bad_arguments(lib):
+    assert lib.egpe_set_wait_limit(None, 5) == 1
+
+
+def test_noalloc_binding_checks_fields_on_the_host(lib):
+    """egpe_energy_grad_noalloc only receives pointers, so the binding checks
+    the tensors against the grid before the call: device, dtype, contiguity
+    and element count (a short buffer would be read out of bounds)."""
+    torch = pytest.importorskip("torch")
+    g = E.make_grid((16, 16, 16), (3.0, 3.0, 3.0))
+    p = E.make_params(((1, 0), (0, 1)), ((0, 0), (0, 0)), 0.0, 1.0, 4, (1, 1, 1))
+    with pytest.raises(ValueError, match="CUDA"):
+        E.egpe_energy_grad_noalloc(g, p, torch.zeros((2, 16, 16, 16), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="torch CUDA tensor"):
+        E.egpe_energy_grad_noalloc(g, p, 12345)

@@ -27,8 +27,9 @@ def E():
     return egpe
 
 
-def _scan_subset(sizes_per_grid=2, nodes=16):
-    """A few instances of each grid size of the parameter scan."""
+def _scan_subset(sizes_per_grid=2, nodes=32):
+    """A few instances of each grid size of the parameter scan (the scan's
+    own 32-node LHY rule)."""
     scan = I.scan_workloads()
     out = []
     for g in range(4):

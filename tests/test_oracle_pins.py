@@ -545,6 +545,22 @@ def test_periodic_restart(c1_small):
     assert sum(t["beta"] > 0 for t in acc if t["n"] % 4) >= 6
 
 
+def test_solver_failure_statuses(c1_small):
+    """A non-finite start ends the solve as "nonfinite"; an acceptance rule no
+    trial can meet ends it as "stagnated" after the first trial and armijo_max
+    halvings (Sec. V, last paragraph)."""
+    g, prm, psi0 = c1_small
+    bad = psi0.copy()
+    bad[1, 2, 3, 4] = np.inf
+    with np.errstate(invalid="ignore"):
+        _, rep = O.ncg_solve(g, prm, bad, O.SolveOpts(precond="kinetic", max_iter=3))
+    assert rep["status"] == "nonfinite" and rep["iters"] == 0
+    tr = []
+    _, rep = O.ncg_solve(g, prm, psi0, O.SolveOpts(precond="kinetic", accept_rtol=-0.9, armijo_max=2), trace=tr)
+    assert rep["status"] == "stagnated" and rep["armijo_steps"] == 3 and rep["iters"] == 0
+    assert len(tr) == 1 and tr[0]["armijo"] == 3 and not tr[0]["accepted"]
+
+
 def test_symmetric_mixture_keeps_components_equal():
     """Symmetric couplings and psi1 = psi2 at the start give psi1 = psi2 throughout;
     swapping the components leaves E unchanged."""

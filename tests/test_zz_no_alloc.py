@@ -10,7 +10,10 @@ passes on its own in a fresh process.
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2510_24543_gb300 import inputs as I
+
+from ._common import oracle_case
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +63,14 @@ def test_noalloc_matches_handle_path_on_two_calls(E, n, complex_state):
     # without a gradient output the energy is the same
     e2, _ = E.egpe_energy_grad_noalloc(grid, prm, psi, None)
     assert abs(e2 - e_ref) < 1e-12 * abs(e_ref)
+    # and both agree with the FP64 oracle (Eq. 1 and the coupled eGPE)
+    og, oprm = oracle_case(w)
+    ev = O.evaluate(og, oprm, psi_np)
+    assert abs(e - ev.E) < 1e-12 * abs(ev.E)
+    for i in range(2):
+        assert abs(mu[i] - ev.mu[i]) < 1e-11 * abs(ev.mu[i])
+    hmax = float(np.max(np.abs(ev.Hpsi)))
+    assert float(np.max(np.abs(g.cpu().numpy() - ev.Hpsi))) < 1e-11 * hmax
 
 
 def test_noalloc_rejects_grids_beyond_its_workspace(E):
@@ -71,3 +82,19 @@ def test_noalloc_rejects_grids_beyond_its_workspace(E):
         E.egpe_energy_grad_noalloc(grid, prm, psi)
     assert ei.value.status == 1
     assert "32" in str(ei.value)
+
+
+def test_noalloc_binding_rejects_mismatched_fields_before_any_launch(E):
+    """The C entry point only sees pointers; the binding checks each tensor
+    against the grid and raises before calling it."""
+    w = I.PRESETS["c1"]
+    grid = E.make_grid(w.n, w.L)
+    prm = E.params_from_workload(w)
+    with pytest.raises(ValueError, match="elements"):
+        E.egpe_energy_grad_noalloc(grid, prm, torch.zeros((2, 16, 32, 32), dtype=torch.complex128, device="cuda"))
+    with pytest.raises(ValueError, match="complex128"):
+        E.egpe_energy_grad_noalloc(grid, prm, torch.zeros((2, 32, 32, 32), dtype=torch.complex64, device="cuda"))
+    psi = torch.zeros((2, 32, 32, 32), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ValueError, match="grad"):
+        E.egpe_energy_grad_noalloc(grid, prm, psi, torch.zeros((2, 32, 32, 16), dtype=torch.complex128,
+                                                                  device="cuda"))
