@@ -38,7 +38,13 @@
  *          Arguments are validated before any launch (EGPE_ERR_INVALID_ARG).
  *          CUDA failures map to EGPE_ERR_CUDA (see egpe_last_error()).
  * Streams: all work is enqueued on the stream given to egpe_create; calls that
- *          return host scalars synchronise that stream before returning.
+ *          return host scalars synchronise that stream before returning.  A
+ *          handle created with a NULL stream works on a stream of its own and
+ *          orders each call after the work already on the legacy default
+ *          stream, and the legacy default stream after the call's work, so
+ *          buffers written or read there by the caller need no extra
+ *          synchronisation.  With a caller's stream, ordering against other
+ *          streams is the caller's.
  */
 #ifndef EGPE_H
 #define EGPE_H
@@ -183,8 +189,9 @@ enum {
 typedef struct egpe_handle egpe_handle;
 
 /* Create a handle for n_inst instances (grids[i], params[i]) of the given
- * precision on the current CUDA device.  cuda_stream is a cudaStream_t (NULL:
- * the legacy default stream).  Allocates every workspace up front (about 26
+ * precision on the current CUDA device.  cuda_stream is a cudaStream_t, or
+ * NULL for a stream owned by the handle and ordered against the legacy default
+ * stream at every call (see Streams above).  Allocates every workspace up front (about 26
  * complex fields per instance and precision).  Errors: INVALID_ARG (bad sizes,
  * non-symmetric couplings, L <= 0, Q out of range), OOM, CUDA. */
 egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n_inst,
@@ -300,6 +307,22 @@ egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi,
  * ignored; out-of-range choices fall back to the untuned shape. */
 egpe_status egpe_set_tuning(egpe_handle* h, int inst, int engine, const egpe_tuning* t, int count);
 
+/* Diagnostic of the LHY interpolation tables that the energy/gradient and
+ * line-search kernels use (no counterpart in the paper, which sums the
+ * Gauss-Legendre rule at every point).  The LHY density is homogeneous of
+ * degree 5/2 in (n1, n2), so mu_LHY,i = n^{3/2} m_i(a) and d^2F/dn_i dn_j =
+ * n^{1/2} h_ij(a) with n = n1 + n2, a = sqrt(min(n1,n2)/n); the quadrature
+ * sums m_i, h_ij over all but a few nodes are tabulated per parameter set as
+ * piecewise polynomials in a, and the remaining nodes are evaluated exactly.
+ * This host function builds the tables for params (as the engines do) and
+ * evaluates them, plus the exact nodes, in FP64 at the count host points
+ * (n1[k], n2[k]) >= 0: mu (2 per point: mu_LHY,1, mu_LHY,2) and hess (3 per
+ * point: d^2F/dn1^2, d^2F/dn1dn2, d^2F/dn2^2); info (may be NULL) receives
+ * the intervals per half and the number of exactly evaluated nodes.  All
+ * arrays are host memory.  Errors: INVALID_ARG. */
+egpe_status egpe_lhy_table_eval(const egpe_params* params, int count, const double* n1, const double* n2,
+                                double* mu, double* hess, int info[2]);
+
 /* Poll budget of the device-side waits of every engine of the handle (the
  * TMA tile loads of the column passes; default 2^20 polls, roughly a second).
  * No counterpart in the paper: a guard of this implementation.  A wait that
@@ -398,7 +421,7 @@ const char* egpe_status_string(egpe_status s);
 /* Message of the last CUDA error seen by this thread's calls ("" if none). */
 const char* egpe_last_error(void);
 
-/* ABI version (major * 100 + minor): 101. */
+/* ABI version (major * 100 + minor): 102. */
 int egpe_version(void);
 
 #ifdef __cplusplus

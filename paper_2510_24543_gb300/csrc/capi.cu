@@ -12,6 +12,7 @@
 
 #include "egpe.h"
 #include "engine.h"
+#include "host_tables.h"
 
 namespace egpe {
 
@@ -33,6 +34,7 @@ struct egpe_handle {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // default-stream ordering of an owned stream
   std::vector<Engine<double>*> e64;
   std::vector<Engine<float>*> e32;
   std::vector<egpe_grid> grids;
@@ -95,6 +97,30 @@ egpe_status validate(const egpe_grid& g, const egpe_params& p) {
 
 bool bad_inst(egpe_handle* h, int inst) { return !h || inst < 0 || inst >= h->n_inst; }
 
+// A handle created without a stream works on a stream of its own, which does
+// not synchronise with the legacy default stream by itself.  Every call on
+// such a handle is therefore ordered after the work already submitted to the
+// legacy default stream (the caller's writes of its input buffers), and the
+// legacy default stream after the call's own work (its writes of the output
+// buffers), so callers on the default stream need no synchronisation.
+struct DefaultStreamJoin {
+  egpe_handle* h;
+  explicit DefaultStreamJoin(egpe_handle* hh) : h(hh) {
+    if (h->own_stream) {
+      cudaEventRecord(h->ev_in, cudaStreamLegacy);
+      cudaStreamWaitEvent(h->stream, h->ev_in, 0);
+    }
+  }
+  ~DefaultStreamJoin() {
+    if (h->own_stream) {
+      cudaEventRecord(h->ev_out, h->stream);
+      cudaStreamWaitEvent(cudaStreamLegacy, h->ev_out, 0);
+    }
+  }
+  DefaultStreamJoin(const DefaultStreamJoin&) = delete;
+  DefaultStreamJoin& operator=(const DefaultStreamJoin&) = delete;
+};
+
 egpe_status sync_and_check(egpe_handle* h) {
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -108,7 +134,7 @@ egpe_status sync_and_check(egpe_handle* h) {
 
 extern "C" {
 
-int egpe_version(void) { return 101; }
+int egpe_version(void) { return 102; }
 
 const char* egpe_last_error(void) { return egpe::g_last_error.c_str(); }
 
@@ -174,8 +200,12 @@ egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n
     h->stream = (cudaStream_t)cuda_stream;
   } else {
     cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-      egpe::set_error("cudaStreamCreateWithFlags", e);
+      egpe::set_error("cudaStreamCreateWithFlags/cudaEventCreateWithFlags", e);
+      if (h->ev_in) cudaEventDestroy(h->ev_in);
+      if (h->stream) cudaStreamDestroy(h->stream);
       delete h;
       return EGPE_ERR_CUDA;
     }
@@ -217,11 +247,14 @@ void egpe_destroy(egpe_handle* h) {
   for (auto* e : h->e64) delete e;
   for (auto* e : h->e32) delete e;
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   delete h;
 }
 
 egpe_status egpe_energy_terms_eval(egpe_handle* h, int inst, const void* psi, egpe_energy_terms* terms, void* grad) {
   if (bad_inst(h, inst) || !psi) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   if (h->prec == EGPE_FP32)
     return h->e32[inst]->energy_grad((const float2*)psi, terms, (float2*)grad);
   return h->e64[inst]->energy_grad((const double2*)psi, terms, (double2*)grad);
@@ -241,12 +274,14 @@ egpe_status egpe_energy_grad(egpe_handle* h, int inst, const void* psi, double* 
 
 egpe_status egpe_line_coeffs(egpe_handle* h, int inst, const void* psi, const void* p, double coeffs[3]) {
   if (bad_inst(h, inst) || !psi || !p || !coeffs) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   if (h->prec == EGPE_FP32) return h->e32[inst]->line_coeffs((const float2*)psi, (const float2*)p, coeffs);
   return h->e64[inst]->line_coeffs((const double2*)psi, (const double2*)p, coeffs);
 }
 
 egpe_status egpe_precondition(egpe_handle* h, int inst, int mode, const void* psi, const void* r, void* z) {
   if (bad_inst(h, inst) || !psi || !z || mode < 0 || mode > 4) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   if (h->prec == EGPE_FP32)
     return h->e32[inst]->precondition(mode, (const float2*)psi, (const float2*)r, (float2*)z);
   return h->e64[inst]->precondition(mode, (const double2*)psi, (const double2*)r, (double2*)z);
@@ -255,6 +290,7 @@ egpe_status egpe_precondition(egpe_handle* h, int inst, int mode, const void* ps
 egpe_status egpe_retract(egpe_handle* h, int inst, const void* psi, const void* p, const double theta[2],
                          void* psi_out) {
   if (bad_inst(h, inst) || !psi || !p || !theta || !psi_out) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   if (!std::isfinite(theta[0]) || !std::isfinite(theta[1])) return EGPE_ERR_INVALID_ARG;
   if (h->prec == EGPE_FP32)
     return h->e32[inst]->retract((const float2*)psi, (const float2*)p, theta, (float2*)psi_out);
@@ -263,6 +299,7 @@ egpe_status egpe_retract(egpe_handle* h, int inst, const void* psi, const void* 
 
 egpe_status egpe_fft(egpe_handle* h, int inst, const void* in, void* out, int nfields, int inverse) {
   if (bad_inst(h, inst) || !in || !out || nfields < 1 || nfields > 64) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   if (h->prec == EGPE_FP32) return h->e32[inst]->fft((const float2*)in, (float2*)out, nfields, inverse ? 1 : 0);
   return h->e64[inst]->fft((const double2*)in, (double2*)out, nfields, inverse ? 1 : 0);
 }
@@ -272,6 +309,7 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
   if (bad_inst(h, inst) || !psi || precond < 0 || precond > 4 || reps < 1 || cap < 1 || !names || !ms || !bytes ||
       !count)
     return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   std::vector<std::string> nm;
   std::vector<double> t, b;
   egpe_status s;
@@ -296,12 +334,14 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
 
 egpe_status egpe_param_grad(egpe_handle* h, int inst, const void* psi, double* dEdp) {
   if (bad_inst(h, inst) || !psi || !dEdp) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   if (h->prec == EGPE_FP32) return h->e32[inst]->param_grad((const float2*)psi, dEdp);
   return h->e64[inst]->param_grad((const double2*)psi, dEdp);
 }
 
 egpe_status egpe_set_params(egpe_handle* h, int inst, const egpe_params* params) {
   if (bad_inst(h, inst) || !params) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   egpe_status s = validate(h->grids[inst], *params);
   if (s != EGPE_OK) return s;
   if (!h->e64.empty()) {
@@ -316,6 +356,7 @@ egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi,
                           egpe_tuning* out, int cap, int* count) {
   if (bad_inst(h, inst) || !psi || precond < 0 || precond > 4 || reps < 1 || cap < 0 || (cap > 0 && !out))
     return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   std::vector<egpe::TuneResult> res;
   egpe_status s;
   if (engine == 0 && !h->e64.empty()) s = h->e64[inst]->autotune((const double2*)psi, precond, reps, res);
@@ -339,6 +380,55 @@ egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi,
   return EGPE_OK;
 }
 
+egpe_status egpe_lhy_table_eval(const egpe_params* params, int count, const double* n1, const double* n2,
+                                double* mu, double* hess, int info[2]) {
+  if (!params || count < 0 || (count > 0 && (!n1 || !n2 || !mu || !hess))) return EGPE_ERR_INVALID_ARG;
+  const egpe_grid g1 = {{16, 16, 16}, {1.0, 1.0, 1.0}};
+  egpe_status s = validate(g1, *params);
+  if (s != EGPE_OK) return s;
+  const egpe_params& p = *params;
+  const egpe::LhyTableHost& T = egpe::lhy_interp_table_cached(p);
+  if (info) {
+    info[0] = T.ni;
+    info[1] = (int)T.exact.size();
+  }
+  std::vector<long double> u, w;
+  egpe::gauss_legendre01(p.lhy_nodes, u, w);
+  const long double c5 = (long double)p.lhy_kappa * powl((long double)p.lhy_eta_scale, -2.5L);
+  const double tscale = T.ni * 1.4142135623730950488;
+  for (int k = 0; k < count; ++k) {
+    if (!(n1[k] >= 0.0) || !(n2[k] >= 0.0)) return EGPE_ERR_INVALID_ARG;
+    long double o[egpe::kTabFun] = {};
+    for (int q : T.exact) {
+      const long double sw = 3.0L * u[q] * u[q] - 1.0L;
+      egpe::lhy_node_terms(p.g[0][0] + p.gdd[0][0] * sw, p.g[1][1] + p.gdd[1][1] * sw, p.g[0][1] + p.gdd[0][1] * sw,
+                           c5 * w[q], n1[k], n2[k], o);
+    }
+    double v[egpe::kTabFun];
+    for (int f = 0; f < egpe::kTabFun; ++f) v[f] = (double)o[f];
+    const double n = n1[k] + n2[k];
+    if (T.ni > 0 && n > 0.0) {  // the device evaluation, in FP64 on the host
+      const int half = n1[k] > n2[k];
+      const double a = std::sqrt(half ? n2[k] : n1[k]) / std::sqrt(n);
+      const double tt = a * tscale;
+      const int i = std::min((int)tt, T.ni - 1);
+      const double x = 2.0 * (tt - i) - 1.0;
+      const long double* c = &T.coef[((size_t)half * T.ni + i) * egpe::kTabRec];
+      for (int f = 0; f < egpe::kTabFun; ++f) {
+        double pv = (double)c[f * egpe::kTabCoef + egpe::kTabDeg];
+        for (int m = egpe::kTabDeg - 1; m >= 0; --m) pv = std::fma(pv, x, (double)c[f * egpe::kTabCoef + m]);
+        v[f] += (f < 2 ? n * std::sqrt(n) : std::sqrt(n)) * pv;
+      }
+    }
+    mu[2 * k] = v[0];
+    mu[2 * k + 1] = v[1];
+    hess[3 * k] = v[2];
+    hess[3 * k + 1] = v[3];
+    hess[3 * k + 2] = v[4];
+  }
+  return EGPE_OK;
+}
+
 egpe_status egpe_set_wait_limit(egpe_handle* h, long long polls) {
   if (!h || polls < 0) return EGPE_ERR_INVALID_ARG;
   for (auto* e : h->e64) e->set_wait_limit(polls);
@@ -348,6 +438,7 @@ egpe_status egpe_set_wait_limit(egpe_handle* h, long long polls) {
 
 egpe_status egpe_set_tuning(egpe_handle* h, int inst, int engine, const egpe_tuning* t, int count) {
   if (bad_inst(h, inst) || count < 0 || (count > 0 && !t)) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   for (int k = 0; k < count; ++k) {
     std::string key(t[k].key, strnlen(t[k].key, sizeof(t[k].key)));
     if (engine == 0 && !h->e64.empty()) h->e64[inst]->set_tuning(key, t[k].choice);
@@ -365,6 +456,7 @@ static bool opts_ok(const egpe_solve_opts& o) {
 
 egpe_status egpe_solver_start(egpe_handle* h, int inst, int engine, const void* psi, const egpe_solve_opts* opts) {
   if (bad_inst(h, inst) || !psi || !opts || !opts_ok(*opts)) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   const egpe_solve_opts& o = *opts;
   if (engine == 0 && !h->e64.empty()) {
     auto* e = h->e64[inst];
@@ -383,6 +475,7 @@ egpe_status egpe_solver_start(egpe_handle* h, int inst, int engine, const void* 
 
 egpe_status egpe_solver_step(egpe_handle* h, int inst, int engine, int attempts) {
   if (bad_inst(h, inst) || attempts < 0) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   if (engine == 0 && !h->e64.empty()) return h->e64[inst]->solve_launch(attempts);
   if (engine == 1 && !h->e32.empty()) return h->e32[inst]->solve_launch(attempts);
   return EGPE_ERR_INVALID_ARG;
@@ -390,6 +483,7 @@ egpe_status egpe_solver_step(egpe_handle* h, int inst, int engine, int attempts)
 
 egpe_status egpe_solver_read(egpe_handle* h, int inst, int engine, egpe_report* report, void* psi_out) {
   if (bad_inst(h, inst) || !report) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   egpe::SolveRun run{};
   egpe_status s;
   if (engine == 0 && !h->e64.empty()) {
@@ -592,6 +686,7 @@ extern "C" {
 egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_solve_opts* opts,
                            egpe_report* reports) {
   if (!h || !psi_inout || !opts) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   const egpe_solve_opts& o = *opts;
   if (!opts_ok(o)) {
     egpe::set_error_msg("egpe_ncg_solve: bad options");
@@ -616,6 +711,7 @@ egpe_status egpe_ncg_solve(egpe_handle* h, void* const* psi_inout, const egpe_so
 egpe_status egpe_ncg_continuation(egpe_handle* h, int inst, const egpe_params* path, int npoints, void* psi_inout,
                                   void* const* psi_out, const egpe_solve_opts* opts, egpe_report* reports) {
   if (bad_inst(h, inst) || !path || npoints < 1 || !psi_inout || !opts) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   const egpe_solve_opts& o = *opts;
   if (!opts_ok(o)) {
     egpe::set_error_msg("egpe_ncg_continuation: bad options");
@@ -665,6 +761,7 @@ void egpe_default_ite_opts(egpe_ite_opts* o) {
 egpe_status egpe_ite_solve(egpe_handle* h, void* const* psi_inout, const egpe_ite_opts* opts,
                            egpe_report* reports) {
   if (!h || !psi_inout || !opts) return EGPE_ERR_INVALID_ARG;
+  DefaultStreamJoin join(h);
   const egpe_ite_opts& o = *opts;
   if (!(o.dtau > 0.0) || !std::isfinite(o.dtau) || !(o.tol_dE > 0.0) || o.max_steps <= 0 || o.poll_every < 0) {
     egpe::set_error_msg("egpe_ite_solve: dtau and tol_dE must be positive and finite, max_steps > 0");

@@ -203,6 +203,9 @@ template <class R> class Engine {
   C* twz_ = nullptr;
   LhyNode<R>* nodes_ = nullptr;
   int nodes_q_ = 0;
+  LhyNode<R>* xnodes_ = nullptr;    // nodes evaluated exactly beside the LHY table
+  R* tab_ = nullptr;                // LHY interpolation table (host_tables.h)
+  size_t tab_elems_ = 0;
   double* partials_ = nullptr;
   unsigned* counter_ = nullptr;
   DevState* st_ = nullptr;

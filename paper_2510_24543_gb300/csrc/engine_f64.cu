@@ -230,7 +230,13 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
   a.Q = p.lhy_nodes;
   a.Qm = qm;
   a.nskip = lhy_skip_threshold(p);
+  // every node evaluated exactly per point (no interpolation table here)
+  a.Qx = a.Q;
+  a.Qxm = qm;
+  a.tab.tab = nullptr;
+  a.tab.ni = 0;
   a.nodes = (const LhyNode<double>*)(base + kOffNodes);
+  a.xnodes = a.nodes;
   a.twx = twd;
   a.twy = twd + kNoAllocMaxN;
   a.twz = twd + 2 * kNoAllocMaxN;

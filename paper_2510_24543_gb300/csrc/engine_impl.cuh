@@ -104,7 +104,31 @@ template <class R> egpe_status Engine<R>::apply_params(const egpe_params& p) {
     nodes_q_ = Q;
   }
   EGPE_CUDA(cudaMemcpy(nodes_, h.data(), Q * sizeof(LhyNode<R>), cudaMemcpyHostToDevice));
+  // interpolated LHY sums and the nodes left to exact evaluation
+  const LhyTableHost& T = lhy_interp_table_cached(p);
+  std::vector<R> tab(T.coef.begin(), T.coef.end());
+  if (tab_ && tab_elems_ != tab.size()) {
+    cudaFree(tab_);
+    tab_ = nullptr;
+    tab_elems_ = 0;
+  }
+  if (!tab_ && !tab.empty()) {
+    EGPE_CUDA(cudaMalloc(&tab_, tab.size() * sizeof(R)));
+    tab_elems_ = tab.size();
+  }
+  if (!tab.empty()) EGPE_CUDA(cudaMemcpy(tab_, tab.data(), tab.size() * sizeof(R), cudaMemcpyHostToDevice));
+  std::vector<LhyNode<R>> xh(std::max<size_t>(T.exact.size(), 1));
+  const int Qxm = lhy_node_table<R>(p, xh.data(), &T.exact);
+  if (!xnodes_) EGPE_CUDA(cudaMalloc(&xnodes_, 64 * sizeof(LhyNode<R>)));
+  if (!T.exact.empty())
+    EGPE_CUDA(cudaMemcpy(xnodes_, xh.data(), T.exact.size() * sizeof(LhyNode<R>), cudaMemcpyHostToDevice));
   KArgs<R>& a = *base_;
+  a.xnodes = xnodes_;
+  a.Qx = (int)T.exact.size();
+  a.Qxm = Qxm;
+  a.tab.tab = T.ni ? tab_ : nullptr;
+  a.tab.ni = T.ni;
+  a.tab.tscale = (R)(T.ni * 1.4142135623730950488);
   a.vx = (R)(0.5 * p.trap[0] * p.trap[0]);
   a.vy = (R)(0.5 * p.trap[1] * p.trap[1]);
   a.vz = (R)(0.5 * p.trap[2] * p.trap[2]);
@@ -279,6 +303,8 @@ template <class R> void Engine<R>::destroy() {
   if (twy_) cudaFree(twy_);
   if (twz_) cudaFree(twz_);
   if (nodes_) cudaFree(nodes_);
+  if (xnodes_) cudaFree(xnodes_);
+  if (tab_) cudaFree(tab_);
   if (partials_) cudaFree(partials_);
   if (counter_) cudaFree(counter_);
   if (st_) cudaFree(st_);
@@ -288,6 +314,9 @@ template <class R> void Engine<R>::destroy() {
   arena_ = nullptr;
   twx_ = twy_ = twz_ = nullptr;
   nodes_ = nullptr;
+  xnodes_ = nullptr;
+  tab_ = nullptr;
+  tab_elems_ = 0;
   partials_ = nullptr;
   counter_ = nullptr;
   st_ = nullptr;

@@ -40,7 +40,10 @@ template <class R> struct KArgs {
   R invN;
   int Q, Qm;  // Gauss-Legendre nodes; the first Qm have det eta > 0
   R nskip;    // LHY terms skipped where n1 + n2 <= nskip (their size is below 1e-30)
-  const LhyNode<R>* nodes;
+  const LhyNode<R>* nodes;   // all Q nodes (parameter derivatives)
+  const LhyNode<R>* xnodes;  // the Qx nodes evaluated exactly next to the table (det eta > 0 first: Qxm)
+  int Qx, Qxm;
+  LhyTab<R> tab;             // interpolated sums over the other nodes (tab.ni = 0: none)
   const C* twx;
   const C* twy;
   const C* twz;
@@ -129,6 +132,15 @@ template <class Op> struct MinBlocks<Op, std::void_t<decltype(Op::MINB)>> {
   static constexpr int v = Op::MINB;
 };
 
+// Row-pass ops whose LHY terms come from the interpolation table plus the
+// exactly evaluated nodes (they stage the exact nodes only).
+template <class Op, class = void> struct LhyTabOp {
+  static constexpr bool v = false;
+};
+template <class Op> struct LhyTabOp<Op, std::void_t<decltype(Op::LHY_TAB)>> {
+  static constexpr bool v = Op::LHY_TAB;
+};
+
 // Threads per block of a row pass: 256 unless the op asks for fewer.
 template <class Op, class = void> struct MaxThreads {
   static constexpr int v = 256;
@@ -156,7 +168,10 @@ template <class Op> __device__ __forceinline__ void xpass_body(const KArgs<typen
   const int tid = threadIdx.x;
   const int mrow = tid / TPL, t = tid - mrow * TPL;
   for (int i = tid; i < L; i += blockDim.x) tw[i] = a.twx[i];
-  if (Op::USES_LHY) stage_lhy_nodes(nodes, a.nodes, a.Q);
+  if constexpr (Op::USES_LHY) {
+    if constexpr (LhyTabOp<Op>::v) stage_lhy_nodes(nodes, a.xnodes, a.Qx);
+    else stage_lhy_nodes(nodes, a.nodes, a.Q);
+  }
   __syncthreads();
   typename Op::Uni u;
   Op::uniform(a, u);
@@ -608,6 +623,67 @@ template <class R_, int L_> struct ZEg {
   static __device__ void finish(const KArgs<R>&, Uni&) {}
 };
 
+// mu_LHY,i and the LHY energy density at NP points: the interpolation table
+// plus the exactly evaluated nodes; F from Euler's identity for the degree-5/2
+// density, F = (2/5)(n1 mu1 + n2 mu2).
+template <class R, int NP>
+__device__ __forceinline__ void lhy_terms(const KArgs<R>& a, const LhyNode<R>* nodes, const LhyCoef<R>& cf,
+                                          const R (&n1)[NP], const R (&n2)[NP], R (&F)[NP], R (&m1)[NP],
+                                          R (&m2)[NP]) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) m1[j] = m2[j] = R(0);
+  if (a.Qx > 0) {
+    // exact nodes two points at a time (few registers for a rarely long loop)
+#pragma unroll
+    for (int j = 0; j < NP; j += 2) {
+      const R q1[2] = {n1[j], n1[j + 1]}, q2[2] = {n2[j], n2[j + 1]};
+      R f[2], x1[2], x2[2];
+      lhy_points<R, 2>(nodes, a.Qx, a.Qxm, cf, q1, q2, f, x1, x2);
+      m1[j] = x1[0];
+      m1[j + 1] = x1[1];
+      m2[j] = x2[0];
+      m2[j + 1] = x2[1];
+    }
+  }
+  if (a.tab.ni > 0) {
+    R t1[NP], t2[NP];
+    lhy_tab_mu<R, NP>(a.tab, n1, n2, t1, t2);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      m1[j] += t1[j];
+      m2[j] += t2[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NP; ++j) F[j] = R(0.4) * (n1[j] * m1[j] + n2[j] * m2[j]);
+}
+
+// n'^T (d^2 F/dn dn) n' at NP points: table plus exactly evaluated nodes.
+template <class R, int NP>
+__device__ __forceinline__ void lhy_second(const KArgs<R>& a, const LhyNode<R>* nodes, const LhyCoef<R>& cf,
+                                           const R (&n1)[NP], const R (&n2)[NP], const R (&n1p)[NP],
+                                           const R (&n2p)[NP], R (&H)[NP]) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) H[j] = R(0);
+  if (a.Qx > 0) {
+#pragma unroll
+    for (int j = 0; j < NP; j += 2) {
+      const R q1[2] = {n1[j], n1[j + 1]}, q2[2] = {n2[j], n2[j + 1]};
+      const R p1[2] = {n1p[j], n1p[j + 1]}, p2[2] = {n2p[j], n2p[j + 1]};
+      R hx[2];
+      lhy_hess<R, 2>(nodes, a.Qx, a.Qxm, cf, q1, q2, p1, p2, hx);
+      H[j] = hx[0];
+      H[j + 1] = hx[1];
+    }
+  }
+  if (a.tab.ni > 0) {
+    R t[NP];
+    lhy_tab_hess<R, NP>(a.tab, n1, n2, n1p, n2p, t);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) H[j] += t[j];
+  }
+}
+
 template <class R_, int L_> struct XInvEG {
   using R = R_;
   using C = C2<R>;
@@ -616,7 +692,7 @@ template <class R_, int L_> struct XInvEG {
   static constexpr const char* NAME = "x-inv energy+LHY";
   static double alg_bytes(const KArgs<R>& a) { return 9.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 3, NS = EG_NS;
-  static constexpr bool INV = true, USES_LHY = true;
+  static constexpr bool INV = true, USES_LHY = true, LHY_TAB = true;
   using Uni = EgUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { XFwdEG<R, L>::uniform(a, u); }
   static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*) {
@@ -656,7 +732,7 @@ template <class R_, int L_> struct XInvEG {
         n1[j] = cabs2(p1[j]);
         n2[j] = cabs2(p2[j]);
       }
-      lhy_points<R, NP>(nodes, a.Q, a.Qm, cf, n1, n2, F, m1, m2);
+      lhy_terms<R, NP>(a, nodes, cf, n1, n2, F, m1, m2);
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
         const int e = e0 + j;
@@ -1142,7 +1218,7 @@ template <class R_, int L_> struct XInvLC {
   static constexpr const char* NAME = "x-inv line sums+LHY";
   static double alg_bytes(const KArgs<R>& a) { return 9.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 1, NS = LC_NS;
-  static constexpr bool INV = true, USES_LHY = true;
+  static constexpr bool INV = true, USES_LHY = true, LHY_TAB = true;
   using Uni = LcUni<R>;
   static __device__ void uniform(const KArgs<R>& a, Uni& u) { lc_uniform(a, u); }
   static __device__ void load(const KArgs<R>& a, Uni&, int row, bool valid, int t, C (&v)[1][8], PAcc<R>*) {
@@ -1198,7 +1274,7 @@ template <class R_, int L_> struct XInvLC {
         s[LC_UPP2] += U2 * a2;
         s[LC_SRHO] += rho1 * (a.g11 * rho1 + a.g12 * rho2 + v[0][e].x) + rho2 * (a.g21 * rho1 + a.g22 * rho2 + v[0][e].y);
       }
-      lhy_hess<R, NP>(nodes, a.Q, a.Qm, cf, n1, n2, n1p, n2p, Hh);
+      lhy_second<R, NP>(a, nodes, cf, n1, n2, n1p, n2p, Hh);
 #pragma unroll
       for (int j = 0; j < NP; ++j) s[LC_HLHY] += Hh[j];
     }

@@ -454,4 +454,101 @@ __device__ __forceinline__ void lhy_eta_sums(const LhyNode<R>* __restrict__ nd, 
   }
 }
 
+// ----------------------------------------------------------------------------
+// Interpolated LHY terms.  The LHY density is homogeneous of degree 5/2 in
+// (n1, n2), so with n = n1 + n2 and a = sqrt(min(n1, n2)/n):
+//   mu_LHY,i = n^{3/2} m_i(a),   d^2 F/dn_i dn_j = n^{1/2} h_ij(a),
+// where m_i, h_ij are the quadrature sums over the table's nodes, stored per
+// half (n1 <= n2, n1 > n2) as degree-11 polynomials on equal intervals of a
+// (host_tables.h builds and checks them).  A record holds, per interval, the
+// 12 coefficients of m1, m2, h11, h12, h22 in the local coordinate x in [-1,1].
+// ----------------------------------------------------------------------------
+constexpr int kLhyTabCoef = 12;
+constexpr int kLhyTabRec = 5 * kLhyTabCoef;
+
+template <class R> struct LhyTab {
+  const R* tab;  // [half][interval][function][coefficient], 16-byte aligned records
+  int ni;        // intervals per half (0: no table)
+  R tscale;      // ni sqrt(2): a tscale is the interval coordinate
+};
+
+// Polynomial of degree 11 at x (Horner), coefficients from global memory
+// through the read-only path in 16-byte loads.
+__device__ __forceinline__ float horner12(const float* c, float x) {
+  const float4* v = reinterpret_cast<const float4*>(c);
+  const float4 a = __ldg(v), b = __ldg(v + 1), d = __ldg(v + 2);
+  float p = d.w;
+  p = fmaf(p, x, d.z);
+  p = fmaf(p, x, d.y);
+  p = fmaf(p, x, d.x);
+  p = fmaf(p, x, b.w);
+  p = fmaf(p, x, b.z);
+  p = fmaf(p, x, b.y);
+  p = fmaf(p, x, b.x);
+  p = fmaf(p, x, a.w);
+  p = fmaf(p, x, a.z);
+  p = fmaf(p, x, a.y);
+  return fmaf(p, x, a.x);
+}
+__device__ __forceinline__ double horner12(const double* c, double x) {
+  const double2* v = reinterpret_cast<const double2*>(c);
+  double2 k[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) k[i] = __ldg(v + i);
+  double p = k[5].y;
+  p = fma(p, x, k[5].x);
+#pragma unroll
+  for (int i = 4; i >= 0; --i) {
+    p = fma(p, x, k[i].y);
+    p = fma(p, x, k[i].x);
+  }
+  return p;
+}
+
+// Interval record of (n1, n2) and its local coordinate x; rs = 1/sqrt(n) (1
+// where n = 0, whose terms vanish with their n-power prefactor).
+template <class R>
+__device__ __forceinline__ const R* lhy_tab_locate(const LhyTab<R>& t, R n1, R n2, R& x, R& rs) {
+  const R n = n1 + n2;
+  rs = rsqrt_(n > R(0) ? n : R(1));
+  const bool h = n1 > n2;
+  const R a = sqrt_pos(h ? n2 : n1) * rs;
+  const R tt = a * t.tscale;
+  int i = (int)tt;  // a <= 1/sqrt(2) up to rounding: clamp to the last interval (NaN converts to 0)
+  i = i < 0 ? 0 : (i < t.ni - 1 ? i : t.ni - 1);
+  x = R(2) * (tt - (R)i) - R(1);
+  return t.tab + (size_t)((h ? t.ni : 0) + i) * kLhyTabRec;
+}
+
+// The table's part of mu_LHY,1 and mu_LHY,2 at NP points.
+template <class R, int NP>
+__device__ __forceinline__ void lhy_tab_mu(const LhyTab<R>& t, const R (&n1)[NP], const R (&n2)[NP], R (&m1)[NP],
+                                           R (&m2)[NP]) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    R x, rs;
+    const R* c = lhy_tab_locate(t, n1[j], n2[j], x, rs);
+    const R n = n1[j] + n2[j];
+    const R n32 = n * n * rs;
+    m1[j] = n32 * horner12(c, x);
+    m2[j] = n32 * horner12(c + kLhyTabCoef, x);
+  }
+}
+
+// The table's part of n'^T (d^2 F/dn dn) n' at NP points.
+template <class R, int NP>
+__device__ __forceinline__ void lhy_tab_hess(const LhyTab<R>& t, const R (&n1)[NP], const R (&n2)[NP],
+                                             const R (&n1p)[NP], const R (&n2p)[NP], R (&H)[NP]) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    R x, rs;
+    const R* c = lhy_tab_locate(t, n1[j], n2[j], x, rs);
+    const R n = n1[j] + n2[j];
+    const R h11 = horner12(c + 2 * kLhyTabCoef, x);
+    const R h12 = horner12(c + 3 * kLhyTabCoef, x);
+    const R h22 = horner12(c + 4 * kLhyTabCoef, x);
+    H[j] = n * rs * (n1p[j] * (h11 * n1p[j] + R(2) * h12 * n2p[j]) + h22 * n2p[j] * n2p[j]);
+  }
+}
+
 }  // namespace egpe

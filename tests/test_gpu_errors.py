@@ -67,8 +67,9 @@ def test_nonfinite_start(E, prec):
     with np.errstate(invalid="ignore"):
         _, orep = O.ncg_solve(g, prm, bad, O.SolveOpts(precond="kinetic", tol_res=1e-8, max_iter=5))
     assert orep["status"] == "nonfinite"
-    # the next solve on a fresh handle is unaffected
-    st, rep, _ = _solve(E, w, psi, prec, _opts(E, tol_res=1e-6))
+    # the next solve on a fresh handle is unaffected (a tolerance above the
+    # FP32 fields' round-off floor when there is an FP32 phase)
+    st, rep, _ = _solve(E, w, psi, prec, _opts(E, tol_res=1e-6 if prec == 0 else 1e-4))
     assert st == 0 and rep["status"] == 0
 
 
@@ -101,18 +102,18 @@ def test_timeout_of_a_device_wait(E, prec):
     try:
         E.egpe_set_wait_limit(h, 0)
         x = torch.from_numpy(psi).to("cuda").to(cd)
-        st, reps, _ = E.egpe_ncg_solve(h, [x], _opts(E, tol_res=1e-6), 1)
+        st, reps, _ = E.egpe_ncg_solve(h, [x], _opts(E, tol_res=1e-4), 1)
         assert st == 7 and reps[0]["status"] == 7, reps[0]
         with pytest.raises(E.EgpeError) as ei:
             E.egpe_energy_grad(h, 0, x)
         assert ei.value.status == 7
         E.egpe_set_wait_limit(h, 1 << 20)
         x = torch.from_numpy(psi).to("cuda").to(cd)
-        st, reps, _ = E.egpe_ncg_solve(h, [x], _opts(E, tol_res=1e-6), 1)
+        st, reps, _ = E.egpe_ncg_solve(h, [x], _opts(E, tol_res=1e-4), 1)
         assert st == 0 and reps[0]["status"] == 0
         E_restored = reps[0]["E"]
     finally:
         E.egpe_destroy(h)
-    st, rep, _ = _solve(E, w, psi, prec, _opts(E, tol_res=1e-6))
+    st, rep, _ = _solve(E, w, psi, prec, _opts(E, tol_res=1e-4))
     assert st == 0 and rep["status"] == 0
     assert abs(rep["E"] - E_restored) <= 1e-12 * abs(E_restored)
