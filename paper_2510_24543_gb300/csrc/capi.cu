@@ -387,7 +387,7 @@ egpe_status egpe_lhy_table_eval(const egpe_params* params, int count, const doub
   egpe_status s = validate(g1, *params);
   if (s != EGPE_OK) return s;
   const egpe_params& p = *params;
-  const egpe::LhyTableHost& T = egpe::lhy_interp_table_cached(p);
+  const egpe::LhyTableHost T = egpe::lhy_interp_table_cached(p);
   if (info) {
     info[0] = T.ni;
     info[1] = (int)T.exact.size();

@@ -335,8 +335,9 @@ inline LhyTableHost lhy_interp_table(const egpe_params& p) {
 }
 
 // The tables of one parameter set, built once per process (the FP32 and FP64
-// engines of an instance, and repeated handles, share the build).
-inline const LhyTableHost& lhy_interp_table_cached(const egpe_params& p) {
+// engines of an instance, and repeated handles, share the build); returned by
+// value, so a later eviction cannot invalidate a caller's copy.
+inline LhyTableHost lhy_interp_table_cached(const egpe_params& p) {
   static std::mutex mu;
   static std::map<std::vector<double>, LhyTableHost> memo;
   const std::vector<double> key = {p.g[0][0], p.g[0][1], p.g[1][0], p.g[1][1], p.gdd[0][0], p.gdd[0][1],

@@ -163,6 +163,41 @@ def _ptr(x) -> int:
     raise TypeError(type(x))
 
 
+# Handles created through this binding: precision and grid sizes, so that
+# tensor arguments can be checked before the library sees their pointers.
+_HANDLES = {}
+
+
+def _field(h: int, inst: int, t, name: str = "psi", nf: int = 2, engine: Optional[int] = None,
+           on_host: bool = False):
+    """Pointer of a field argument.  A tensor is checked against the handle:
+    a CUDA tensor (a host tensor when on_host), contiguous, complex64 for the
+    FP32 engine and complex128 otherwise, with nf*nx*ny*nz elements of
+    instance inst's grid; ValueError otherwise.  Raw integer pointers are
+    passed through unchecked."""
+    if t is None or isinstance(t, int):
+        return t
+    info = _HANDLES.get(h)
+    if info is not None and hasattr(t, "dtype"):
+        prec, grids = info
+        if not 0 <= inst < len(grids):
+            raise ValueError(f"instance {inst} out of range")
+        n = grids[inst]
+        if engine is None:
+            engine = 1 if prec == EGPE_FP32 else 0
+        want_dtype = "torch.complex64" if engine == 1 else "torch.complex128"
+        want = nf * n[0] * n[1] * n[2]
+        if bool(t.is_cuda) == bool(on_host):
+            raise ValueError(f"{name} must be a {'host' if on_host else 'CUDA'} tensor")
+        if str(t.dtype) != want_dtype:
+            raise ValueError(f"{name} must be {want_dtype[6:]} for this handle/engine, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() != want:
+            raise ValueError(f"{name} has {t.numel()} elements; instance {inst} needs {want}")
+    return _ptr(t)
+
+
 def make_grid(n, L) -> egpe_grid:
     g = egpe_grid()
     for a in range(3):
@@ -193,19 +228,21 @@ def egpe_create(grids: Sequence[egpe_grid], params: Sequence[egpe_params], prec:
     P = (egpe_params * n)(*params)
     h = ct.c_void_p()
     _check("egpe_create", lib.egpe_create(G, P, n, prec, ct.c_void_p(stream or None), ct.byref(h)))
+    _HANDLES[h.value] = (prec, [tuple(g.n) for g in grids])
     return h.value
 
 
 def egpe_destroy(h: int):
     if h:
+        _HANDLES.pop(h, None)
         load().egpe_destroy(ct.c_void_p(h))
 
 
 def egpe_energy_terms_eval(h: int, inst: int, psi, grad=None) -> dict:
     t = egpe_energy_terms()
     _check("egpe_energy_terms_eval",
-           load().egpe_energy_terms_eval(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), ct.byref(t),
-                                         ct.c_void_p(_ptr(grad))))
+           load().egpe_energy_terms_eval(ct.c_void_p(h), inst, ct.c_void_p(_field(h, inst, psi)), ct.byref(t),
+                                         ct.c_void_p(_field(h, inst, grad, "grad"))))
     return dict(E=t.E, kin1=t.kin[0], kin2=t.kin[1], trap=t.trap, contact=t.contact, dipolar=t.dipolar,
                 lhy=t.lhy, mu=(t.mu[0], t.mu[1]), norm2=(t.norm2[0], t.norm2[1]), shift=(t.shift[0], t.shift[1]))
 
@@ -213,8 +250,8 @@ def egpe_energy_terms_eval(h: int, inst: int, psi, grad=None) -> dict:
 def egpe_energy_grad(h: int, inst: int, psi, grad=None):
     E = ct.c_double()
     mu = (ct.c_double * 2)()
-    _check("egpe_energy_grad", load().egpe_energy_grad(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), ct.byref(E),
-                                                       mu, ct.c_void_p(_ptr(grad))))
+    _check("egpe_energy_grad", load().egpe_energy_grad(ct.c_void_p(h), inst, ct.c_void_p(_field(h, inst, psi)),
+                                                       ct.byref(E), mu, ct.c_void_p(_field(h, inst, grad, "grad"))))
     return E.value, (mu[0], mu[1])
 
 
@@ -253,24 +290,28 @@ def egpe_energy_grad_noalloc(grid: egpe_grid, params: egpe_params, psi, grad=Non
 
 def egpe_line_coeffs(h: int, inst: int, psi, p):
     c = (ct.c_double * 3)()
-    _check("egpe_line_coeffs", load().egpe_line_coeffs(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)),
-                                                       ct.c_void_p(_ptr(p)), c))
+    _check("egpe_line_coeffs", load().egpe_line_coeffs(ct.c_void_p(h), inst, ct.c_void_p(_field(h, inst, psi)),
+                                                       ct.c_void_p(_field(h, inst, p, "p")), c))
     return c[0], c[1], c[2]
 
 
 def egpe_precondition(h: int, inst: int, mode: int, psi, r, z):
-    _check("egpe_precondition", load().egpe_precondition(ct.c_void_p(h), inst, int(mode), ct.c_void_p(_ptr(psi)),
-                                                         ct.c_void_p(_ptr(r)), ct.c_void_p(_ptr(z))))
+    _check("egpe_precondition", load().egpe_precondition(ct.c_void_p(h), inst, int(mode),
+                                                         ct.c_void_p(_field(h, inst, psi)),
+                                                         ct.c_void_p(_field(h, inst, r, "r")),
+                                                         ct.c_void_p(_field(h, inst, z, "z"))))
 
 
 def egpe_retract(h: int, inst: int, psi, p, theta, out):
     th = (ct.c_double * 2)(float(theta[0]), float(theta[1]))
-    _check("egpe_retract", load().egpe_retract(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), ct.c_void_p(_ptr(p)),
-                                               th, ct.c_void_p(_ptr(out))))
+    _check("egpe_retract", load().egpe_retract(ct.c_void_p(h), inst, ct.c_void_p(_field(h, inst, psi)),
+                                               ct.c_void_p(_field(h, inst, p, "p")), th,
+                                               ct.c_void_p(_field(h, inst, out, "out"))))
 
 
 def egpe_fft(h: int, inst: int, x, out, nfields: int, inverse: bool = False):
-    _check("egpe_fft", load().egpe_fft(ct.c_void_p(h), inst, ct.c_void_p(_ptr(x)), ct.c_void_p(_ptr(out)),
+    _check("egpe_fft", load().egpe_fft(ct.c_void_p(h), inst, ct.c_void_p(_field(h, inst, x, "x", int(nfields))),
+                                       ct.c_void_p(_field(h, inst, out, "out", int(nfields))),
                                        int(nfields), 1 if inverse else 0))
 
 
@@ -280,7 +321,8 @@ def egpe_profile_attempt(h: int, inst: int, engine: int, psi, precond: int, reps
     ms = (ct.c_double * cap)()
     by = (ct.c_double * cap)()
     n = ct.c_int()
-    _check("egpe_profile_attempt", load().egpe_profile_attempt(ct.c_void_p(h), inst, engine, ct.c_void_p(_ptr(psi)),
+    _check("egpe_profile_attempt", load().egpe_profile_attempt(ct.c_void_p(h), inst, engine,
+                                                               ct.c_void_p(_field(h, inst, psi, engine=engine)),
                                                                int(precond), int(reps), cap, names, ms, by,
                                                                ct.byref(n)))
     raw = names.raw
@@ -301,7 +343,8 @@ def egpe_ncg_solve(h: int, psis, opts: egpe_solve_opts, n_inst: int = 1, trace_c
     """Runs the solver in place on psis (list of tensors/pointers).  Returns
     (status, [report dicts], [trace dicts of instance 0])."""
     lib = load()
-    ptrs = (ct.c_void_p * n_inst)(*[ct.c_void_p(_ptr(x)) for x in psis])
+    ptrs = (ct.c_void_p * n_inst)(*[ct.c_void_p(_field(h, i, x, on_host=bool(opts.psi_on_host)))
+                                    for i, x in enumerate(psis)])
     reps = (egpe_report * n_inst)()
     tr = None
     if trace_cap > 0:
@@ -331,7 +374,8 @@ def egpe_default_ite_opts() -> egpe_ite_opts:
 def egpe_ite_solve(h: int, psis, opts: egpe_ite_opts, n_inst: int = 1):
     """Imaginary-time evolution in place on psis.  Returns (status, [report dicts])."""
     lib = load()
-    ptrs = (ct.c_void_p * n_inst)(*[ct.c_void_p(_ptr(x)) for x in psis])
+    ptrs = (ct.c_void_p * n_inst)(*[ct.c_void_p(_field(h, i, x, on_host=bool(opts.psi_on_host)))
+                                    for i, x in enumerate(psis)])
     reps = (egpe_report * n_inst)()
     status = lib.egpe_ite_solve(ct.c_void_p(h), ptrs, ct.byref(opts), reps)
     if status in (1, 2, 3):
@@ -346,9 +390,12 @@ def egpe_ncg_continuation(h: int, inst: int, path, psi, opts: egpe_solve_opts, p
     P = (egpe_params * n)(*path)
     outs = None
     if psi_out is not None:
-        outs = (ct.c_void_p * n)(*[ct.c_void_p(_ptr(x)) for x in psi_out])
+        outs = (ct.c_void_p * n)(*[ct.c_void_p(_field(h, inst, x, "psi_out", on_host=bool(opts.psi_on_host)))
+                                   for x in psi_out])
     reps = (egpe_report * n)()
-    status = load().egpe_ncg_continuation(ct.c_void_p(h), inst, P, n, ct.c_void_p(_ptr(psi)), outs, ct.byref(opts),
+    status = load().egpe_ncg_continuation(ct.c_void_p(h), inst, P, n,
+                                          ct.c_void_p(_field(h, inst, psi, on_host=bool(opts.psi_on_host))), outs,
+                                          ct.byref(opts),
                                           reps)
     if status in (1, 2, 3):
         raise EgpeError("egpe_ncg_continuation", status)
@@ -358,7 +405,7 @@ def egpe_ncg_continuation(h: int, inst: int, path, psi, opts: egpe_solve_opts, p
 def egpe_param_grad(h: int, inst: int, psi) -> dict:
     """dE/dp at fixed psi for p in PARAM_NAMES."""
     out = (ct.c_double * len(PARAM_NAMES))()
-    _check("egpe_param_grad", load().egpe_param_grad(ct.c_void_p(h), inst, ct.c_void_p(_ptr(psi)), out))
+    _check("egpe_param_grad", load().egpe_param_grad(ct.c_void_p(h), inst, ct.c_void_p(_field(h, inst, psi)), out))
     return {k: out[i] for i, k in enumerate(PARAM_NAMES)}
 
 
@@ -370,7 +417,8 @@ def egpe_autotune(h: int, inst: int, engine: int, psi, precond: int, reps: int =
     """Tunes the instance's launch shapes from psi; returns one dict per kernel."""
     arr = (egpe_tuning * cap)()
     n = ct.c_int(0)
-    _check("egpe_autotune", load().egpe_autotune(ct.c_void_p(h), inst, engine, ct.c_void_p(_ptr(psi)), precond,
+    _check("egpe_autotune", load().egpe_autotune(ct.c_void_p(h), inst, engine,
+                                                 ct.c_void_p(_field(h, inst, psi, engine=engine)), precond,
                                                  reps, arr, cap, ct.byref(n)))
     return [dict(key=t.key.decode(), name=t.name.decode(), L=t.L, kind=t.kind, choice=t.choice,
                  default_choice=t.default_choice, ms_best=t.ms_best, ms_default=t.ms_default)
@@ -415,7 +463,8 @@ def _report_dict(r) -> dict:
 
 
 def egpe_solver_start(h: int, inst: int, engine: int, psi, opts: egpe_solve_opts):
-    _check("egpe_solver_start", load().egpe_solver_start(ct.c_void_p(h), inst, engine, ct.c_void_p(_ptr(psi)),
+    _check("egpe_solver_start", load().egpe_solver_start(ct.c_void_p(h), inst, engine,
+                                                         ct.c_void_p(_field(h, inst, psi, engine=engine)),
                                                          ct.byref(opts)))
 
 
@@ -426,7 +475,8 @@ def egpe_solver_step(h: int, inst: int, engine: int, attempts: int):
 def egpe_solver_read(h: int, inst: int, engine: int, psi_out=None) -> dict:
     r = egpe_report()
     _check("egpe_solver_read", load().egpe_solver_read(ct.c_void_p(h), inst, engine, ct.byref(r),
-                                                       ct.c_void_p(_ptr(psi_out))))
+                                                       ct.c_void_p(_field(h, inst, psi_out, "psi_out",
+                                                                          engine=engine))))
     return _report_dict(r)
 
 

@@ -122,3 +122,27 @@ def test_noalloc_binding_checks_fields_on_the_host(lib):
         E.egpe_energy_grad_noalloc(g, p, torch.zeros((2, 16, 16, 16), dtype=torch.complex128))
     with pytest.raises(ValueError, match="torch CUDA tensor"):
         E.egpe_energy_grad_noalloc(g, p, 12345)
+
+
+def test_binding_checks_handle_fields_on_the_host():
+    """Tensor arguments of handle calls are checked against the handle's
+    precision and grid before their pointers reach the library (host tensors
+    stand in here for the psi_on_host case; device tensors get the same
+    dtype and size checks)."""
+    torch = pytest.importorskip("torch")
+    h = 0xABC0
+    E._HANDLES[h] = (E.EGPE_FP32, [(16, 16, 16), (32, 16, 16)])
+    try:
+        ok = torch.zeros((2, 16, 16, 16), dtype=torch.complex64)
+        assert E._field(h, 0, ok, on_host=True) == ok.data_ptr()
+        with pytest.raises(ValueError, match="complex64"):
+            E._field(h, 0, ok.to(torch.complex128), on_host=True)
+        with pytest.raises(ValueError, match="elements"):
+            E._field(h, 1, ok, on_host=True)
+        with pytest.raises(ValueError, match="CUDA"):
+            E._field(h, 0, ok)
+        with pytest.raises(ValueError, match="complex128"):
+            E._field(h, 0, ok, on_host=True, engine=0)
+        assert E._field(h, 0, 1234) == 1234  # raw pointers pass unchecked
+    finally:
+        E._HANDLES.pop(h, None)

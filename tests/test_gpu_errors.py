@@ -49,9 +49,12 @@ def _opts(E, **kw):
 def _solve(E, w, psi_np, prec, o):
     h = E.egpe_create([E.make_grid(w.n, w.L)], [E.params_from_workload(w)], prec)
     try:
-        x = torch.from_numpy(psi_np).to("cuda")
-        st, reps, _ = E.egpe_ncg_solve(h, [x], o, 1)
-        return st, reps[0], x
+        x = torch.from_numpy(psi_np).to("cuda").to(torch.complex64 if prec == 1 else torch.complex128)
+        st, reps, tr = E.egpe_ncg_solve(h, [x], o, 1, trace_cap=8)
+        rep = dict(reps[0])
+        rep["trace"] = [{k: t[k] for k in ("n", "kind", "armijo", "flags", "E", "E_trial", "res", "beta", "alpha")}
+                        for t in tr[:4]]
+        return st, rep, x
     finally:
         E.egpe_destroy(h)
 
@@ -70,7 +73,7 @@ def test_nonfinite_start(E, prec):
     # the next solve on a fresh handle is unaffected (a tolerance above the
     # FP32 fields' round-off floor when there is an FP32 phase)
     st, rep, _ = _solve(E, w, psi, prec, _opts(E, tol_res=1e-6 if prec == 0 else 1e-4))
-    assert st == 0 and rep["status"] == 0
+    assert st == 0 and rep["status"] == 0, rep
 
 
 def test_stagnated_when_the_halvings_run_out(E):
@@ -115,5 +118,5 @@ def test_timeout_of_a_device_wait(E, prec):
     finally:
         E.egpe_destroy(h)
     st, rep, _ = _solve(E, w, psi, prec, _opts(E, tol_res=1e-4))
-    assert st == 0 and rep["status"] == 0
+    assert st == 0 and rep["status"] == 0, rep
     assert abs(rep["E"] - E_restored) <= 1e-12 * abs(E_restored)
