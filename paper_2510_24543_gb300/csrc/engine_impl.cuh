@@ -7,7 +7,9 @@
 #include <chrono>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <typeinfo>
+#include <unordered_map>
 #include <vector>
 
 #include "engine.h"
@@ -79,6 +81,27 @@ static bool make_col_map(CUtensorMap& tm, const void* base, int nx, int ny, int 
   return fn(&tm, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Lets a kernel take every byte of dynamic shared memory the device allows.
+// The attribute belongs to the function, process-wide, so it is set once to
+// the maximum rather than per launch shape (engines that launch one kernel
+// with different shapes would otherwise lower it under each other).
+inline cudaError_t allow_max_dynamic_smem(const void* fn) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, cudaError_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(fn);
+  if (it != done.end()) return it->second;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  done[fn] = e;
+  return e;
 }
 
 static inline bool supported_len(int n) {
@@ -325,12 +348,21 @@ template <class R> void Engine<R>::destroy() {
   base_ = nullptr;
 }
 
+// Status of the launch just issued, naming the pass and its shape on failure.
+static inline egpe_status launch_status(const char* name, int L, int block, size_t smem) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return EGPE_OK;
+  set_error_msg(std::string("launch of ") + name + " L=" + std::to_string(L) + " (block " + std::to_string(block) +
+                ", " + std::to_string(smem) + " B shared): " + cudaGetErrorString(e));
+  return EGPE_ERR_CUDA;
+}
+
 template <class R> int Engine<R>::occupancy(const void* fn, int block, size_t smem) {
   const unsigned long long key = ((unsigned long long)(uintptr_t)fn) ^ ((unsigned long long)block << 48) ^
                                  ((unsigned long long)smem << 20);
   auto it = occ_.find(key);
   if (it != occ_.end()) return it->second;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) allow_max_dynamic_smem(fn);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem) != cudaSuccess || occ < 1) occ = 1;
   occ_[key] = occ;
@@ -570,9 +602,8 @@ egpe_status Engine<R>::launch_point(void (*kern)(KArgs<R>), void (*kern_b)(KBatc
 }
 
 template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> a) {
-  constexpr int L = Op::L, TPL = L / 8, NF = Op::NF, NS = Op::NS;
-  constexpr int LP = row_len_padded<R, L>();
-  const size_t rowbytes = (size_t)NF * LP * sizeof(C);
+  constexpr int L = Op::L, TPL = L / 8;
+  const size_t rowbytes = xpass_row_bytes<Op>();
   int mx = std::max(1, 32 / TPL);
   while ((mx * 2) * TPL <= MaxThreads<Op>::v && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
   const int mx_default = mx;
@@ -584,8 +615,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   }
   a.MX = mx;
   const int block = mx * TPL;
-  const size_t smem_fixed =
-      L * sizeof(C) + (Op::USES_LHY ? lhy_stage_bytes<R>(a.Q) : 0) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const size_t smem_fixed = xpass_fixed_bytes<Op>(a.Q);
   const size_t smem = smem_fixed + mx * rowbytes;
   const int rows = ny * nz;
   const int groups = (rows + mx - 1) / mx;
@@ -614,8 +644,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   kern<<<grid, block, smem, stream>>>(a);
   if (timing_) t_end();
   ++kernels_;
-  EGPE_CUDA(cudaGetLastError());
-  return EGPE_OK;
+  return launch_status(Op::NAME, L, block, smem);
 }
 
 template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R> a, const CUtensorMap* tm) {
@@ -665,8 +694,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
     if (timing_) t_end();
   }
   ++kernels_;
-  EGPE_CUDA(cudaGetLastError());
-  return EGPE_OK;
+  return launch_status(Op::NAME, L, block, tma ? smem_tma : smem_plain);
 }
 
 template <class R> template <template <class, int> class OpT, int... Ls>
