@@ -205,8 +205,7 @@ egpe_status egpe_create(const egpe_grid* grids, const egpe_params* params, int n
  * loops that must never enter the CUDA allocator -- and so cannot create a
  * handle (egpe_create allocates the workspaces).  Same kernels and arithmetic
  * as egpe_energy_grad on an EGPE_FP64 handle.  psi: complex128 device field
- * (2,nz,ny,nx), 16-byte aligned, read only; grad: complex128 device output
- * H_i psi_i or NULL;
+ * (2,nz,ny,nx), read only; grad: complex128 device output H_i psi_i or NULL;
  * E, mu: host outputs or NULL; cuda_stream: a cudaStream_t (NULL: the legacy
  * default stream); the call waits for its stream before returning.
  * Limit: 16 or 32 points per axis (at most 32^3 points); larger grids return

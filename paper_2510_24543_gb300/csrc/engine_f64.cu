@@ -74,16 +74,14 @@ cudaError_t noalloc_scratch(int dev, unsigned char** out) {
 
 template <class Op> cudaError_t noalloc_launch_x(egpe::KArgs<double> a, int rows, cudaStream_t s) {
   using namespace egpe;
-  constexpr int L = Op::L, TPL = L / 8;
-  const size_t rowbytes = xpass_row_bytes<Op>();
+  constexpr int L = Op::L, TPL = L / 8, NF = Op::NF, NS = Op::NS;
+  constexpr int LP = row_len_padded<double, L>();
+  const size_t rowbytes = (size_t)NF * LP * sizeof(double2);
   int mx = std::max(1, 32 / TPL);
-  while ((mx * 2) * TPL <= MaxThreads<Op>::v && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
+  while ((mx * 2) * TPL <= 256 && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
   a.MX = mx;
-  const size_t smem = xpass_fixed_bytes<Op>(a.Q) + mx * rowbytes;
-  if (smem > 48 * 1024) {
-    const cudaError_t e = allow_max_dynamic_smem((const void*)xpass_kernel<Op>);
-    if (e != cudaSuccess) return e;
-  }
+  const size_t smem = L * sizeof(double2) + (Op::USES_LHY ? lhy_stage_bytes<double>(a.Q) : 0) +
+                      mx * rowbytes + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const int groups = (rows + mx - 1) / mx;
   const int grid = std::min(groups, (int)kNoAllocBlocks);
   xpass_kernel<Op><<<grid, mx * TPL, smem, s>>>(a);
@@ -132,10 +130,6 @@ extern "C" egpe_status egpe_energy_grad_noalloc(const egpe_grid* grid, const egp
   using namespace egpe;
   if (!grid || !params || !psi) {
     set_error_msg("egpe_energy_grad_noalloc: grid, params and psi are required");
-    return EGPE_ERR_INVALID_ARG;
-  }
-  if (reinterpret_cast<uintptr_t>(psi) % 16 != 0) {  // its rows are fetched by bulk copies
-    set_error_msg("egpe_energy_grad_noalloc: psi must be 16-byte aligned");
     return EGPE_ERR_INVALID_ARG;
   }
   const egpe_grid& g = *grid;

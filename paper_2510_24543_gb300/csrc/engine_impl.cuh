@@ -602,8 +602,9 @@ egpe_status Engine<R>::launch_point(void (*kern)(KArgs<R>), void (*kern_b)(KBatc
 }
 
 template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> a) {
-  constexpr int L = Op::L, TPL = L / 8;
-  const size_t rowbytes = xpass_row_bytes<Op>();
+  constexpr int L = Op::L, TPL = L / 8, NF = Op::NF, NS = Op::NS;
+  constexpr int LP = row_len_padded<R, L>();
+  const size_t rowbytes = (size_t)NF * LP * sizeof(C);
   int mx = std::max(1, 32 / TPL);
   while ((mx * 2) * TPL <= MaxThreads<Op>::v && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
   const int mx_default = mx;
@@ -615,7 +616,8 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   }
   a.MX = mx;
   const int block = mx * TPL;
-  const size_t smem_fixed = xpass_fixed_bytes<Op>(a.Q);
+  const size_t smem_fixed =
+      L * sizeof(C) + (Op::USES_LHY ? lhy_stage_bytes<R>(a.Q) : 0) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const size_t smem = smem_fixed + mx * rowbytes;
   const int rows = ny * nz;
   const int groups = (rows + mx - 1) / mx;

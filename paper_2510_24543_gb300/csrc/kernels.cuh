@@ -132,28 +132,6 @@ template <class Op> struct MinBlocks<Op, std::void_t<decltype(Op::MINB)>> {
   static constexpr int v = Op::MINB;
 };
 
-// Row-pass ops whose epilogue inputs are staged into shared memory by bulk
-// copies (NIN fields at most, rows of the op's row group, issued before the
-// row transform so that their latency overlaps it).
-template <class Op, class = void> struct StagedIn {
-  static constexpr int v = 0;
-};
-template <class Op> struct StagedIn<Op, std::void_t<decltype(Op::NIN)>> {
-  static constexpr int v = Op::NIN;
-};
-
-// Shared memory of a row pass: fixed part plus per row of the block.
-template <class Op> __host__ __device__ constexpr size_t xpass_row_bytes() {
-  using C = C2<typename Op::R>;
-  return (size_t)Op::NF * row_len_padded<typename Op::R, Op::L>() * sizeof(C) +
-         (size_t)StagedIn<Op>::v * Op::L * sizeof(C);
-}
-template <class Op> inline size_t xpass_fixed_bytes(int Q) {
-  using R = typename Op::R;
-  return Op::L * sizeof(C2<R>) + (Op::USES_LHY ? lhy_stage_bytes<R>(Q) : 0) +
-         (Op::NS > 0 ? sizeof(RedSmem<Op::NS>) : 0) + (StagedIn<Op>::v > 0 ? 16 : 0);
-}
-
 // Row-pass ops whose LHY terms come from the interpolation table plus the
 // exactly evaluated nodes (they stage the exact nodes only).
 template <class Op, class = void> struct LhyTabOp {
@@ -181,28 +159,14 @@ template <class Op> __device__ __forceinline__ void xpass_body(const KArgs<typen
   constexpr int NSR = NS > 0 ? NS : 1;
   constexpr int TPL = L / 8;
   constexpr int LP = row_len_padded<R, L>();
-  constexpr int NIN = StagedIn<Op>::v;
   if (!gate_open(a)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ uint64_t in_bar;  // completion of the staged epilogue inputs
   C* tw = reinterpret_cast<C*>(smraw);
   LhyNode<R>* nodes = reinterpret_cast<LhyNode<R>*>(tw + L);
   C* buf = reinterpret_cast<C*>(reinterpret_cast<unsigned char*>(nodes) + (Op::USES_LHY ? lhy_stage_bytes<R>(a.Q) : 0));
-  unsigned char* after = reinterpret_cast<unsigned char*>(buf + NF * a.MX * LP);
-  C* sin = nullptr;  // staged inputs: field f, row m of the group at sin + (f MX + m) L
-  if constexpr (NIN > 0) {
-    sin = reinterpret_cast<C*>((reinterpret_cast<uintptr_t>(after) + 15) & ~(uintptr_t)15);
-    after = reinterpret_cast<unsigned char*>(sin + (size_t)NIN * a.MX * L);
-  }
-  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(after);
+  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(buf + NF * a.MX * LP);
   const int tid = threadIdx.x;
   const int mrow = tid / TPL, t = tid - mrow * TPL;
-  if constexpr (NIN > 0) {
-    if (tid == 0) {
-      mbar_init(&in_bar, 1);
-      fence_barrier_init();
-    }
-  }
   for (int i = tid; i < L; i += blockDim.x) tw[i] = a.twx[i];
   if constexpr (Op::USES_LHY) {
     if constexpr (LhyTabOp<Op>::v) stage_lhy_nodes(nodes, a.xnodes, a.Qx);
@@ -214,36 +178,12 @@ template <class Op> __device__ __forceinline__ void xpass_body(const KArgs<typen
   PAcc<R> acc[NSR];
   const int rows = a.ny * a.nz;
   const int ngroups = (rows + a.MX - 1) / a.MX;
-  bool timed_out = false;
-  int it = 0;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const int row = grp * a.MX + mrow;
     const bool valid = row < rows;
-    if constexpr (NIN > 0) {
-      // the group's rows are contiguous in every field: one bulk copy per field;
-      // the buffer's previous reads ended with the barrier of the last iteration
-      if (tid == 0) {
-        const int row0 = grp * a.MX;
-        const int nv = rows - row0 < a.MX ? rows - row0 : a.MX;
-        const uint32_t bytes = (uint32_t)((size_t)nv * L * sizeof(C));
-        const int nin = Op::nin(a, u);
-        fence_proxy_async();
-        mbar_expect_tx(&in_bar, bytes * (uint32_t)nin);
-        for (int f = 0; f < nin; ++f)
-          bulk_copy_g2s(sin + (size_t)f * a.MX * L, Op::in_field(a, u, f) + (size_t)row0 * L, bytes, &in_bar);
-      }
-    }
     C v[NF][8];
     Op::load(a, u, row, valid, t, v, acc);
     fft_line<C, L, Op::INV, NF>(v, buf + mrow * LP, a.MX * LP, tw, t, RowIdx<PadShift<R>::v>{});
-    if constexpr (NIN > 0) {
-      const bool ok = mbar_wait(&in_bar, (uint32_t)(it & 1), a.wait_polls);
-      if (__syncthreads_or(!ok)) {
-        timed_out = true;
-        break;
-      }
-    }
-    const C* sinr = sin + (size_t)mrow * L;  // this thread's row of the staged inputs
     if constexpr (StageOut<Op>::v) {
       // park the transform outputs in the (idle) exchange buffer: the FFT
       // registers are dead during the epilogue, which frees them for it
@@ -253,30 +193,13 @@ template <class Op> __device__ __forceinline__ void xpass_body(const KArgs<typen
       for (int f = 0; f < NF; ++f)
 #pragma unroll
         for (int e = 0; e < 8; ++e) sm[f * a.MX * LP + si(Plan<L>::exit_pos(Op::INV, t, e))] = v[f][e];
-      if constexpr (NIN > 0) Op::store_staged(a, u, row, valid, t, sm, a.MX * LP, acc, nodes, sinr, a.MX * L);
-      else Op::store_staged(a, u, row, valid, t, sm, a.MX * LP, acc, nodes);
+      Op::store_staged(a, u, row, valid, t, sm, a.MX * LP, acc, nodes);
       // the next row group's exchanges reuse the buffer (a warp's own rows when
       // the length is a power of two, else rows that may straddle warps)
-      if constexpr (IsPow2<L>::v && NIN == 0) __syncwarp();
+      if constexpr (IsPow2<L>::v) __syncwarp();
       else __syncthreads();
     } else {
-      if constexpr (NIN > 0) {
-        Op::store(a, u, row, valid, t, v, acc, nodes, sinr, a.MX * L);
-        __syncthreads();  // every read of the staged inputs precedes the next group's copies
-      } else {
-        Op::store(a, u, row, valid, t, v, acc, nodes);
-      }
-    }
-  }
-  if constexpr (NIN > 0) {
-    if (timed_out) {
-      // the copies already issued land before the block leaves (full budget)
-      mbar_wait(&in_bar, (uint32_t)(it & 1), kTmaWaitPolls);
-      if (tid == 0) {
-        a.st->timeout = 1;
-        a.st->status = 7;  // EGPE_ERR_TIMEOUT
-        a.st->phase = PH_DONE;
-      }
+      Op::store(a, u, row, valid, t, v, acc, nodes);
     }
   }
   if constexpr (NS > 0) {
@@ -782,15 +705,11 @@ template <class R_, int L_> struct XInvEG {
   }
   static constexpr int NP = LhyNP<R>::v;
   static constexpr bool STAGE_OUT = true;
-  static constexpr int NIN = 2;  // staged rows: psi_1, psi_2 of the evaluated slot
-  static __device__ int nin(const KArgs<R>&, const Uni&) { return NIN; }
-  static __device__ const C* in_field(const KArgs<R>& a, const Uni& u, int f) {
-    return a.psi[u.slot] + (f ? (size_t)a.N : 0);
-  }
   static __device__ void store_staged(const KArgs<R>& a, Uni& u, int row, bool valid, int t, const C* sm, int fs,
-                                      PAcc<R>* acc, const LhyNode<R>* nodes, const C* sr, int ifs) {
+                                      PAcc<R>* acc, const LhyNode<R>* nodes) {
     const RowIdx<PadShift<R>::v> si{};
     if (!valid) return;
+    const C* ps = a.psi[u.slot];
     C* hp = a.hp[u.slot];
     C* ax = a.ax[u.slot];
     const size_t N = a.N;
@@ -807,9 +726,9 @@ template <class R_, int L_> struct XInvEG {
       R n1[NP], n2[NP], F[NP], m1[NP], m2[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
-        const int x = Plan<L>::exit_pos(true, t, e0 + j);
-        p1[j] = sr[x];
-        p2[j] = sr[ifs + x];
+        const size_t idx = (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e0 + j);
+        p1[j] = ps[idx];
+        p2[j] = ps[N + idx];
         n1[j] = cabs2(p1[j]);
         n2[j] = cabs2(p2[j]);
       }
@@ -1061,17 +980,8 @@ template <class R_, int L_> struct XInvPC {
       v[1][e] = valid ? a.W[(size_t)a.N + idx] : cmk<C>(0, 0);
     }
   }
-  // staged rows: r_1, r_2, r_prev_1, r_prev_2, p_prev_1, p_prev_2, psi_1, psi_2, and
-  // (muL_1, muL_2) for the blended preconditioner
-  static constexpr int NIN = 9;
-  static __device__ int nin(const KArgs<R>& a, const Uni&) { return a.blend ? 9 : 8; }
-  static __device__ const C* in_field(const KArgs<R>& a, const Uni& u, int f) {
-    const C* b = f < 2 ? a.rb[u.nsel] : f < 4 ? a.rb[u.nsel ^ 1] : f < 6 ? a.pb[u.nsel ^ 1] : f < 8 ? a.psi[u.cur]
-                                                                                             : a.ax[u.cur];
-    return b + ((f & 1) || f == 8 ? (size_t)a.N : 0);
-  }
   static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[2][8], PAcc<R>* acc,
-                               const LhyNode<R>*, const C* sr, int fs) {
+                               const LhyNode<R>*) {
     if (!valid) return;
     const int yy = row % a.ny, zz = row / a.ny;
     const R Yc = -a.Ly + (R)yy * a.hy, Zc = -a.Lz + (R)zz * a.hz;
@@ -1084,17 +994,7 @@ template <class R_, int L_> struct XInvPC {
     for (int e0 = 0; e0 < 8; e0 += CH) {
       PcSumIn<R> in[CH];
 #pragma unroll
-      for (int j = 0; j < CH; ++j) {
-        const int x = Plan<L>::exit_pos(true, t, e0 + j);
-        in[j].r1 = sr[x];
-        in[j].r2 = sr[fs + x];
-        in[j].q1 = sr[2 * fs + x];
-        in[j].q2 = sr[3 * fs + x];
-        in[j].d1 = sr[4 * fs + x];
-        in[j].d2 = sr[5 * fs + x];
-        in[j].p1 = sr[6 * fs + x];
-        in[j].p2 = sr[7 * fs + x];
-      }
+      for (int j = 0; j < CH; ++j) pc_sum_load<R>(a, u, (size_t)row * a.nx + Plan<L>::exit_pos(true, t, e0 + j), in[j]);
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
         const int e = e0 + j;
@@ -1102,7 +1002,7 @@ template <class R_, int L_> struct XInvPC {
         const size_t idx = (size_t)row * a.nx + x;
         C z1 = v[0][e], z2 = v[1][e];
         if (a.blend) {  // z = (1 - w) P_Delta^{-1} r + w P_V^{-1} r
-          const C ml = sr[8 * fs + x];
+          const C ml = a.ax[u.cur][(size_t)a.N + idx];
           const R X = -a.Lx + (R)x * a.hx;
           const R V = a.vx * X * X + vyz;
           const R n1 = cabs2(in[j].p1), n2 = cabs2(in[j].p2);
@@ -1327,16 +1227,14 @@ template <class R_, int L_> struct XInvLC {
       v[0][e] = valid ? a.W[(size_t)2 * a.N + (size_t)row * a.nx + Plan<L>::entry_pos(true, t, e)] : cmk<C>(0, 0);
   }
   static constexpr int NP = LhyNP<R>::v;
-  // staged rows: psi_1, psi_2, p_1, p_2, H psi_1, H psi_2, (Phi_1, Phi_2), (muL_1, muL_2)
-  static constexpr int NIN = 8;
-  static __device__ int nin(const KArgs<R>&, const Uni&) { return NIN; }
-  static __device__ const C* in_field(const KArgs<R>& a, const Uni& u, int f) {
-    const C* b = f < 2 ? a.psi[u.cur] : f < 4 ? a.pb[u.nsel] : f < 6 ? a.hp[u.cur] : a.ax[u.cur];
-    return b + (f & 1 ? (size_t)a.N : 0);
-  }
   static __device__ void store(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[1][8], PAcc<R>* acc,
-                               const LhyNode<R>* nodes, const C* sr, int fs) {
+                               const LhyNode<R>* nodes) {
     if (!valid) return;
+    const size_t N = a.N;
+    const C* ps = a.psi[u.cur];
+    const C* pd = a.pb[u.nsel];
+    const C* hp = a.hp[u.cur];
+    const C* ax = a.ax[u.cur];
     const int y = row % a.ny, z = row / a.ny;
     const R Y = -a.Ly + (R)y * a.hy, Z = -a.Lz + (R)z * a.hz;
     const R vyz = a.vy * Y * Y + a.vz * Z * Z;
@@ -1351,10 +1249,11 @@ template <class R_, int L_> struct XInvLC {
       for (int j = 0; j < NP; ++j) {
         const int e = e0 + j;
         const int x = Plan<L>::exit_pos(true, t, e);
-        const C p1 = sr[x], p2 = sr[fs + x];
-        const C q1 = sr[2 * fs + x], q2 = sr[3 * fs + x];
-        const C h1 = sr[4 * fs + x], h2 = sr[5 * fs + x];
-        const C phi = sr[6 * fs + x], ml = sr[7 * fs + x];
+        const size_t idx = (size_t)row * a.nx + x;
+        const C p1 = ps[idx], p2 = ps[N + idx];
+        const C q1 = pd[idx], q2 = pd[N + idx];
+        const C h1 = hp[idx], h2 = hp[N + idx];
+        const C phi = ax[idx], ml = ax[N + idx];
         n1[j] = cabs2(p1);
         n2[j] = cabs2(p2);
         const R a1 = cabs2(q1), a2 = cabs2(q2);
