@@ -8,6 +8,11 @@
 // of one attempt for all live instances, gathers the instances' phases in one
 // small copy per poll, and rebuilds the graph whenever instances finish, so
 // finished instances drop out of the launches instead of occupying them.
+// The launch chains of different groups are independent: with `concurrent`
+// they are captured as parallel branches of the graph (one forked stream per
+// group), each launch sized by its group's share of the live grid points, so
+// the groups of uneven grids fill the GPU together; otherwise one after the
+// other, each launch filling one wave by itself.
 // Included by engine_f64.cu and engine_f32.cu only.
 #pragma once
 #include <map>
@@ -25,7 +30,8 @@ template <class R> __global__ void phase_gather_kernel(DevState* const* sts, int
 
 template <class R> class BatchRunner {
  public:
-  BatchRunner(const std::vector<Engine<R>*>& eng, cudaStream_t s) : eng_(eng), stream_(s) {}
+  BatchRunner(const std::vector<Engine<R>*>& eng, cudaStream_t s, bool concurrent)
+      : eng_(eng), stream_(s), concurrent_(concurrent) {}
   ~BatchRunner() { release(); }
 
   // Solves every instance from the state in its psi slot 0; options as in
@@ -71,6 +77,9 @@ template <class R> class BatchRunner {
  private:
   std::vector<Engine<R>*> eng_;
   cudaStream_t stream_ = nullptr;
+  bool concurrent_ = false;
+  std::vector<cudaStream_t> branch_;  // forked capture streams, one per group (concurrent mode)
+  std::vector<cudaEvent_t> join_;     // [0]: fork point, [1 + g]: end of group g's chain
   cudaGraphExec_t graph_ = nullptr;
   std::vector<int> built_;
   long long per_replay_ = 0;
@@ -82,6 +91,10 @@ template <class R> class BatchRunner {
   void release() {
     if (graph_) cudaGraphExecDestroy(graph_);
     graph_ = nullptr;
+    for (cudaStream_t b : branch_) cudaStreamDestroy(b);
+    for (cudaEvent_t e : join_) cudaEventDestroy(e);
+    branch_.clear();
+    join_.clear();
     if (d_sts_) cudaFree(d_sts_);
     if (d_phase_) cudaFree(d_phase_);
     if (h_phase_) cudaFreeHost(h_phase_);
@@ -131,8 +144,12 @@ template <class R> class BatchRunner {
       int block;
       size_t smem;
       std::unique_ptr<KBatch<R>> kb;
+      int branch;
     };
     std::vector<Launch> launches;
+    double live_points = 0.0;
+    for (int i : active) live_points += (double)eng_[i]->N;
+    int branch = 0;
     std::vector<std::vector<LaunchRec<R>>> recs;
     std::vector<std::vector<KArgs<R>>> args;
     for (auto& g : groups) {
@@ -165,14 +182,34 @@ template <class R> class BatchRunner {
             L.kb->k[c] = args[c][rc.arg];
             if (rc.tm) L.kb->tm[c] = *rc.tm;
           }
-          // one full wave over all instances of the chunk: a rounded-up share
-          // would spill a few blocks into a second wave
+          // sequential chunks: one full wave over the chunk's instances (a
+          // rounded-up share would spill a few blocks into a second wave);
+          // concurrent chunks: the wave shared in proportion to grid points
           const int occ = e0.occupancy(r0.fn, r0.block, r0.smem);
-          const long long fill = ((long long)occ * e0.nsm_) / nc;
+          const long long wave = (long long)occ * e0.nsm_;
+          const long long fill = concurrent_ ? (long long)(wave * ((double)e0.N / live_points)) : wave / nc;
           const long long gx = std::max<long long>(1, std::min<long long>(r0.units, std::min<long long>(fill, 16384)));
           L.grid = dim3((unsigned)gx, (unsigned)nc, 1);
+          L.branch = branch;
           launches.push_back(std::move(L));
         }
+        ++branch;
+      }
+    }
+    if (concurrent_) {
+      // capture streams and events for every branch (kept across rebuilds)
+      if (join_.empty()) {
+        cudaEvent_t e;
+        EGPE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        join_.push_back(e);
+      }
+      while ((int)branch_.size() < branch) {
+        cudaStream_t b;
+        cudaEvent_t e;
+        EGPE_CUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+        branch_.push_back(b);
+        EGPE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        join_.push_back(e);
       }
     }
     if (graph_) cudaGraphExecDestroy(graph_);
@@ -180,10 +217,22 @@ template <class R> class BatchRunner {
     cudaGraph_t g = nullptr;
     EGPE_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
+    if (concurrent_) {
+      // fork: every branch stream waits on the capture origin, then joins back
+      le = cudaEventRecord(join_[0], stream_);
+      for (int b = 0; b < branch && le == cudaSuccess; ++b) le = cudaStreamWaitEvent(branch_[b], join_[0], 0);
+    }
     for (Launch& L : launches) {
-      void* params[1] = {(void*)L.kb.get()};
-      le = cudaLaunchKernel(L.fn, L.grid, dim3((unsigned)L.block), params, L.smem, stream_);
       if (le != cudaSuccess) break;
+      void* params[1] = {(void*)L.kb.get()};
+      cudaStream_t s = concurrent_ ? branch_[L.branch] : stream_;
+      le = cudaLaunchKernel(L.fn, L.grid, dim3((unsigned)L.block), params, L.smem, s);
+    }
+    if (concurrent_) {
+      for (int b = 0; b < branch && le == cudaSuccess; ++b) {
+        le = cudaEventRecord(join_[1 + b], branch_[b]);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(stream_, join_[1 + b], 0);
+      }
     }
     cudaError_t ce = cudaStreamEndCapture(stream_, &g);
     if (le != cudaSuccess || ce != cudaSuccess) {
@@ -209,7 +258,7 @@ template <class R>
 egpe_status batch_solve(const std::vector<Engine<R>*>& eng, cudaStream_t s, const egpe_solve_opts& o, int fp32_phase,
                         int max_iter, double tol_res, double accept_rtol, std::vector<SolveRun>& runs,
                         egpe_trace_entry* trace_out, int trace_cap, int* graph_builds) {
-  BatchRunner<R> br(eng, s);
+  BatchRunner<R> br(eng, s, o.batch >= 2);
   const egpe_status st = br.solve(o, fp32_phase, max_iter, tol_res, accept_rtol, runs, trace_out, trace_cap);
   if (graph_builds) *graph_builds = br.graph_builds();
   return st;

@@ -57,12 +57,14 @@ def _solve(E, ws, prec, batch, tol=1e-9, trace_cap=0, max_iter=3000, **kw):
         E.egpe_destroy(h)
 
 
-def test_batched_equals_one_by_one(E):
-    """Eight instances on 48^3, 64^3, 80^3 and 96^3: batched and sequential
-    solves reach the same energies and states (they differ only in how the
-    per-block partial sums are grouped)."""
+@pytest.mark.parametrize("batch", [1, 2])
+def test_batched_equals_one_by_one(E, batch):
+    """Eight instances on 48^3, 64^3, 80^3 and 96^3: batched solves (the grid
+    shapes' launches in sequence, batch 1, or as concurrent graph branches,
+    batch 2) and one-by-one solves reach the same energies and states (they
+    differ only in how the per-block partial sums are grouped)."""
     ws = _scan_subset()
-    st_b, rb, _, psi_b = _solve(E, ws, E.EGPE_FP64, 1)
+    st_b, rb, _, psi_b = _solve(E, ws, E.EGPE_FP64, batch)
     st_s, rs, _, psi_s = _solve(E, ws, E.EGPE_FP64, 0)
     assert st_b == 0 and st_s == 0
     for i in range(len(ws)):
@@ -81,7 +83,7 @@ def test_batched_lockstep_with_oracle(E):
     g, prm = oracle_case(w)
     otr = []
     O.ncg_solve(g, prm, I.gaussian_start(w), O.SolveOpts(precond="kinetic", tol_res=1e-8, max_iter=6), trace=otr)
-    st, reps, tr, _ = _solve(E, ws, E.EGPE_FP64, 1, max_iter=6, trace_cap=64)
+    st, reps, tr, _ = _solve(E, ws, E.EGPE_FP64, 2, max_iter=6, trace_cap=64)
     acc = [t for t in tr if t["flags"] & 1]
     oacc = [t for t in otr if t["accepted"]]
     assert len(acc) == len(oacc) == 6
@@ -97,7 +99,7 @@ def test_batched_mixed_scan_against_oracle(E):
     subset: converged, and the oracle's evaluation of two returned states
     (48^3 and 96^3) gives the reported energy and a residual below 1e-8."""
     ws = _scan_subset()
-    st, reps, _, psis = _solve(E, ws, E.EGPE_MIXED, 1, tol_fp32_switch=1e-4)
+    st, reps, _, psis = _solve(E, ws, E.EGPE_MIXED, 2, tol_fp32_switch=1e-4)
     assert st == 0
     for r in reps:
         assert r["status"] == 0 and r["iters_fp32"] > 0 and r["res"] < 1e-9
