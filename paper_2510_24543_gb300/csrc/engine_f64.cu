@@ -77,8 +77,8 @@ template <class Op> cudaError_t noalloc_launch_x(egpe::KArgs<double> a, int rows
   constexpr int L = Op::L, TPL = L / 8, NF = Op::NF, NS = Op::NS;
   constexpr int LP = row_len_padded<double, L>();
   const size_t rowbytes = (size_t)NF * LP * sizeof(double2);
-  int mx = std::max(1, 32 / TPL);
-  while ((mx * 2) * TPL <= 256 && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
+  int mx = whole_warp_rows(L);
+  while ((mx * 2) * TPL <= MaxThreads<Op>::v && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
   a.MX = mx;
   const size_t smem = L * sizeof(double2) + (Op::USES_LHY ? lhy_stage_bytes<double>(a.Q) : 0) +
                       mx * rowbytes + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
@@ -91,7 +91,7 @@ template <class Op> cudaError_t noalloc_launch_x(egpe::KArgs<double> a, int rows
 template <class Op> cudaError_t noalloc_launch_col(egpe::KArgs<double> a, int other, cudaStream_t s) {
   using namespace egpe;
   constexpr int L = Op::L, TPL = L / 8, NS = Op::NS;
-  int M = std::max((int)(128 / sizeof(double2)), 32 / TPL);
+  int M = std::max((int)(128 / sizeof(double2)), whole_warp_rows(L));
   M = std::min(M, a.nx);
   a.M = M;
   const size_t smem = L * sizeof(double2) + (size_t)M * L * sizeof(double2) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);

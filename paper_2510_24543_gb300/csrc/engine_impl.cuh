@@ -60,8 +60,8 @@ template <class C> static inline int col_tile_width(int L, int nx) {
   const int TPL = L / 8;
   const bool pow2 = (L & (L - 1)) == 0;
   int M = pow2 ? std::min((int)(EGPE_COL_BYTES / sizeof(C)), 512 / TPL) : (int)(128 / sizeof(C));
-  M = std::min(std::max(M, 32 / TPL), nx);
-  while (M > 1 && nx % M != 0) M /= 2;  // whole tiles across x
+  M = std::min(std::max(M, whole_warp_rows(L)), nx);
+  while (M > whole_warp_rows(L) && nx % M != 0) M /= 2;  // whole tiles across x
   return M;
 }
 
@@ -349,6 +349,14 @@ template <class R> void Engine<R>::destroy() {
 }
 
 // Status of the launch just issued, naming the pass and its shape on failure.
+// Passes run whole warps (full-mask shuffles); the geometry rules guarantee it.
+static inline egpe_status check_whole_warps(const char* name, int L, int block) {
+  if (block % 32 == 0) return EGPE_OK;
+  set_error_msg(std::string(name) + " L=" + std::to_string(L) + ": block of " + std::to_string(block) +
+                " threads is not whole warps");
+  return EGPE_ERR_UNSUPPORTED;
+}
+
 static inline egpe_status launch_status(const char* name, int L, int block, size_t smem) {
   const cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) return EGPE_OK;
@@ -508,7 +516,7 @@ egpe_status Engine<R>::autotune(const C* psi, int precond, int reps, std::vector
     std::vector<int> cand;
     if (r.kind == 0) {
       for (int mx = r.mx; mx >= 1; mx /= 2)
-        if (mx * r.tpl >= 32 || mx == r.mx) cand.push_back(mx);
+        if ((mx * r.tpl) % 32 == 0) cand.push_back(mx);  // whole warps only
       const int up = r.mx * 2;
       if (up * r.tpl <= r.max_threads && (size_t)up * r.rowbytes + r.smem_fixed <= 200 * 1024) cand.push_back(up);
     } else {
@@ -605,17 +613,18 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
   constexpr int L = Op::L, TPL = L / 8, NF = Op::NF, NS = Op::NS;
   constexpr int LP = row_len_padded<R, L>();
   const size_t rowbytes = (size_t)NF * LP * sizeof(C);
-  int mx = std::max(1, 32 / TPL);
+  int mx = whole_warp_rows(L);
   while ((mx * 2) * TPL <= MaxThreads<Op>::v && (size_t)(mx * 2) * rowbytes <= 46 * 1024) mx *= 2;
   const int mx_default = mx;
   if (!tune_.empty()) {
     auto it = tune_.find(typeid(Op).name());
     if (it != tune_.end() && it->second >= 1 && it->second * TPL <= MaxThreads<Op>::v &&
-        (size_t)it->second * rowbytes <= 200 * 1024)
+        (it->second * TPL) % 32 == 0 && (size_t)it->second * rowbytes <= 200 * 1024)
       mx = it->second;
   }
   a.MX = mx;
   const int block = mx * TPL;
+  EGPE_TRY(check_whole_warps(Op::NAME, L, block));
   const size_t smem_fixed =
       L * sizeof(C) + (Op::USES_LHY ? lhy_stage_bytes<R>(a.Q) : 0) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const size_t smem = smem_fixed + mx * rowbytes;
@@ -654,6 +663,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   const int M = col_tile_width<C>(L, nx);
   a.M = M;
   const int block = M * TPL;
+  EGPE_TRY(check_whole_warps(Op::NAME, L, block));
   const int other = (Op::AXIS == 1) ? nz : ny;
   const int tiles = (nx / M) * other * a.nf;
   const size_t smem_tma = (size_t)kColStages * M * L * sizeof(C) + L * sizeof(C) + kColStages * sizeof(uint64_t) +

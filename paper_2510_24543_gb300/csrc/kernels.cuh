@@ -141,12 +141,25 @@ template <class Op> struct LhyTabOp<Op, std::void_t<decltype(Op::LHY_TAB)>> {
   static constexpr bool v = Op::LHY_TAB;
 };
 
-// Threads per block of a row pass: 256 unless the op asks for fewer.
-template <class Op, class = void> struct MaxThreads {
+// Every pass runs whole warps: the block reductions and the warp exchanges use
+// full-mask shuffles.  A row (x) pass gives each row L/8 threads and a column
+// pass each column L/8 threads, so a block holds a multiple of
+// whole_warp_rows(L) rows or columns.
+__host__ __device__ constexpr int gcd_i(int a, int b) { return b == 0 ? a : gcd_i(b, a % b); }
+__host__ __device__ constexpr int whole_warp_rows(int L) { return 32 / gcd_i(L / 8, 32); }
+
+// Threads per block of a row pass: 256 unless the op asks for fewer, rounded
+// down to whole warps of whole rows (at least one such group).
+template <class Op, class = void> struct MaxThreadsWant {
   static constexpr int v = 256;
 };
-template <class Op> struct MaxThreads<Op, std::void_t<decltype(Op::MAXT)>> {
+template <class Op> struct MaxThreadsWant<Op, std::void_t<decltype(Op::MAXT)>> {
   static constexpr int v = Op::MAXT;
+};
+template <class Op> struct MaxThreads {
+  static constexpr int G = whole_warp_rows(Op::L) * (Op::L / 8);
+  static constexpr int W = MaxThreadsWant<Op>::v;
+  static constexpr int v = W >= G ? W - W % G : G;
 };
 
 // ----------------------------------------------------------------------------
@@ -203,10 +216,7 @@ template <class Op> __device__ __forceinline__ void xpass_body(const KArgs<typen
     }
   }
   if constexpr (NS > 0) {
-    double dacc[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) dacc[s] = acc[s].get();
-    if (reduce_blocks<NS>(dacc, a.partials, a.counter, Op::out(a, u), *red)) {
+    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
       if (threadIdx.x == 0) Op::finish(a, u);
     }
   }
@@ -252,7 +262,8 @@ static_assert(EGPE_COL_MINB == 1 || EGPE_COL_BYTES == 128, "exact column bounds 
 template <class Op> struct ColMaxThreads {
   static constexpr int TPL = Op::L / 8;
   static constexpr int MC = (int)(128 / sizeof(C2<typename Op::R>));
-  static constexpr int exact = (MC > 32 / TPL ? MC : 32 / TPL) * TPL;
+  static constexpr int MW = whole_warp_rows(Op::L);
+  static constexpr int exact = (MC > MW ? MC : MW) * TPL;
   static constexpr int v = (IsPow2<Op::L>::v && EGPE_COL_MINB == 1) ? 512 : exact;
   // resident blocks per SM the compiler is asked to allow for (caps registers)
   static constexpr int minb = (EGPE_COL_MINB > 1 && exact <= 256) ? EGPE_COL_MINB : 1;
@@ -297,10 +308,7 @@ template <class Op> __device__ __forceinline__ void colpass_body(const KArgs<typ
     Op::process(a, u, f, x, o, base, lstride, t, v, buf + m, tw, ColIdx{a.M}, acc);
   }
   if constexpr (NS > 0) {
-    double dacc[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) dacc[s] = acc[s].get();
-    if (reduce_blocks<NS>(dacc, a.partials, a.counter, Op::out(a, u), *red)) {
+    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
       if (threadIdx.x == 0) Op::finish(a, u);
     }
   }
@@ -415,10 +423,7 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     }
   }
   if constexpr (NS > 0) {
-    double dacc[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) dacc[s] = acc[s].get();
-    if (reduce_blocks<NS>(dacc, a.partials, a.counter, Op::out(a, u), *red)) {
+    if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
       if (threadIdx.x == 0) Op::finish(a, u);
     }
   }
@@ -522,10 +527,12 @@ template <class R_, int L_> struct XFwdEG {
     u.cur = __ldcg(&a.st->cur);
     u.slot = a.flag ? (u.cur ^ 1) : u.cur;
     u.nsel = __ldcg(&a.st->n) & 1;
-    for (int i = 0; i < 2; ++i) {
-      u.ca[i] = (R)__ldcg(&a.st->coef_a[i]);
-      u.cb[i] = (R)__ldcg(&a.st->coef_b[i]);
-    }
+    R c[4];
+    load_uniforms<R, 4>({&a.st->coef_a[0], &a.st->coef_a[1], &a.st->coef_b[0], &a.st->coef_b[1]}, c);
+    u.ca[0] = c[0];
+    u.ca[1] = c[1];
+    u.cb[0] = c[2];
+    u.cb[1] = c[3];
   }
   static __device__ void load(const KArgs<R>& a, Uni& u, int row, bool valid, int t, C (&v)[3][8], PAcc<R>*) {
     const C* src = a.psi[u.cur];
@@ -785,13 +792,24 @@ template <class R> __device__ __forceinline__ void pc_uniform(const KArgs<R>& a,
   u.cur = __ldcg(&a.st->cur);
   u.nsel = __ldcg(&a.st->n) & 1;
   u.rgiven = a.flag;
-  u.wv = (R)__ldcg(&a.st->opt.pc_blend);
-  const double fl = __ldcg(&a.st->opt.pv_floor);
-  for (int i = 0; i < 2; ++i) {
-    u.mu[i] = (R)__ldcg(&a.st->mu[i]);
-    const double sh = __ldcg(&a.st->shift[i]);
-    u.shift[i] = (R)sh;
-    u.floor_[i] = (R)(fl * sh);
+  if constexpr (sizeof(R) == sizeof(double)) {
+    u.wv = __ldcg(&a.st->opt.pc_blend);
+    const double fl = __ldcg(&a.st->opt.pv_floor);
+    for (int i = 0; i < 2; ++i) {
+      u.mu[i] = __ldcg(&a.st->mu[i]);
+      u.shift[i] = __ldcg(&a.st->shift[i]);
+      u.floor_[i] = fl * u.shift[i];
+    }
+  } else {
+    R c[6];
+    load_uniforms<R, 6>(
+        {&a.st->opt.pc_blend, &a.st->opt.pv_floor, &a.st->mu[0], &a.st->mu[1], &a.st->shift[0], &a.st->shift[1]}, c);
+    u.wv = c[0];
+    for (int i = 0; i < 2; ++i) {
+      u.mu[i] = c[2 + i];
+      u.shift[i] = c[4 + i];
+      u.floor_[i] = c[1] * c[4 + i];
+    }
   }
 }
 
@@ -938,8 +956,7 @@ template <class R_, int L_> struct ZPc {
     R shift[2];
   };
   static __device__ void uniform(const KArgs<R>& a, Uni& u) {
-    u.shift[0] = (R)__ldcg(&a.st->shift[0]);
-    u.shift[1] = (R)__ldcg(&a.st->shift[1]);
+    load_uniforms<R, 2>({&a.st->shift[0], &a.st->shift[1]}, u.shift);
   }
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
@@ -1063,10 +1080,7 @@ __device__ __forceinline__ void pc_point_body(const KArgs<R>& a) {
 #pragma unroll
     for (int k = 0; k < PC_NS; ++k) acc[k].add(s[k]);
   }
-  double dacc[PC_NS];
-#pragma unroll
-  for (int k = 0; k < PC_NS; ++k) dacc[k] = acc[k].get();
-  if (reduce_blocks<PC_NS>(dacc, a.partials, a.counter, a.st->pc, red)) {
+  if (reduce_blocks<PC_NS>(acc, a.partials, a.counter, a.st->pc, red)) {
     if (threadIdx.x == 0 && a.ctrl) ctrl_after_pc(a.st);
   }
 }
@@ -1090,9 +1104,11 @@ template <class R> __device__ __forceinline__ void lc_uniform(const KArgs<R>& a,
   u.nsel = __ldcg(&a.st->n) & 1;
   u.pgiven = a.flag;
   u.fallback = __ldcg(&a.st->fallback);
-  u.beta = (R)__ldcg(&a.st->beta);
-  u.c[0] = (R)__ldcg(&a.st->c[0]);
-  u.c[1] = (R)__ldcg(&a.st->c[1]);
+  R c[3];
+  load_uniforms<R, 3>({&a.st->beta, &a.st->c[0], &a.st->c[1]}, c);
+  u.beta = c[0];
+  u.c[0] = c[1];
+  u.c[1] = c[2];
 }
 
 template <class R_, int L_> struct XFwdLC {
@@ -1440,8 +1456,16 @@ template <class R> __device__ __forceinline__ void ite_scale_body(const KArgs<R>
   if (!gate_open(a)) return;
   const int cur = __ldcg(&a.st->cur);
   const double dV = __ldcg(&a.st->dV);
-  const R s1 = (R)(1.0 / sqrt(__ldcg(&a.st->rt[0]) * dV));
-  const R s2 = (R)(1.0 / sqrt(__ldcg(&a.st->rt[1]) * dV));
+  R s1, s2;
+  if constexpr (sizeof(R) == sizeof(double)) {
+    s1 = 1.0 / sqrt(__ldcg(&a.st->rt[0]) * dV);
+    s2 = 1.0 / sqrt(__ldcg(&a.st->rt[1]) * dV);
+  } else {  // FP32 fields: lane i forms ||psi_i||^2 in FP64, one conversion per warp
+    const float q = (float)(__ldcg(&a.st->rt[threadIdx.x & 1]) * dV);
+    const float sc = rsqrtf(q);
+    s1 = __shfl_sync(0xffffffffu, sc, 0);
+    s2 = __shfl_sync(0xffffffffu, sc, 1);
+  }
   C2<R>* ps = a.psi[cur];
   const size_t N = a.N;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
@@ -1586,16 +1610,14 @@ template <class R_, int L_> struct XInvPG {
 // sums over (psi = gin, p = gout-as-input) for the standalone retraction
 template <class R> __global__ void __launch_bounds__(256) rt_sums_kernel(KArgs<R> a, const C2<R>* psi, const C2<R>* p) {
   __shared__ RedSmem<RT_NS> red;
-  double acc[RT_NS];
-#pragma unroll
-  for (int k = 0; k < RT_NS; ++k) acc[k] = 0.0;
+  PAcc<R> acc[RT_NS];
   const size_t N = a.N;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
     for (int i = 0; i < 2; ++i) {
       const C2<R> u = psi[i * N + idx], q = p[i * N + idx];
-      acc[RT_P1 + i] += (double)cabs2(q);
-      acc[RT_PSIP1 + i] += (double)cdot(u, q);
-      acc[RT_PSI1 + i] += (double)cabs2(u);
+      acc[RT_P1 + i].add(cabs2(q));
+      acc[RT_PSIP1 + i].add(cdot(u, q));
+      acc[RT_PSI1 + i].add(cabs2(u));
     }
   }
   reduce_blocks<RT_NS>(acc, a.partials, a.counter, a.st->rt, red);
@@ -1614,9 +1636,10 @@ __global__ void __launch_bounds__(256) rt_apply_kernel(size_t N, const C2<R>* ps
 // ||r_i||^2 of the current point (final report of a solve).
 template <class R> __global__ void __launch_bounds__(256) resnorm_kernel(KArgs<R> a) {
   __shared__ RedSmem<2> red;
-  double acc[2] = {0.0, 0.0};
+  PAcc<R> acc[2];
   const int cur = __ldcg(&a.st->cur);
-  const R mu[2] = {(R)__ldcg(&a.st->mu[0]), (R)__ldcg(&a.st->mu[1])};
+  R mu[2];
+  load_uniforms<R, 2>({&a.st->mu[0], &a.st->mu[1]}, mu);
   const size_t N = a.N;
   const C2<R>* ps = a.psi[cur];
   const C2<R>* hp = a.hp[cur];
@@ -1624,7 +1647,7 @@ template <class R> __global__ void __launch_bounds__(256) resnorm_kernel(KArgs<R
     for (int i = 0; i < 2; ++i) {
       const C2<R> u = ps[i * N + idx], h = hp[i * N + idx];
       const C2<R> r = cmk<C2<R>>(h.x - mu[i] * u.x, h.y - mu[i] * u.y);
-      acc[i] += (double)cabs2(r);
+      acc[i].add(cabs2(r));
     }
   }
   reduce_blocks<2>(acc, a.partials, a.counter, a.st->pca, red);
