@@ -20,11 +20,19 @@
 #include "reduce.cuh"
 #include "tma.cuh"
 
+// Resident blocks per SM asked of the FP32 x-inverse epilogue passes, which
+// caps their registers: energy 4 x 128 threads (128 registers, no spills),
+// line coefficients 2 x 256 (128 registers, a few spilled bytes),
+// preconditioner 1 (at 128 registers it spills ~250 bytes).  At 128^3 the
+// energy pass went from 55.5 to 49.5 us and the line pass from 59 to 57 us.
 #ifndef EGPE_EG_MINB
-#define EGPE_EG_MINB 1
+#define EGPE_EG_MINB 4
 #endif
 #ifndef EGPE_LC_MINB
-#define EGPE_LC_MINB 1
+#define EGPE_LC_MINB 2
+#endif
+#ifndef EGPE_PC_MINB
+#define EGPE_PC_MINB 1
 #endif
 
 namespace egpe {
@@ -983,6 +991,7 @@ template <class R_, int L_> struct XInvPC {
   using R = R_;
   using C = C2<R>;
   static constexpr int MAXT = 128;  // heavy epilogue: smaller blocks, more of them per SM
+  static constexpr int MINB = sizeof(R_) == 4 ? EGPE_PC_MINB : 1;
   static constexpr const char* NAME = "x-inv precond sums";
   static double alg_bytes(const KArgs<R>& a) { return 12.0 * a.N * sizeof(C); }
   static constexpr int L = L_, NF = 2, NS = PC_NS;
