@@ -94,7 +94,7 @@ template <class Op> cudaError_t noalloc_launch_col(egpe::KArgs<double> a, int ot
   int M = std::max((int)(128 / sizeof(double2)), whole_warp_rows(L));
   M = std::min(M, a.nx);
   a.M = M;
-  const size_t smem = L * sizeof(double2) + (size_t)M * L * sizeof(double2) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const size_t smem = L * sizeof(double2) + 2 * (size_t)M * L * sizeof(double2) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   const int tiles = (a.nx / M) * other * a.nf;
   const int grid = std::min(tiles, (int)kNoAllocBlocks);
   colpass_kernel<Op><<<grid, M * TPL, smem, s>>>(a);

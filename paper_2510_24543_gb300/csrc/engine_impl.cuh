@@ -666,9 +666,9 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   EGPE_TRY(check_whole_warps(Op::NAME, L, block));
   const int other = (Op::AXIS == 1) ? nz : ny;
   const int tiles = (nx / M) * other * a.nf;
-  const size_t smem_tma = (size_t)kColStages * M * L * sizeof(C) + L * sizeof(C) + kColStages * sizeof(uint64_t) +
-                          (NS > 0 ? sizeof(RedSmem<NS>) : 0);
-  const size_t smem_plain = L * sizeof(C) + (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const size_t smem_tma = (size_t)(kColStages + 1) * M * L * sizeof(C) + L * sizeof(C) +
+                          kColStages * sizeof(uint64_t) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
+  const size_t smem_plain = L * sizeof(C) + 2 * (size_t)M * L * sizeof(C) + (NS > 0 ? sizeof(RedSmem<NS>) : 0);
   bool tma = tm && use_tma_;
   if (tma && !tune_.empty()) {
     auto it = tune_.find(typeid(Op).name());

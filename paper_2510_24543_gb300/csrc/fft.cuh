@@ -81,6 +81,14 @@ template <class SI> __device__ __forceinline__ void line_sync() {
   if constexpr (std::is_same<SI, ColIdx>::value) __syncthreads();
   else __syncwarp();
 }
+// Column lines (power-of-two lengths) exchange through two buffers in turn,
+// so one block barrier per exchange suffices: a buffer is written again only
+// after the barrier of the exchange that used the other one, which every
+// thread reaches after its reads of the first.  Row lines reuse one buffer
+// with two warp barriers per exchange.
+template <class SI> struct PingPong {
+  static constexpr bool v = std::is_same<SI, ColIdx>::value;
+};
 
 template <class C> __device__ __forceinline__ C mul_i(C a) { return cmk<C>(-a.y, a.x); }
 template <class C> __device__ __forceinline__ C mul_mi(C a) { return cmk<C>(a.y, -a.x); }
@@ -199,6 +207,11 @@ __device__ __forceinline__ void fft_passes(C (&v)[NF][8], C* sm, int fstride, co
     for (int f = 0; f < NF; ++f) dft_r<r, INV>(&v[f][b * r]);
   }
   if constexpr (p + 1 < PL::P) {
+    // exchange p goes through the second buffer when p is even (column lines)
+    C* xb = sm;
+    if constexpr (PingPong<SI>::v) {
+      if constexpr ((p & 1) == 0) xb = sm + si.alt;
+    }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = t + b * TPL;
@@ -207,7 +220,7 @@ __device__ __forceinline__ void fft_passes(C (&v)[NF][8], C* sm, int fstride, co
       for (int q = 0; q < r; ++q) {
         const int o = si(base + q * Ns);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) sm[f * fstride + o] = v[f][b * r + q];
+        for (int f = 0; f < NF; ++f) xb[f * fstride + o] = v[f][b * r + q];
       }
     }
     line_sync<SI>();
@@ -220,10 +233,10 @@ __device__ __forceinline__ void fft_passes(C (&v)[NF][8], C* sm, int fstride, co
       for (int q = 0; q < r2; ++q) {
         const int o = si(j + q * (L / r2));
 #pragma unroll
-        for (int f = 0; f < NF; ++f) v[f][b * r2 + q] = sm[f * fstride + o];
+        for (int f = 0; f < NF; ++f) v[f][b * r2 + q] = xb[f * fstride + o];
       }
     }
-    line_sync<SI>();
+    if constexpr (!PingPong<SI>::v) line_sync<SI>();
     fft_passes<C, L, INV, NF, p + 1, SI>(v, sm, fstride, tw, t, si);
   }
 }
@@ -312,8 +325,22 @@ template <int PADSHIFT> struct RowIdx {
 };
 struct ColIdx {
   int M;
+  int alt;  // offset (elements) of the second exchange buffer from the first
   __device__ __forceinline__ int operator()(int pos) const { return pos * M; }
 };
+// A column transform of power-of-two length L makes P - 1 exchanges, the first
+// through the second buffer.  When that count is odd the transform ends having
+// written the second buffer last, so a following transform of the same line
+// starts with the roles of the buffers swapped (its first exchange then writes
+// the buffer whose last reads preceded the earlier barrier).
+template <int L, class C> __device__ __forceinline__ void col_after(C*& sm, ColIdx& si) {
+  if constexpr (IsPow2<L>::v) {
+    if constexpr (((Plan<L>::P - 1) & 1) != 0) {
+      sm += si.alt;
+      si.alt = -si.alt;
+    }
+  }
+}
 template <class R> struct PadShift;
 template <> struct PadShift<double> { static constexpr int v = 3; };  // 8 x 16 B
 template <> struct PadShift<float> { static constexpr int v = 4; };   // 16 x 8 B

@@ -288,8 +288,8 @@ template <class Op> __device__ __forceinline__ void colpass_body(const KArgs<typ
   if (!gate_open(a)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* tw = reinterpret_cast<C*>(smraw);
-  C* buf = tw + L;
-  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(buf + a.M * L);
+  C* buf = tw + L;  // two exchange buffers of M lines each
+  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(buf + 2 * a.M * L);
   const int tid = threadIdx.x;
   const int m = tid % a.M, t = tid / a.M;
   const C* twsrc = (Op::AXIS == 1) ? a.twy : a.twz;
@@ -313,7 +313,9 @@ template <class Op> __device__ __forceinline__ void colpass_body(const KArgs<typ
     C v[1][8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[0][e] = src[base + (size_t)Plan<L>::entry_pos(Op::FIRST_INV, t, e) * lstride];
-    Op::process(a, u, f, x, o, base, lstride, t, v, buf + m, tw, ColIdx{a.M}, acc);
+    Op::process(a, u, f, x, o, base, lstride, t, v, buf + m, tw, ColIdx{a.M, a.M * L}, acc);
+    // the last exchange's reads end before the next tile's first writes
+    if constexpr (IsPow2<L>::v) __syncthreads();
   }
   if constexpr (NS > 0) {
     if (reduce_blocks<NS>(acc, a.partials, a.counter, Op::out(a, u), *red)) {
@@ -349,8 +351,9 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
   if (!gate_open(a)) return;
   extern __shared__ __align__(128) unsigned char smraw_tma[];
   const int tileC = a.M * L;
-  C* tiles = reinterpret_cast<C*>(smraw_tma);  // NST tiles
-  C* tw = tiles + NST * tileC;
+  C* tiles = reinterpret_cast<C*>(smraw_tma);  // NST tiles, then the second exchange buffer
+  C* xbuf = tiles + NST * tileC;
+  C* tw = xbuf + tileC;
   uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
   RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(bar + NST);
   const int tid = threadIdx.x;
@@ -408,15 +411,18 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     C v[1][8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[0][e] = tb[Plan<L>::entry_pos(Op::FIRST_INV, t, e) * a.M + m];
-    __syncthreads();  // the tile buffer becomes the FFT's exchange buffer
+    // power-of-two lengths exchange through the second buffer first, and the
+    // barrier of that exchange orders these reads before the tile's reuse;
+    // the mixed-radix passes work in place in the tile
+    if constexpr (!IsPow2<L>::v) __syncthreads();
     const int xb = tile % xb_n;
     const int rest = tile / xb_n;
     const int o = rest % other_n;
     const int f = a.f0 + rest / other_n;
     const int x = xb * a.M + m;
     const size_t base = (size_t)f * a.N + (Op::AXIS == 1 ? (size_t)o * a.nx * a.ny : (size_t)o * a.nx) + x;
-    Op::process(a, u, f, x, o, base, lstride, t, v, tb + m, tw, ColIdx{a.M}, acc);
-    __syncthreads();  // buffer b may be refilled from the next iteration on
+    Op::process(a, u, f, x, o, base, lstride, t, v, tb + m, tw, ColIdx{a.M, (int)(xbuf - tb)}, acc);
+    __syncthreads();  // buffer b may be refilled, and the second buffer rewritten, from here on
   }
   if (timed_out) {
     // let every copy already issued land before exiting: these waits keep the
@@ -630,6 +636,7 @@ template <class R_, int L_> struct ZEg {
       v[0][e] = cscale(v[0][e], mult);
     }
     if (f < 2) acc[f].add(ekin);
+    col_after<L>(sm, si);
     fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
@@ -979,6 +986,7 @@ template <class R_, int L_> struct ZPc {
       const R kz = wavenum<R>(Plan<L>::exit_pos(false, t, e), a.nz, a.dkz);
       v[0][e] = cscale(v[0][e], a.invN / (sh + R(0.5) * (kxy2 + kz * kz)));
     }
+    col_after<L>(sm, si);
     fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
@@ -1228,6 +1236,7 @@ template <class R_, int L_> struct ZLc {
       const R mult = (k2 > R(0)) ? (R(3) * kz * kz / k2 - R(1)) * a.invN : R(0);
       v[0][e] = cscale(v[0][e], mult);
     }
+    col_after<L>(sm, si);
     fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
@@ -1413,6 +1422,7 @@ template <class R_, int L_> struct ZKin {
       const int kz = Plan<L>::exit_pos(false, t, e);
       v[0][e] = cscale(v[0][e], exy * a.kin_tab[a.nx + a.ny + kz]);
     }
+    col_after<L>(sm, si);
     fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
@@ -1545,6 +1555,7 @@ template <class R_, int L_> struct ZPg {
       const R k2 = kxy2 + kz * kz;
       v[0][e] = cscale(v[0][e], (k2 > R(0)) ? (R(3) * kz * kz / k2 - R(1)) * a.invN : R(0));
     }
+    col_after<L>(sm, si);
     fft_line<C, L, true, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.W[base + (size_t)Plan<L>::exit_pos(true, t, e) * ls] = v[0][e];
