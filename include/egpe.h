@@ -317,14 +317,17 @@ egpe_status egpe_set_tuning(egpe_handle* h, int inst, int engine, const egpe_tun
  * n^{1/2} h_ij(a) with n = n1 + n2, a = sqrt(min(n1,n2)/n); the quadrature
  * sums m_i, h_ij over all but a few nodes are tabulated per parameter set as
  * piecewise polynomials in a, and the remaining nodes are evaluated exactly.
- * This host function builds the tables for params (as the engines do) and
- * evaluates them, plus the exact nodes, in FP64 at the count host points
- * (n1[k], n2[k]) >= 0: mu (2 per point: mu_LHY,1, mu_LHY,2) and hess (3 per
- * point: d^2F/dn1^2, d^2F/dn1dn2, d^2F/dn2^2); info (may be NULL) receives
- * the intervals per half and the number of exactly evaluated nodes.  All
- * arrays are host memory.  Errors: INVALID_ARG. */
-egpe_status egpe_lhy_table_eval(const egpe_params* params, int count, const double* n1, const double* n2,
-                                double* mu, double* hess, int info[2]);
+ * This host function builds the tables for params as the engine of the given
+ * precision does (EGPE_FP64: degree 11, checked to 2e-15 of each function's
+ * largest magnitude; EGPE_FP32: degree 7, checked to 1e-9) and evaluates
+ * them from their unrounded coefficients, plus the exact nodes, in FP64 at
+ * the count host points (n1[k], n2[k]) >= 0: mu (2 per point: mu_LHY,1,
+ * mu_LHY,2) and hess (3 per point: d^2F/dn1^2, d^2F/dn1dn2, d^2F/dn2^2); info
+ * (may be NULL) receives the intervals per half and the number of exactly
+ * evaluated nodes.  All arrays are host memory.  Errors: INVALID_ARG (also
+ * for a precision other than EGPE_FP64 or EGPE_FP32). */
+egpe_status egpe_lhy_table_eval(const egpe_params* params, int precision, int count, const double* n1,
+                                const double* n2, double* mu, double* hess, int info[2]);
 
 /* Poll budget of the device-side waits of every engine of the handle (the
  * TMA tile loads of the column passes; default 2^20 polls, roughly a second).
@@ -425,7 +428,7 @@ const char* egpe_status_string(egpe_status s);
 /* Message of the last CUDA error seen by this thread's calls ("" if none). */
 const char* egpe_last_error(void);
 
-/* ABI version (major * 100 + minor): 102. */
+/* ABI version (major * 100 + minor): 103. */
 int egpe_version(void);
 
 #ifdef __cplusplus

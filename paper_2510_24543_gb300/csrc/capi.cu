@@ -134,7 +134,7 @@ egpe_status sync_and_check(egpe_handle* h) {
 
 extern "C" {
 
-int egpe_version(void) { return 102; }
+int egpe_version(void) { return 103; }
 
 const char* egpe_last_error(void) { return egpe::g_last_error.c_str(); }
 
@@ -380,14 +380,17 @@ egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi,
   return EGPE_OK;
 }
 
-egpe_status egpe_lhy_table_eval(const egpe_params* params, int count, const double* n1, const double* n2,
-                                double* mu, double* hess, int info[2]) {
+egpe_status egpe_lhy_table_eval(const egpe_params* params, int precision, int count, const double* n1,
+                                const double* n2, double* mu, double* hess, int info[2]) {
   if (!params || count < 0 || (count > 0 && (!n1 || !n2 || !mu || !hess))) return EGPE_ERR_INVALID_ARG;
+  if (precision != EGPE_FP64 && precision != EGPE_FP32) return EGPE_ERR_INVALID_ARG;
   const egpe_grid g1 = {{16, 16, 16}, {1.0, 1.0, 1.0}};
   egpe_status s = validate(g1, *params);
   if (s != EGPE_OK) return s;
   const egpe_params& p = *params;
-  const egpe::LhyTableHost T = egpe::lhy_interp_table_cached(p);
+  const egpe::LhyTableHost T = precision == EGPE_FP32 ? egpe::lhy_interp_table_cached<float>(p)
+                                                      : egpe::lhy_interp_table_cached<double>(p);
+  const int NC = T.deg + 1, NR = egpe::kTabFun * NC;
   if (info) {
     info[0] = T.ni;
     info[1] = (int)T.exact.size();
@@ -413,10 +416,10 @@ egpe_status egpe_lhy_table_eval(const egpe_params* params, int count, const doub
       const double tt = a * tscale;
       const int i = std::min((int)tt, T.ni - 1);
       const double x = 2.0 * (tt - i) - 1.0;
-      const long double* c = &T.coef[((size_t)half * T.ni + i) * egpe::kTabRec];
+      const long double* c = &T.coef[((size_t)half * T.ni + i) * NR];
       for (int f = 0; f < egpe::kTabFun; ++f) {
-        double pv = (double)c[f * egpe::kTabCoef + egpe::kTabDeg];
-        for (int m = egpe::kTabDeg - 1; m >= 0; --m) pv = std::fma(pv, x, (double)c[f * egpe::kTabCoef + m]);
+        double pv = (double)c[f * NC + T.deg];
+        for (int m = T.deg - 1; m >= 0; --m) pv = std::fma(pv, x, (double)c[f * NC + m]);
         v[f] += (f < 2 ? n * std::sqrt(n) : std::sqrt(n)) * pv;
       }
     }

@@ -128,7 +128,8 @@ template <class R> egpe_status Engine<R>::apply_params(const egpe_params& p) {
   }
   EGPE_CUDA(cudaMemcpy(nodes_, h.data(), Q * sizeof(LhyNode<R>), cudaMemcpyHostToDevice));
   // interpolated LHY sums and the nodes left to exact evaluation
-  const LhyTableHost T = lhy_interp_table_cached(p);
+  const LhyTableHost T = lhy_interp_table_cached<R>(p);
+  static_assert(TabSpec<R>::deg + 1 == LhyTabDim<R>::coef, "table layout");
   std::vector<R> tab(T.coef.begin(), T.coef.end());
   if (tab_ && tab_elems_ != tab.size()) {
     cudaFree(tab_);

@@ -129,9 +129,11 @@ inline double lhy_skip_threshold(const egpe_params& p) {
 //   mu_LHY,i(n1, n2) = n^{3/2} m_i(a),   d^2 F / dn_i dn_j = n^{1/2} h_ij(a),
 // with one set of functions of a per half (half 0: n1 <= n2, half 1:
 // n1 > n2).  Summed over the nodes they are tabulated as piecewise
-// polynomials: NI equal intervals of a, degree 11, Chebyshev interpolation
-// in long double stored as monomial coefficients in the local coordinate
-// x = 2 (a NI sqrt(2) - i) - 1 of interval i.  A node's terms are analytic in
+// polynomials: NI equal intervals of a, Chebyshev interpolation in long
+// double stored as monomial coefficients in the local coordinate
+// x = 2 (a NI sqrt(2) - i) - 1 of interval i.  The FP64 engine's tables have
+// degree 11 and are checked to 2e-15; the FP32 engine's have degree 7 (two
+// 16-byte loads per function) and are checked to 1e-9, below FP32 rounding.  A node's terms are analytic in
 // a on the closed half except for the branch points of
 // s = sqrt(delta^2 + 4 eta12^2 n1 n2), which sit at a distance of about
 // d = |eta_jj| / (2 |eta12|) from a = 0 (j the majority component); nodes with
@@ -139,13 +141,19 @@ inline double lhy_skip_threshold(const egpe_params& p) {
 // exactly per point.  Each table is then checked against the exact sums at
 // the interval ends and midway between the interpolation nodes, and further
 // nodes (smallest d first) move to the exact list until every function
-// matches to kTabTol of its largest magnitude on that half.
+// matches to the tolerance of its largest magnitude on that half.
 // ---------------------------------------------------------------------------
-constexpr int kTabDeg = 11;                    // polynomial degree per interval
-constexpr int kTabCoef = kTabDeg + 1;
-constexpr int kTabFun = 5;                     // mu1, mu2, H11, H12, H22
-constexpr int kTabRec = kTabFun * kTabCoef;    // coefficients per interval
-constexpr long double kTabTol = 2e-15L;
+constexpr int kTabFun = 5;  // mu1, mu2, H11, H12, H22
+// Degree and check tolerance of the tables for field type R.
+template <class R> struct TabSpec;
+template <> struct TabSpec<double> {
+  static constexpr int deg = 11;
+  static constexpr long double tol = 2e-15L;
+};
+template <> struct TabSpec<float> {
+  static constexpr int deg = 7;
+  static constexpr long double tol = 1e-9L;
+};
 
 // Node q's contributions (W-weighted) to mu1, mu2, H11, H12, H22 at (n1, n2):
 // F_q = W sum_+- max(V_+-,0)^{5/2}, V_+- = A +- s (see lhy.cuh for the
@@ -182,6 +190,7 @@ inline void lhy_node_terms(long double e11, long double e22, long double e12, lo
 
 struct LhyTableHost {
   int ni = 0;                      // intervals per half; 0: no table (every node exact)
+  int deg = 0;                     // polynomial degree (deg + 1 coefficients per function)
   std::vector<long double> coef;   // [half][interval][function][coefficient]
   std::vector<int> exact;          // node indices evaluated exactly per point
 };
@@ -206,25 +215,27 @@ inline void point(int half, long double a, long double& n1, long double& n2) {
 // Builds the tables for NI intervals per half; returns false if the check
 // failed for some node set it could still shrink (then `worst` names the half
 // whose smallest-d regular node should move to the exact list).
+template <int DEG>
 inline bool lhy_table_try(const std::vector<tab_detail::NodeEta>& nd, const std::vector<char>& regular, int NI,
-                          std::vector<long double>& coef, int& worst_half) {
+                          long double tol, std::vector<long double>& coef, int& worst_half) {
   using namespace tab_detail;
+  constexpr int NC = DEG + 1, NR = kTabFun * NC;
   const long double amax = sqrtl(0.5L), h = amax / NI;
   const long double pi = 3.141592653589793238462643383279502884L;
-  coef.assign((size_t)2 * NI * kTabRec, 0.0L);
-  long double xs[kTabCoef], T[kTabCoef][kTabCoef];
-  for (int j = 0; j < kTabCoef; ++j) {
-    xs[j] = cosl(pi * (j + 0.5L) / kTabCoef);
+  coef.assign((size_t)2 * NI * NR, 0.0L);
+  long double xs[NC], T[NC][NC];
+  for (int j = 0; j < NC; ++j) {
+    xs[j] = cosl(pi * (j + 0.5L) / NC);
     T[j][0] = 1.0L;
     T[j][1] = xs[j];
-    for (int k = 2; k < kTabCoef; ++k) T[j][k] = 2.0L * xs[j] * T[j][k - 1] - T[j][k - 2];
+    for (int k = 2; k < NC; ++k) T[j][k] = 2.0L * xs[j] * T[j][k - 1] - T[j][k - 2];
   }
   // monomial coefficients of the Chebyshev polynomials: mono[k][m] = [x^m] T_k
-  long double mono[kTabCoef][kTabCoef] = {};
+  long double mono[NC][NC] = {};
   mono[0][0] = 1.0L;
   mono[1][1] = 1.0L;
-  for (int k = 2; k < kTabCoef; ++k)
-    for (int m = 0; m < kTabCoef; ++m)
+  for (int k = 2; k < NC; ++k)
+    for (int m = 0; m < NC; ++m)
       mono[k][m] = (m > 0 ? 2.0L * mono[k - 1][m - 1] : 0.0L) - mono[k - 2][m];
   std::vector<char> all(nd.size(), 1);
   bool ok = true;
@@ -233,40 +244,40 @@ inline bool lhy_table_try(const std::vector<tab_detail::NodeEta>& nd, const std:
   for (int half = 0; half < 2; ++half) {
     long double scale[kTabFun] = {}, err[kTabFun] = {};
     for (int i = 0; i < NI; ++i) {
-      long double f[kTabCoef][kTabFun];
-      for (int j = 0; j < kTabCoef; ++j) {
+      long double f[NC][kTabFun];
+      for (int j = 0; j < NC; ++j) {
         long double n1, n2;
         point(half, i * h + (xs[j] + 1.0L) * 0.5L * h, n1, n2);
         sums(nd, regular, n1, n2, f[j]);
       }
-      long double* out = &coef[((size_t)half * NI + i) * kTabRec];
+      long double* out = &coef[((size_t)half * NI + i) * NR];
       for (int fn = 0; fn < kTabFun; ++fn) {
-        long double c[kTabCoef];
-        for (int k = 0; k < kTabCoef; ++k) {
+        long double c[NC];
+        for (int k = 0; k < NC; ++k) {
           long double acc = 0;
-          for (int j = 0; j < kTabCoef; ++j) acc += f[j][fn] * T[j][k];
-          c[k] = acc * 2.0L / kTabCoef;
+          for (int j = 0; j < NC; ++j) acc += f[j][fn] * T[j][k];
+          c[k] = acc * 2.0L / NC;
         }
         c[0] *= 0.5L;
-        for (int m = 0; m < kTabCoef; ++m) {
+        for (int m = 0; m < NC; ++m) {
           long double b = 0;
-          for (int k = m; k < kTabCoef; ++k) b += c[k] * mono[k][m];
-          out[fn * kTabCoef + m] = b;
+          for (int k = m; k < NC; ++k) b += c[k] * mono[k][m];
+          out[fn * NC + m] = b;
         }
       }
       // check at both ends and midway between consecutive interpolation nodes
-      for (int j = -1; j < kTabCoef; ++j) {
+      for (int j = -1; j < NC; ++j) {
         long double x;
         if (j < 0) x = -1.0L;
-        else if (j == kTabCoef - 1) x = 1.0L;
+        else if (j == NC - 1) x = 1.0L;
         else x = 0.5L * (xs[j] + xs[j + 1]);
         long double n1, n2, ex[kTabFun], full[kTabFun];
         point(half, i * h + (x + 1.0L) * 0.5L * h, n1, n2);
         sums(nd, regular, n1, n2, ex);
         sums(nd, all, n1, n2, full);
         for (int fn = 0; fn < kTabFun; ++fn) {
-          long double p = out[fn * kTabCoef + kTabDeg];
-          for (int m = kTabDeg - 1; m >= 0; --m) p = p * x + out[fn * kTabCoef + m];
+          long double p = out[fn * NC + DEG];
+          for (int m = DEG - 1; m >= 0; --m) p = p * x + out[fn * NC + m];
           err[fn] = std::max(err[fn], fabsl(p - ex[fn]));
           scale[fn] = std::max(scale[fn], fabsl(full[fn]));
         }
@@ -274,7 +285,7 @@ inline bool lhy_table_try(const std::vector<tab_detail::NodeEta>& nd, const std:
     }
     for (int fn = 0; fn < kTabFun; ++fn) {
       const long double r = scale[fn] > 0 ? err[fn] / scale[fn] : 0.0L;
-      if (r > kTabTol) ok = false;
+      if (r > tol) ok = false;
       if (r > worst) {
         worst = r;
         worst_half = half;
@@ -285,8 +296,8 @@ inline bool lhy_table_try(const std::vector<tab_detail::NodeEta>& nd, const std:
 }
 
 // Tables for the couplings p (NI = 32 or 64 intervals per half, whichever
-// leaves fewer nodes to exact evaluation; ties go to 32).
-inline LhyTableHost lhy_interp_table(const egpe_params& p) {
+// leaves fewer nodes to exact evaluation; ties go to 32) for field type R.
+template <class R> inline LhyTableHost lhy_interp_table(const egpe_params& p) {
   using namespace tab_detail;
   const int Q = p.lhy_nodes;
   std::vector<long double> u, w;
@@ -316,7 +327,7 @@ inline LhyTableHost lhy_interp_table(const egpe_params& p) {
       int nreg = 0;
       for (char r : regular) nreg += r;
       if (nreg == 0) break;
-      if (lhy_table_try(nd, regular, NI, coef, half)) break;
+      if (lhy_table_try<TabSpec<R>::deg>(nd, regular, NI, TabSpec<R>::tol, coef, half)) break;
       int qmin = -1;
       for (int q = 0; q < Q; ++q)
         if (regular[q] && (qmin < 0 || dist[half][q] < dist[half][qmin])) qmin = q;
@@ -328,16 +339,17 @@ inline LhyTableHost lhy_interp_table(const egpe_params& p) {
     if (exact.size() < best.exact.size()) {
       best.exact = exact;
       best.ni = (int)exact.size() == Q ? 0 : NI;
+      best.deg = TabSpec<R>::deg;
       best.coef = best.ni ? coef : std::vector<long double>();
     }
   }
   return best;
 }
 
-// The tables of one parameter set, built once per process (the FP32 and FP64
-// engines of an instance, and repeated handles, share the build); returned by
-// value, so a later eviction cannot invalidate a caller's copy.
-inline LhyTableHost lhy_interp_table_cached(const egpe_params& p) {
+// The tables of one parameter set and field type, built once per process
+// (repeated handles share the build); returned by value, so a later eviction
+// cannot invalidate a caller's copy.
+template <class R> inline LhyTableHost lhy_interp_table_cached(const egpe_params& p) {
   static std::mutex mu;
   static std::map<std::vector<double>, LhyTableHost> memo;
   const std::vector<double> key = {p.g[0][0], p.g[0][1], p.g[1][0], p.g[1][1], p.gdd[0][0], p.gdd[0][1],
@@ -346,7 +358,7 @@ inline LhyTableHost lhy_interp_table_cached(const egpe_params& p) {
   auto it = memo.find(key);
   if (it != memo.end()) return it->second;
   if (memo.size() >= 1024) memo.clear();
-  return memo.emplace(key, lhy_interp_table(p)).first->second;
+  return memo.emplace(key, lhy_interp_table<R>(p)).first->second;
 }
 
 }  // namespace egpe

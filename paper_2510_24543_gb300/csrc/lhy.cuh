@@ -459,12 +459,18 @@ __device__ __forceinline__ void lhy_eta_sums(const LhyNode<R>* __restrict__ nd, 
 // (n1, n2), so with n = n1 + n2 and a = sqrt(min(n1, n2)/n):
 //   mu_LHY,i = n^{3/2} m_i(a),   d^2 F/dn_i dn_j = n^{1/2} h_ij(a),
 // where m_i, h_ij are the quadrature sums over the table's nodes, stored per
-// half (n1 <= n2, n1 > n2) as degree-11 polynomials on equal intervals of a
-// (host_tables.h builds and checks them).  A record holds, per interval, the
-// 12 coefficients of m1, m2, h11, h12, h22 in the local coordinate x in [-1,1].
+// half (n1 <= n2, n1 > n2) as polynomials on equal intervals of a (the host
+// builds and checks them).  A record holds, per interval, the coefficients of
+// m1, m2, h11, h12, h22 in the local coordinate x in [-1,1].
 // ----------------------------------------------------------------------------
-constexpr int kLhyTabCoef = 12;
-constexpr int kLhyTabRec = 5 * kLhyTabCoef;
+// Coefficients per function: degree 11 for FP64 fields, degree 7 for FP32.
+template <class R> struct LhyTabDim;
+template <> struct LhyTabDim<double> {
+  static constexpr int coef = 12, rec = 5 * coef;
+};
+template <> struct LhyTabDim<float> {
+  static constexpr int coef = 8, rec = 5 * coef;
+};
 
 template <class R> struct LhyTab {
   const R* tab;  // [half][interval][function][coefficient], 16-byte aligned records
@@ -472,16 +478,12 @@ template <class R> struct LhyTab {
   R tscale;      // ni sqrt(2): a tscale is the interval coordinate
 };
 
-// Polynomial of degree 11 at x (Horner), coefficients from global memory
-// through the read-only path in 16-byte loads.
-__device__ __forceinline__ float horner12(const float* c, float x) {
+// The interval polynomial at x (Horner), coefficients from global memory
+// through the read-only path in 16-byte loads: degree 7 in FP32, 11 in FP64.
+__device__ __forceinline__ float horner_tab(const float* c, float x) {
   const float4* v = reinterpret_cast<const float4*>(c);
-  const float4 a = __ldg(v), b = __ldg(v + 1), d = __ldg(v + 2);
-  float p = d.w;
-  p = fmaf(p, x, d.z);
-  p = fmaf(p, x, d.y);
-  p = fmaf(p, x, d.x);
-  p = fmaf(p, x, b.w);
+  const float4 a = __ldg(v), b = __ldg(v + 1);
+  float p = b.w;
   p = fmaf(p, x, b.z);
   p = fmaf(p, x, b.y);
   p = fmaf(p, x, b.x);
@@ -490,7 +492,7 @@ __device__ __forceinline__ float horner12(const float* c, float x) {
   p = fmaf(p, x, a.y);
   return fmaf(p, x, a.x);
 }
-__device__ __forceinline__ double horner12(const double* c, double x) {
+__device__ __forceinline__ double horner_tab(const double* c, double x) {
   const double2* v = reinterpret_cast<const double2*>(c);
   double2 k[6];
 #pragma unroll
@@ -517,7 +519,7 @@ __device__ __forceinline__ const R* lhy_tab_locate(const LhyTab<R>& t, R n1, R n
   int i = (int)tt;  // a <= 1/sqrt(2) up to rounding: clamp to the last interval (NaN converts to 0)
   i = i < 0 ? 0 : (i < t.ni - 1 ? i : t.ni - 1);
   x = R(2) * (tt - (R)i) - R(1);
-  return t.tab + (size_t)((h ? t.ni : 0) + i) * kLhyTabRec;
+  return t.tab + (size_t)((h ? t.ni : 0) + i) * LhyTabDim<R>::rec;
 }
 
 // The table's part of mu_LHY,1 and mu_LHY,2 at NP points.
@@ -530,8 +532,8 @@ __device__ __forceinline__ void lhy_tab_mu(const LhyTab<R>& t, const R (&n1)[NP]
     const R* c = lhy_tab_locate(t, n1[j], n2[j], x, rs);
     const R n = n1[j] + n2[j];
     const R n32 = n * n * rs;
-    m1[j] = n32 * horner12(c, x);
-    m2[j] = n32 * horner12(c + kLhyTabCoef, x);
+    m1[j] = n32 * horner_tab(c, x);
+    m2[j] = n32 * horner_tab(c + LhyTabDim<R>::coef, x);
   }
 }
 
@@ -544,9 +546,9 @@ __device__ __forceinline__ void lhy_tab_hess(const LhyTab<R>& t, const R (&n1)[N
     R x, rs;
     const R* c = lhy_tab_locate(t, n1[j], n2[j], x, rs);
     const R n = n1[j] + n2[j];
-    const R h11 = horner12(c + 2 * kLhyTabCoef, x);
-    const R h12 = horner12(c + 3 * kLhyTabCoef, x);
-    const R h22 = horner12(c + 4 * kLhyTabCoef, x);
+    const R h11 = horner_tab(c + 2 * LhyTabDim<R>::coef, x);
+    const R h12 = horner_tab(c + 3 * LhyTabDim<R>::coef, x);
+    const R h22 = horner_tab(c + 4 * LhyTabDim<R>::coef, x);
     H[j] = n * rs * (n1p[j] * (h11 * n1p[j] + R(2) * h12 * n2p[j]) + h22 * n2p[j] * n2p[j]);
   }
 }

@@ -112,8 +112,8 @@ _SIGS = {
                                  ct.POINTER(egpe_tuning), ct.c_int, ct.POINTER(ct.c_int)]),
     "egpe_set_tuning": (ct.c_int, [ct.c_void_p, ct.c_int, ct.c_int, ct.POINTER(egpe_tuning), ct.c_int]),
     "egpe_set_wait_limit": (ct.c_int, [ct.c_void_p, ct.c_longlong]),
-    "egpe_lhy_table_eval": (ct.c_int, [ct.POINTER(egpe_params), ct.c_int, ct.c_void_p, ct.c_void_p, ct.c_void_p,
-                                       ct.c_void_p, ct.POINTER(ct.c_int)]),
+    "egpe_lhy_table_eval": (ct.c_int, [ct.POINTER(egpe_params), ct.c_int, ct.c_int, ct.c_void_p, ct.c_void_p,
+                                       ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_int)]),
     "egpe_default_solve_opts": (None, [ct.POINTER(egpe_solve_opts)]),
     "egpe_status_string": (ct.c_char_p, [ct.c_int]),
     "egpe_last_error": (ct.c_char_p, []),
@@ -434,10 +434,11 @@ def egpe_set_tuning(h: int, inst: int, engine: int, entries) -> None:
     _check("egpe_set_tuning", load().egpe_set_tuning(ct.c_void_p(h), inst, engine, arr, len(entries)))
 
 
-def egpe_lhy_table_eval(params: egpe_params, n1, n2):
-    """The LHY interpolation tables (plus exact nodes) evaluated on the host at
-    points (n1[k], n2[k]): returns (mu (count, 2), hess (count, 3), (intervals
-    per half, exact nodes))."""
+def egpe_lhy_table_eval(params: egpe_params, n1, n2, precision: int = 0):
+    """The LHY interpolation tables of the engine of `precision` (EGPE_FP64 or
+    EGPE_FP32), plus its exact nodes, evaluated on the host at points
+    (n1[k], n2[k]): returns (mu (count, 2), hess (count, 3), (intervals per
+    half, exact nodes))."""
     import numpy as np
     a = np.ascontiguousarray(n1, dtype=np.float64).ravel()
     b = np.ascontiguousarray(n2, dtype=np.float64).ravel()
@@ -446,8 +447,8 @@ def egpe_lhy_table_eval(params: egpe_params, n1, n2):
     mu = np.empty((a.size, 2))
     hs = np.empty((a.size, 3))
     info = (ct.c_int * 2)()
-    _check("egpe_lhy_table_eval", load().egpe_lhy_table_eval(ct.byref(params), a.size, a.ctypes.data, b.ctypes.data,
-                                                             mu.ctypes.data, hs.ctypes.data, info))
+    _check("egpe_lhy_table_eval", load().egpe_lhy_table_eval(ct.byref(params), int(precision), a.size, a.ctypes.data,
+                                                             b.ctypes.data, mu.ctypes.data, hs.ctypes.data, info))
     return mu, hs, (info[0], info[1])
 
 

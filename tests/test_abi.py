@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert E.egpe_version() == 102
+    assert E.egpe_version() == 103
     for s in range(9):
         assert E.egpe_status_string(s)
     assert E.egpe_status_string(99) == "unknown status"
