@@ -114,9 +114,13 @@ typedef struct {
   char name[48];            /* readable pass name                                   */
   int L;                    /* line length of the pass                              */
   int kind;                 /* 0 row pass: choice = rows per block; 1 column pass:
-                               choice 1 = TMA-fed tile loads, 0 = plain loads       */
+                               choice 1 = TMA-fed tile loads, 0 = plain loads;
+                               2 (key "column tile row bytes"): choice = row width
+                               of every column-pass tile, 64, 128 or 256 bytes     */
   int choice, default_choice;
-  double ms_best, ms_default;  /* device ms per launch: chosen and untuned shape     */
+  double ms_best, ms_default;  /* device ms of the attempt's launch sequence with the
+                                  chosen and with the default choice (the earlier
+                                  entries' choices applied)                         */
 } egpe_tuning;
 
 /* Options of egpe_ncg_solve (Algorithm 1 with the readings named below). */
@@ -294,13 +298,15 @@ egpe_status egpe_profile_attempt(egpe_handle* h, int inst, int engine, const voi
                                  int cap, char* names, double* ms, double* bytes, int* count);
 
 /* Launch-shape autotuner (no counterpart in the paper: it picks how the
- * transforms of Sec. VI.B are tiled on this GPU).  Times every kernel of one
- * attempt of the instance's engine (0 FP64, 1 FP32) from psi (device) with
- * each candidate shape -- rows per block of the row passes, TMA-fed or plain
- * loads of the column passes -- `reps` launches each (controller off), keeps
- * the fastest in the handle for every later call (captured graphs are
- * rebuilt), and writes up to cap results to out (host).  The arithmetic does
- * not change with the shape.  Leaves the instance's solver state reset. */
+ * transforms of Sec. VI.B are tiled on this GPU).  Replays the launch sequence
+ * of one attempt of the instance's engine (0 FP64, 1 FP32) from psi (device),
+ * controller off, `reps` times per candidate, trying one choice at a time --
+ * rows per block of each row pass, TMA-fed or plain loads of each column
+ * pass, then the tile row width of all column passes -- and keeps a candidate
+ * only if the sequence gets faster by more than 0.3%.  The choices stay in
+ * the handle for every later call (captured graphs are rebuilt); up to cap
+ * results go to out (host).  The arithmetic of each point does not change with
+ * the shape (sums may regroup).  Leaves the instance's solver state reset. */
 egpe_status egpe_autotune(egpe_handle* h, int inst, int engine, const void* psi, int precond, int reps,
                           egpe_tuning* out, int cap, int* count);
 

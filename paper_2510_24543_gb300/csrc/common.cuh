@@ -53,6 +53,9 @@ enum PgSlot {  // parameter-derivative sums (x dV later)
   PG_N11 = 0, PG_N12, PG_N22, PG_K11, PG_K12, PG_K22, PG_X2, PG_Y2, PG_Z2,
   PG_F, PG_L11, PG_L22, PG_L12, PG_M11, PG_M22, PG_M12, PG_NS
 };
+// Default row width in bytes of a column-pass tile (one cache line); the
+// autotuner may pick 64 or 256 for the power-of-two lengths.
+#define EGPE_COL_BYTES 128
 static constexpr int MAX_NS = 16;
 static_assert(PG_NS <= MAX_NS, "reduction slots");
 

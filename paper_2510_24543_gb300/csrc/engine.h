@@ -41,8 +41,12 @@ template <class R> struct LaunchRec {
   long long rows = 0;
 };
 
-// One tuned launch shape: rows per block (row passes) or 1 = TMA-fed / 0 =
-// plain loads (column passes).
+// Key of the tuning entry that sets the column tile width (kind 2).
+inline const char* const kColBytesKey = "column tile row bytes";
+
+// One tuned launch shape: rows per block (row passes), 1 = TMA-fed / 0 =
+// plain loads (column passes), or the column tile row width in bytes.
+
 struct TuneResult {
   std::string key, name;
   int L = 0, kind = 0, choice = 0, default_choice = 0;
@@ -108,13 +112,18 @@ template <class R> class Engine {
   egpe_status autotune(const C* psi, int precond, int reps, std::vector<TuneResult>& out);
   // Applies previously tuned shapes (by key); unknown keys are ignored.
   void set_tuning(const std::string& key, int choice) {
+    if (key == kColBytesKey) return set_col_bytes(choice);
     tune_[key] = choice;
     drop_graphs();
   }
   void clear_tuning() {
     tune_.clear();
+    set_col_bytes(EGPE_COL_BYTES);
     drop_graphs();
   }
+  // Row width in bytes (64, 128 or 256; anything else: the default) of the
+  // column-pass tiles of the power-of-two lengths; rebuilds the tensor maps.
+  void set_col_bytes(int bytes);
   // Poll budget of the device-side TMA waits (default kTmaWaitPolls; 0 gives
   // up before the first poll, which tests use to reach the timeout path).
   void set_wait_limit(long long polls);
@@ -191,6 +200,7 @@ template <class R> class Engine {
   // strided passes fed by TMA (tensor maps over the workspace W)
   bool use_tma_ = true;
   bool have_maps_ = false;
+  int col_bytes_ = EGPE_COL_BYTES;  // column tile row width (set_col_bytes)
   CUtensorMap tmW_y_{}, tmW_z_{};
   size_t tpos_ = 0;
 

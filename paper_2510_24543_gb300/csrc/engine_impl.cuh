@@ -53,13 +53,16 @@ static TmaEncodeFn tma_encode_fn() {
   return fn;
 }
 
-// Columns per tile of the strided passes: EGPE_COL_BYTES-wide rows (128 B:
-// one cache line) and at least one warp; the power-of-two lengths, whose
-// kernels are bound to 512 threads, may take wider rows.
-template <class C> static inline int col_tile_width(int L, int nx) {
+// Columns per tile of the strided passes: tile rows of col_bytes (64, 128 or
+// 256; EGPE_COL_BYTES = 128, one cache line, unless the autotuner chose
+// another width) for the power-of-two lengths, whose kernels are bound to 512
+// threads, and of 128 bytes for the mixed-radix lengths (bound to that width);
+// whole warps, and the TMA-fed pass's tiles within 200 KB of shared memory.
+template <class C> static inline int col_tile_width(int L, int nx, int col_bytes) {
   const int TPL = L / 8;
   const bool pow2 = (L & (L - 1)) == 0;
-  int M = pow2 ? std::min((int)(EGPE_COL_BYTES / sizeof(C)), 512 / TPL) : (int)(128 / sizeof(C));
+  int M = pow2 ? std::min((int)(col_bytes / sizeof(C)), 512 / TPL) : (int)(128 / sizeof(C));
+  while (pow2 && M > 1 && (size_t)(kColStages + 1) * M * L * sizeof(C) > 200 * 1024) M /= 2;
   M = std::min(std::max(M, whole_warp_rows(L)), nx);
   while (M > whole_warp_rows(L) && nx % M != 0) M /= 2;  // whole tiles across x
   return M;
@@ -68,11 +71,12 @@ template <class C> static inline int col_tile_width(int L, int nx) {
 // Tensor map of `nfields` consecutive complex fields (nx, ny, nz), box = one
 // column tile of the y (axis 1) or z (axis 2) pass.
 template <class C>
-static bool make_col_map(CUtensorMap& tm, const void* base, int nx, int ny, int nz, int nfields, int axis) {
+static bool make_col_map(CUtensorMap& tm, const void* base, int nx, int ny, int nz, int nfields, int axis,
+                         int col_bytes) {
   TmaEncodeFn fn = tma_encode_fn();
   if (!fn) return false;
   const int L = axis == 1 ? ny : nz;
-  const int M = col_tile_width<C>(L, nx);
+  const int M = col_tile_width<C>(L, nx, col_bytes);
   const cuuint64_t esz = sizeof(C) / 8;
   cuuint64_t dims[3] = {(cuuint64_t)nx * esz, (cuuint64_t)ny, (cuuint64_t)nz * nfields};
   cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(C), (cuuint64_t)nx * ny * sizeof(C)};
@@ -288,8 +292,18 @@ template <class R> egpe_status Engine<R>::create(const egpe_grid& g, const egpe_
   a.kin_tab = kin_tab_;
   a.wait_polls = kTmaWaitPolls;
   a.gate = GATE_ALWAYS;
-  have_maps_ = make_col_map<C>(tmW_y_, a.W, nx, ny, nz, 3, 1) && make_col_map<C>(tmW_z_, a.W, nx, ny, nz, 3, 2);
+  have_maps_ = make_col_map<C>(tmW_y_, a.W, nx, ny, nz, 3, 1, col_bytes_) &&
+               make_col_map<C>(tmW_z_, a.W, nx, ny, nz, 3, 2, col_bytes_);
   return reset_state(nullptr, 0, 0, 0.0, 0.0);
+}
+
+template <class R> void Engine<R>::set_col_bytes(int b) {
+  if (b != 64 && b != 128 && b != 256) b = EGPE_COL_BYTES;
+  if (b == col_bytes_) return;
+  col_bytes_ = b;
+  have_maps_ = make_col_map<C>(tmW_y_, base_->W, nx, ny, nz, 3, 1, b) &&
+               make_col_map<C>(tmW_z_, base_->W, nx, ny, nz, 3, 2, b);
+  drop_graphs();
 }
 
 template <class R> void Engine<R>::set_wait_limit(long long polls) {
@@ -474,10 +488,15 @@ egpe_status Engine<R>::record_attempt(int mode, std::vector<LaunchRec<R>>& recs,
   return s;
 }
 
-// Launch-shape autotuning.  Each distinct kernel of one attempt is launched
-// on its own (controller off, gate open) with every candidate shape and timed
-// with CUDA events; the fastest shape is kept in tune_ (by op key) and used by
-// every later launch, recording and graph capture of this engine.
+// Launch-shape autotuning.  The kernels of one attempt are recorded and the
+// whole sequence is replayed (controller off, gates open) with CUDA events
+// around it, so each kernel runs with the caches its predecessors leave, as in
+// a solve; a kernel timed alone finds its own inputs in L2 and prefers shapes
+// that lose in the pipeline.  Candidates are tried one op key at a time
+// (coordinate descent over the keys in launch order), then the column tile
+// width; a candidate replaces the current choice only if the sequence gets
+// faster by more than 0.3%.  Choices go to tune_ (by op key) and col_bytes_,
+// and are used by every later launch, recording and graph capture.
 template <class R>
 egpe_status Engine<R>::autotune(const C* psi, int precond, int reps, std::vector<TuneResult>& out) {
   out.clear();
@@ -496,24 +515,87 @@ egpe_status Engine<R>::autotune(const C* psi, int precond, int reps, std::vector
   EGPE_TRY(enq_eg(0, GATE_ALWAYS, 1));
   EGPE_TRY(enq_attempt(o.precond));  // realistic coefficients in the state
   EGPE_CUDA(cudaStreamSynchronize(stream));
+  tune_.clear();
+  set_col_bytes(EGPE_COL_BYTES);
   std::vector<LaunchRec<R>> recs;
   std::vector<KArgs<R>> args;
-  const auto saved = tune_;
-  tune_.clear();  // record the untuned shapes
-  egpe_status s = record_attempt(o.precond, recs, args);
-  tune_ = saved;
-  EGPE_TRY(s);
+  EGPE_TRY(record_attempt(o.precond, recs, args));
   cudaEvent_t e0, e1;
   EGPE_CUDA(cudaEventCreate(&e0));
   EGPE_CUDA(cudaEventCreate(&e1));
-  std::unordered_map<std::string, int> seen;
   egpe_status st = EGPE_OK;
+  // shape of a recorded launch under the current choices (kind 0/1 only)
+  auto choice_of = [&](const LaunchRec<R>& r) {
+    auto it = tune_.find(r.key);
+    return it != tune_.end() ? it->second : r.mx;
+  };
+  // min over reps of the device time of the whole recorded sequence
+  auto time_seq = [&](const std::vector<LaunchRec<R>>& rs, const std::vector<KArgs<R>>& as) -> double {
+    double tmin = 1e30;
+    for (int k = 0; k <= reps && st == EGPE_OK; ++k) {
+      cudaEventRecord(e0, stream);
+      for (const LaunchRec<R>& r : rs) {
+        if (r.kind > 1 || !r.key) continue;  // pointwise passes have one shape
+        KArgs<R> a = as[r.arg];
+        a.ctrl = 0;
+        a.gate = GATE_ALWAYS;
+        const int c = choice_of(r);
+        const void* fn;
+        int block;
+        size_t smem;
+        long long units;
+        CUtensorMap tmc;
+        void* params[2];
+        if (r.kind == 0) {
+          a.MX = c;
+          fn = r.fn1;
+          block = c * r.tpl;
+          smem = r.smem_fixed + (size_t)c * r.rowbytes;
+          units = (r.rows + c - 1) / c;
+          params[0] = &a;
+        } else {
+          const bool tma = c != 0 && r.tm && use_tma_;
+          fn = tma ? r.fn1_tma : r.fn1;
+          block = r.block;
+          smem = tma ? r.smem_tma : r.smem_plain;
+          units = r.units;
+          if (tma) {
+            tmc = *r.tm;
+            params[0] = &tmc;
+            params[1] = &a;
+          } else {
+            params[0] = &a;
+          }
+        }
+        const int occ = occupancy(fn, block, smem);
+        const dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(units, std::min(occ * nsm_, 16384))));
+        const cudaError_t le = cudaLaunchKernel(fn, grid, dim3((unsigned)block), params, smem, stream);
+        if (le != cudaSuccess) {
+          set_error("autotune launch", le);
+          st = EGPE_ERR_CUDA;
+          break;
+        }
+      }
+      cudaEventRecord(e1, stream);
+      if (st != EGPE_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        set_error("autotune", cudaGetLastError());
+        st = EGPE_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (k > 0) tmin = std::min(tmin, (double)ms);  // the first replay warms up
+    }
+    return tmin;
+  };
+  constexpr double kGain = 0.997;  // a change must save more than 0.3%
+  double cur = time_seq(recs, args);
+  std::unordered_map<std::string, int> seen;
   for (const LaunchRec<R>& r : recs) {
+    if (st != EGPE_OK) break;
     if (r.kind > 1 || !r.key || seen.count(r.key)) continue;
     seen[r.key] = 1;
-    KArgs<R> a = args[r.arg];
-    a.ctrl = 0;
-    a.gate = GATE_ALWAYS;
     std::vector<int> cand;
     if (r.kind == 0) {
       for (int mx = r.mx; mx >= 1; mx /= 2)
@@ -530,61 +612,46 @@ egpe_status Engine<R>::autotune(const C* psi, int precond, int reps, std::vector
     tr.L = r.L;
     tr.kind = r.kind;
     tr.default_choice = r.mx;
-    double best = 1e30;
+    tr.choice = r.mx;
+    tr.ms_default = tr.ms_best = cur;
     for (int c : cand) {
-      const void* fn;
-      int block;
-      size_t smem;
-      long long units;
-      CUtensorMap tmc;
-      void* params[2];
-      if (r.kind == 0) {
-        a.MX = c;
-        fn = r.fn1;
-        block = c * r.tpl;
-        smem = r.smem_fixed + (size_t)c * r.rowbytes;
-        units = (r.rows + c - 1) / c;
-        params[0] = &a;
-      } else {
-        fn = c ? r.fn1_tma : r.fn1;
-        block = r.block;
-        smem = c ? r.smem_tma : r.smem_plain;
-        units = r.units;
-        if (c) {
-          tmc = *r.tm;
-          params[0] = &tmc;
-          params[1] = &a;
-        } else {
-          params[0] = &a;
-        }
-      }
-      const int occ = occupancy(fn, block, smem);
-      const dim3 grid((unsigned)std::max<long long>(1, std::min<long long>(units, std::min(occ * nsm_, 16384))));
-      double tmin = 1e30;
-      for (int k = 0; k <= reps && st == EGPE_OK; ++k) {
-        cudaEventRecord(e0, stream);
-        cudaError_t le = cudaLaunchKernel(fn, grid, dim3((unsigned)block), params, smem, stream);
-        cudaEventRecord(e1, stream);
-        if (le != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-          set_error("autotune launch", le != cudaSuccess ? le : cudaGetLastError());
-          st = EGPE_ERR_CUDA;
-          break;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (k > 0) tmin = std::min(tmin, (double)ms);  // the first launch warms up
-      }
+      if (c == r.mx) continue;
+      tune_[r.key] = c;
+      const double t = time_seq(recs, args);
       if (st != EGPE_OK) break;
-      if (c == r.mx) tr.ms_default = tmin;
-      if (tmin < best) {
-        best = tmin;
+      if (t < kGain * tr.ms_best) {
+        tr.ms_best = t;
         tr.choice = c;
       }
     }
     if (st != EGPE_OK) break;
-    tr.ms_best = best;
-    tune_[tr.key] = tr.choice;
+    tune_[r.key] = tr.choice;
+    cur = tr.ms_best;
     out.push_back(tr);
+  }
+  // the column tile width: re-recorded at each width (the shapes change)
+  if (st == EGPE_OK) {
+    TuneResult tr;
+    tr.key = kColBytesKey;
+    tr.name = "column tile row bytes";
+    tr.kind = 2;
+    tr.default_choice = tr.choice = EGPE_COL_BYTES;
+    tr.ms_default = tr.ms_best = cur;
+    for (int w : {64, 256}) {
+      set_col_bytes(w);
+      std::vector<LaunchRec<R>> wr;
+      std::vector<KArgs<R>> wa;
+      st = record_attempt(o.precond, wr, wa);
+      if (st != EGPE_OK) break;
+      const double t = time_seq(wr, wa);
+      if (st != EGPE_OK) break;
+      if (t < kGain * tr.ms_best) {
+        tr.ms_best = t;
+        tr.choice = w;
+      }
+    }
+    set_col_bytes(tr.choice);
+    if (st == EGPE_OK) out.push_back(tr);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -661,7 +728,7 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_x(KArgs<R> 
 
 template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R> a, const CUtensorMap* tm) {
   constexpr int L = Op::L, TPL = L / 8, NS = Op::NS;
-  const int M = col_tile_width<C>(L, nx);
+  const int M = col_tile_width<C>(L, nx, col_bytes_);
   a.M = M;
   const int block = M * TPL;
   EGPE_TRY(check_whole_warps(Op::NAME, L, block));
@@ -991,8 +1058,8 @@ template <class R> egpe_status Engine<R>::fft(const C* in, C* out, int nf, int i
     EGPE_TRY(plain_x(inverse, a));
     a.gin = out + (size_t)f * N;
     CUtensorMap my, mz;
-    const bool ok = use_tma_ && make_col_map<C>(my, out + (size_t)f * N, nx, ny, nz, 1, 1) &&
-                    make_col_map<C>(mz, out + (size_t)f * N, nx, ny, nz, 1, 2);
+    const bool ok = use_tma_ && make_col_map<C>(my, out + (size_t)f * N, nx, ny, nz, 1, 1, col_bytes_) &&
+                    make_col_map<C>(mz, out + (size_t)f * N, nx, ny, nz, 1, 2, col_bytes_);
     EGPE_TRY(plain_col(1, inverse, a, ok ? &my : nullptr));
     EGPE_TRY(plain_col(2, inverse, a, ok ? &mz : nullptr));
   }

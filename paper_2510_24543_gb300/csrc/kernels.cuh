@@ -257,24 +257,17 @@ __global__ void __launch_bounds__(MaxThreads<Op>::v, MinBlocks<Op>::v)
 // rest loading).
 constexpr int kColStages = EGPE_COL_STAGES;
 
-// Threads per block of a column pass: at most max(128 B / element, 32 / (L/8))
-// columns times L/8 threads.  The power-of-two lengths keep the 512 bound they
-// were tuned with; the mixed-radix lengths give the compiler the exact bound.
-#ifndef EGPE_COL_MINB
-#define EGPE_COL_MINB 1
-#endif
-#ifndef EGPE_COL_BYTES
-#define EGPE_COL_BYTES 128  // row width of a column-pass tile (see col_tile_width)
-#endif
-static_assert(EGPE_COL_MINB == 1 || EGPE_COL_BYTES == 128, "exact column bounds assume 128-byte tile rows");
+// Threads per block of a column pass.  The power-of-two lengths are bound to
+// 512 threads (tile rows of 64 to 256 bytes, chosen at run time); the
+// mixed-radix lengths keep 128-byte rows, max(128 B / element, whole warps)
+// columns times L/8 threads, and give the compiler that exact bound.
 template <class Op> struct ColMaxThreads {
   static constexpr int TPL = Op::L / 8;
   static constexpr int MC = (int)(128 / sizeof(C2<typename Op::R>));
   static constexpr int MW = whole_warp_rows(Op::L);
   static constexpr int exact = (MC > MW ? MC : MW) * TPL;
-  static constexpr int v = (IsPow2<Op::L>::v && EGPE_COL_MINB == 1) ? 512 : exact;
-  // resident blocks per SM the compiler is asked to allow for (caps registers)
-  static constexpr int minb = (EGPE_COL_MINB > 1 && exact <= 256) ? EGPE_COL_MINB : 1;
+  static constexpr int v = IsPow2<Op::L>::v ? 512 : exact;
+  static constexpr int minb = 1;
 };
 
 // ----------------------------------------------------------------------------
