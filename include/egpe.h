@@ -144,12 +144,12 @@ typedef struct {
   int max_iter_fp32;        /* MIXED: cap of the FP32 phase                         */
   int trace_cap;            /* entries available in trace (0: no trace)             */
   void* trace;              /* HOST array of egpe_trace_entry, or NULL              */
-  int batch;                /* n_inst > 1: 0 one instance after the other; 1 all
-                               instances together, one launch per pass for up to 16
-                               instances of one grid shape, the shapes' launches in
-                               sequence; 2 (default) as 1 with the launch chains of
-                               different grid shapes run as concurrent branches of
-                               the replayed graph                                 */
+  int batch;                /* n_inst > 1: 0 one instance after the other; 1
+                               (default) all instances together, one launch per
+                               pass for up to 16 instances of one grid shape, the
+                               shapes' launches in sequence; 2 as 1 with the
+                               launch chains of different grid shapes run as
+                               concurrent branches of the replayed graph           */
   int stall_iters_fp32;     /* FP32 fields (FP32 handles, MIXED's FP32 phase): stop
                                when the best ||r|| has not dropped by 10% within this
                                many iterations (its round-off floor); 0: off       */
@@ -424,8 +424,8 @@ egpe_status egpe_solver_read(egpe_handle* h, int inst, int engine, egpe_report* 
 /* Defaults: kinetic preconditioner, HS+, K_r = 20, tol_res 1e-8, c1 1e-4,
  * 30 halvings, theta_max = pi/2, accept_rtol 1e-13 (FP64) / 1e-6 (FP32),
  * pv_floor 1e-2, graph replay with polls every 8 attempts, MIXED switch at
- * ||r|| < 1e-4, no FP32 stall limit, batched instances with concurrent grid
- * shapes (batch = 2). */
+ * ||r|| < 1e-4, no FP32 stall limit, batched instances with the grid shapes'
+ * launches in sequence (batch = 1). */
 void egpe_default_solve_opts(egpe_solve_opts* opts);
 
 /* Human-readable status; never NULL. */

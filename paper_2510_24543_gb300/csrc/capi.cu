@@ -175,7 +175,7 @@ void egpe_default_solve_opts(egpe_solve_opts* o) {
   o->max_iter_fp32 = 2000;
   o->trace_cap = 0;
   o->trace = nullptr;
-  o->batch = 2;
+  o->batch = 1;
   o->stall_iters_fp32 = 0;
   o->pc_blend = 0.5;
 }
