@@ -2,8 +2,8 @@
 """Benchmark of the eGPE ground-state solver hot path on one GB300 per rank.
 
 Headline: NCG iterations per second on the 128^3 two-component dipolar eGPE
-(the stripe/supersolid couplings on [-16,16]^2 x [-8,8]) with FP32 fields and
-FP64 reductions/controller, the FP64 path timed beside it, time to ground
+(the stripe/supersolid couplings on [-16,16]^2 x [-8,8]) with FP32 fields, sums
+reduced to FP64 values and an FP64 controller, the FP64 path timed beside it, time to ground
 state (mixed vs FP64, relative energy 1e-8), and the HBM roofline of the
 dominant kernel.  One "step" is one attempt of the NCG loop body (precondition,
 line-search coefficients, trial energy/gradient, controller); steps are timed
@@ -425,7 +425,9 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, f64 reductions/controller",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "precision": "FP32 fields and transforms; sums reduced deterministically (float-float) to "
+                             "FP64 values; FP64 controller",
                 "data": "synthetic (seeded Gaussian + 1% noise start)",
                 "config": {"workload": w0.name + " on [-16,16]^2x[-8,8], trap (0.5,1,2), g=300/300/280, "
                                        "g_dd=420/420/400, LHY c=100",

@@ -6,8 +6,8 @@
  * correction (arXiv:2510.24543, Eq. 1) on a periodic 3D grid, with the
  * preconditioned nonlinear conjugate-gradient method of its Algorithm 1.
  * Every step runs in hand-written CUDA kernels (Stockham FFTs fused with the
- * k-space multiplies, fused pointwise passes, deterministic FP64 reductions,
- * an on-device controller).  No cuFFT and no host fallback.
+ * k-space multiplies, fused pointwise passes, deterministic reductions to FP64
+ * values, an on-device controller).  No cuFFT and no host fallback.
  *
  * Conventions shared by every entry point
  * ---------------------------------------

@@ -1,4 +1,5 @@
-// Engine<float>: FP32 fields and transforms with FP64 reductions and controller.
+// Engine<float>: FP32 fields and transforms; sums reduced deterministically
+// (float-float) to FP64 values for the FP64 controller.
 #include "batch.cuh"
 template class egpe::Engine<float>;
 template egpe_status egpe::batch_solve<float>(const std::vector<egpe::Engine<float>*>&, cudaStream_t,
