@@ -26,3 +26,22 @@ def test_reference_arm_prints_the_contract_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_record_follows_the_source_digest(tmp_path, monkeypatch):
+    """bench.py reports a kernel's ncu DRAM bytes only while the committed
+    summary carries the digest of the current CUDA sources and the workload."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2510_24543_gb300 import build as B
+
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    rec = {"kernels": {"k": {"workload": "c3p", "dram_bytes_per_launch": 1.5e8}}}
+    path = tmp_path / "profiles" / "traffic.json"
+    path.write_text(json.dumps({**rec, "sources": B._digest()}))
+    assert bench.traffic_record("k", "c3p") == 1.5e8
+    assert bench.traffic_record("k", "c1") is None
+    assert bench.traffic_record("other", "c3p") is None
+    path.write_text(json.dumps({**rec, "sources": "not the current sources"}))
+    assert bench.traffic_record("k", "c3p") is None
