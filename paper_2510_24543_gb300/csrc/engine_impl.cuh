@@ -742,16 +742,22 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
     auto it = tune_.find(typeid(Op).name());
     if (it != tune_.end()) tma = it->second != 0;
   }
+  // the default tile width runs the kernels compiled for it
+  constexpr int MD = ColDefaultM<Op>::v;
+  const bool cm = M == MD;
+  const void* fn_plain = cm ? (const void*)colpass_kernel<Op, MD> : (const void*)colpass_kernel<Op, 0>;
+  const void* fn_tma = cm ? (const void*)colpass_tma_kernel<Op, MD> : (const void*)colpass_tma_kernel<Op, 0>;
   if (rec_) {
-    if (tma) EGPE_TRY(record(a, tm, (const void*)colpass_tma_kernel_b<Op>, block, smem_tma, tiles));
-    else EGPE_TRY(record(a, nullptr, (const void*)colpass_kernel_b<Op>, block, smem_plain, tiles));
+    const void* fb = tma ? (cm ? (const void*)colpass_tma_kernel_b<Op, MD> : (const void*)colpass_tma_kernel_b<Op, 0>)
+                         : (cm ? (const void*)colpass_kernel_b<Op, MD> : (const void*)colpass_kernel_b<Op, 0>);
+    EGPE_TRY(record(a, tma ? tm : nullptr, fb, block, tma ? smem_tma : smem_plain, tiles));
     LaunchRec<R>& r = rec_->back();
     r.kind = 1;
     r.key = typeid(Op).name();
     r.name = Op::NAME;
     r.L = L;
-    r.fn1 = (const void*)colpass_kernel<Op>;
-    r.fn1_tma = (const void*)colpass_tma_kernel<Op>;
+    r.fn1 = fn_plain;
+    r.fn1_tma = fn_tma;
     r.tm = tm;  // kept for tuning even when this launch uses plain loads
     r.smem_plain = smem_plain;
     r.smem_tma = smem_tma;
@@ -760,17 +766,19 @@ template <class R> template <class Op> egpe_status Engine<R>::launch_col(KArgs<R
   }
   if (tma) {
     const size_t smem = smem_tma;
-    const int occ = occupancy((const void*)colpass_tma_kernel<Op>, block, smem);
+    const int occ = occupancy(fn_tma, block, smem);
     const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
     if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
-    colpass_tma_kernel<Op><<<grid, block, smem, stream>>>(*tm, a);
+    if (cm) colpass_tma_kernel<Op, MD><<<grid, block, smem, stream>>>(*tm, a);
+    else colpass_tma_kernel<Op, 0><<<grid, block, smem, stream>>>(*tm, a);
     if (timing_) t_end();
   } else {
     const size_t smem = smem_plain;
-    const int occ = occupancy((const void*)colpass_kernel<Op>, block, smem);
+    const int occ = occupancy(fn_plain, block, smem);
     const int grid = std::min(tiles, std::min(occ * nsm_, 16384));
     if (timing_) t_begin(Op::NAME, L, Op::alg_bytes(a));
-    colpass_kernel<Op><<<grid, block, smem, stream>>>(a);
+    if (cm) colpass_kernel<Op, MD><<<grid, block, smem, stream>>>(a);
+    else colpass_kernel<Op, 0><<<grid, block, smem, stream>>>(a);
     if (timing_) t_end();
   }
   ++kernels_;

@@ -72,13 +72,19 @@ template <int L> struct Plan<L, true> {
   }
 };
 
-struct ColIdx;
+template <int MC> struct ColIdxT;
+template <class SI> struct IsColIdx {
+  static constexpr bool v = false;
+};
+template <int MC> struct IsColIdx<ColIdxT<MC>> {
+  static constexpr bool v = true;
+};
 // Synchronisation of one transform's exchange buffer.  A row line's L/8
 // threads are consecutive and, for the power-of-two lengths (L/8 <= 32
 // dividing 32), inside one warp with a buffer of their own: a warp barrier
 // suffices.  Column lines spread over the block and need the block barrier.
 template <class SI> __device__ __forceinline__ void line_sync() {
-  if constexpr (std::is_same<SI, ColIdx>::value) __syncthreads();
+  if constexpr (IsColIdx<SI>::v) __syncthreads();
   else __syncwarp();
 }
 // Column lines (power-of-two lengths) exchange through two buffers in turn,
@@ -87,7 +93,7 @@ template <class SI> __device__ __forceinline__ void line_sync() {
 // thread reaches after its reads of the first.  Row lines reuse one buffer
 // with two warp barriers per exchange.
 template <class SI> struct PingPong {
-  static constexpr bool v = std::is_same<SI, ColIdx>::value;
+  static constexpr bool v = IsColIdx<SI>::v;
 };
 
 template <class C> __device__ __forceinline__ C mul_i(C a) { return cmk<C>(-a.y, a.x); }
@@ -323,17 +329,21 @@ __device__ __forceinline__ void fft_line(C (&v)[NF][8], C* sm, int fstride, cons
 template <int PADSHIFT> struct RowIdx {
   __device__ __forceinline__ int operator()(int pos) const { return pos + (pos >> PADSHIFT); }
 };
-struct ColIdx {
+// MC > 0: the tile width M is the compile-time constant MC (the default tile
+// rows), so the exchange offsets fold into the shared-memory instructions;
+// MC = 0: M at run time (the other tile widths).
+template <int MC> struct ColIdxT {
   int M;
   int alt;  // offset (elements) of the second exchange buffer from the first
-  __device__ __forceinline__ int operator()(int pos) const { return pos * M; }
+  __device__ __forceinline__ int operator()(int pos) const { return pos * (MC > 0 ? MC : M); }
 };
+using ColIdx = ColIdxT<0>;
 // A column transform of power-of-two length L makes P - 1 exchanges, the first
 // through the second buffer.  When that count is odd the transform ends having
 // written the second buffer last, so a following transform of the same line
 // starts with the roles of the buffers swapped (its first exchange then writes
 // the buffer whose last reads preceded the earlier barrier).
-template <int L, class C> __device__ __forceinline__ void col_after(C*& sm, ColIdx& si) {
+template <int L, class C, class SI> __device__ __forceinline__ void col_after(C*& sm, SI& si) {
   if constexpr (IsPow2<L>::v) {
     if constexpr (((Plan<L>::P - 1) & 1) != 0) {
       sm += si.alt;

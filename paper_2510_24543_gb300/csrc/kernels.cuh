@@ -270,28 +270,50 @@ template <class Op> struct ColMaxThreads {
   static constexpr int minb = 1;
 };
 
+// Columns per tile at the default 128-byte tile rows (what the host picks for
+// every grid while the column tile width is untuned): the kernels for this
+// width take it as a compile-time constant.
+template <class Op> struct ColDefaultM {
+  static constexpr int TPL = Op::L / 8;
+  static constexpr int MB = (int)(128 / sizeof(C2<typename Op::R>));
+  static constexpr int M0 = IsPow2<Op::L>::v ? (MB < 512 / TPL ? MB : 512 / TPL) : MB;
+  static constexpr int v = M0 > whole_warp_rows(Op::L) ? M0 : whole_warp_rows(Op::L);
+};
+// Launch bounds of a column kernel: the run-time width keeps ColMaxThreads; a
+// compile-time width MC has exactly MC L/8 threads, and the FP32 plain y/z
+// passes (the ColPlain op, small epilogue) of up to 256 threads ask for three
+// resident blocks, as their run-time-width build reached without a bound.
+template <class Op> struct ColMinB {
+  static constexpr int v = 1;
+};
+template <class Op, int MC> struct ColBounds {
+  static constexpr int threads = MC > 0 ? MC * (Op::L / 8) : ColMaxThreads<Op>::v;
+  static constexpr int minb = MC > 0 && threads <= 256 ? ColMinB<Op>::v : ColMaxThreads<Op>::minb;
+};
+
 // ----------------------------------------------------------------------------
 // Column (y or z) pass kernel
 // ----------------------------------------------------------------------------
-template <class Op> __device__ __forceinline__ void colpass_body(const KArgs<typename Op::R>& a) {
+template <class Op, int MC> __device__ __forceinline__ void colpass_body(const KArgs<typename Op::R>& a) {
   using R = typename Op::R;
   using C = C2<R>;
   constexpr int L = Op::L, NS = Op::NS;
   constexpr int NSR = NS > 0 ? NS : 1;
   if (!gate_open(a)) return;
+  const int M = MC > 0 ? MC : a.M;  // columns per tile
   extern __shared__ __align__(16) unsigned char smraw[];
   C* tw = reinterpret_cast<C*>(smraw);
   C* buf = tw + L;  // two exchange buffers of M lines each
-  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(buf + 2 * a.M * L);
+  RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(buf + 2 * M * L);
   const int tid = threadIdx.x;
-  const int m = tid % a.M, t = tid / a.M;
+  const int m = tid % M, t = tid / M;
   const C* twsrc = (Op::AXIS == 1) ? a.twy : a.twz;
   for (int i = tid; i < L; i += blockDim.x) tw[i] = twsrc[i];
   __syncthreads();
   typename Op::Uni u;
   Op::uniform(a, u);
   PAcc<R> acc[NSR];
-  const int xb_n = a.nx / a.M;
+  const int xb_n = a.nx / M;
   const int other_n = (Op::AXIS == 1) ? a.nz : a.ny;
   const int tiles = xb_n * other_n * a.nf;
   const size_t lstride = (Op::AXIS == 1) ? (size_t)a.nx : (size_t)a.nx * a.ny;
@@ -300,13 +322,13 @@ template <class Op> __device__ __forceinline__ void colpass_body(const KArgs<typ
     const int rest = tile / xb_n;
     const int o = rest % other_n;
     const int f = a.f0 + rest / other_n;
-    const int x = xb * a.M + m;
+    const int x = xb * M + m;
     const size_t base = (size_t)f * a.N + (Op::AXIS == 1 ? (size_t)o * a.nx * a.ny : (size_t)o * a.nx) + x;
     const C* src = Op::src(a);
     C v[1][8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[0][e] = src[base + (size_t)Plan<L>::entry_pos(Op::FIRST_INV, t, e) * lstride];
-    Op::process(a, u, f, x, o, base, lstride, t, v, buf + m, tw, ColIdx{a.M, a.M * L}, acc);
+    Op::process(a, u, f, x, o, base, lstride, t, v, buf + m, tw, ColIdxT<MC>{M, M * L}, acc);
     // the last exchange's reads end before the next tile's first writes
     if constexpr (IsPow2<L>::v) __syncthreads();
   }
@@ -316,14 +338,15 @@ template <class Op> __device__ __forceinline__ void colpass_body(const KArgs<typ
     }
   }
 }
-template <class Op>
-__global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb) colpass_kernel(KArgs<typename Op::R> a) {
-  colpass_body<Op>(a);
+template <class Op, int MC = 0>
+__global__ void __launch_bounds__(ColBounds<Op, MC>::threads, ColBounds<Op, MC>::minb)
+    colpass_kernel(KArgs<typename Op::R> a) {
+  colpass_body<Op, MC>(a);
 }
-template <class Op>
-__global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
+template <class Op, int MC = 0>
+__global__ void __launch_bounds__(ColBounds<Op, MC>::threads, ColBounds<Op, MC>::minb)
     colpass_kernel_b(const __grid_constant__ KBatch<typename Op::R> kb) {
-  colpass_body<Op>(kb.k[blockIdx.y]);
+  colpass_body<Op, MC>(kb.k[blockIdx.y]);
 }
 
 // ----------------------------------------------------------------------------
@@ -334,7 +357,7 @@ __global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
 // is already loading into the other buffer.  Results go straight to global
 // memory from registers.
 // ----------------------------------------------------------------------------
-template <class Op>
+template <class Op, int MC>
 __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KArgs<typename Op::R>& a) {
   using R = typename Op::R;
   using C = C2<R>;
@@ -342,15 +365,16 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
   constexpr int NSR = NS > 0 ? NS : 1;
   constexpr int NST = kColStages;
   if (!gate_open(a)) return;
+  const int M = MC > 0 ? MC : a.M;  // columns per tile
   extern __shared__ __align__(128) unsigned char smraw_tma[];
-  const int tileC = a.M * L;
+  const int tileC = M * L;
   C* tiles = reinterpret_cast<C*>(smraw_tma);  // NST tiles, then the second exchange buffer
   C* xbuf = tiles + NST * tileC;
   C* tw = xbuf + tileC;
   uint64_t* bar = reinterpret_cast<uint64_t*>(tw + L);
   RedSmem<NSR>* red = reinterpret_cast<RedSmem<NSR>*>(bar + NST);
   const int tid = threadIdx.x;
-  const int m = tid % a.M, t = tid / a.M;
+  const int m = tid % M, t = tid / M;
   const C* twsrc = (Op::AXIS == 1) ? a.twy : a.twz;
   for (int i = tid; i < L; i += blockDim.x) tw[i] = twsrc[i];
   if (tid == 0) {
@@ -362,7 +386,7 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
   typename Op::Uni u;
   Op::uniform(a, u);
   PAcc<R> acc[NSR];
-  const int xb_n = a.nx / a.M;
+  const int xb_n = a.nx / M;
   const int other_n = (Op::AXIS == 1) ? a.nz : a.ny;
   const int tiles_n = xb_n * other_n * a.nf;
   const size_t lstride = (Op::AXIS == 1) ? (size_t)a.nx : (size_t)a.nx * a.ny;
@@ -373,7 +397,7 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     const int rest = tile / xb_n;
     const int o = rest % other_n;
     const int f = a.f0 + rest / other_n;
-    const int c0 = xb * a.M * ESZ;
+    const int c0 = xb * M * ESZ;
     const int c1 = (Op::AXIS == 1) ? 0 : o;
     const int c2 = (Op::AXIS == 1) ? f * a.nz + o : f * a.nz;
     fence_proxy_async();
@@ -403,7 +427,7 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     C* tb = tiles + b * tileC;
     C v[1][8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[0][e] = tb[Plan<L>::entry_pos(Op::FIRST_INV, t, e) * a.M + m];
+    for (int e = 0; e < 8; ++e) v[0][e] = tb[Plan<L>::entry_pos(Op::FIRST_INV, t, e) * M + m];
     // power-of-two lengths exchange through the second buffer first, and the
     // barrier of that exchange orders these reads before the tile's reuse;
     // the mixed-radix passes work in place in the tile
@@ -412,9 +436,9 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     const int rest = tile / xb_n;
     const int o = rest % other_n;
     const int f = a.f0 + rest / other_n;
-    const int x = xb * a.M + m;
+    const int x = xb * M + m;
     const size_t base = (size_t)f * a.N + (Op::AXIS == 1 ? (size_t)o * a.nx * a.ny : (size_t)o * a.nx) + x;
-    Op::process(a, u, f, x, o, base, lstride, t, v, tb + m, tw, ColIdx{a.M, (int)(xbuf - tb)}, acc);
+    Op::process(a, u, f, x, o, base, lstride, t, v, tb + m, tw, ColIdxT<MC>{M, (int)(xbuf - tb)}, acc);
     __syncthreads();  // buffer b may be refilled, and the second buffer rewritten, from here on
   }
   if (timed_out) {
@@ -435,15 +459,15 @@ __device__ __forceinline__ void colpass_tma_body(const CUtensorMap* tm, const KA
     }
   }
 }
-template <class Op>
-__global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
+template <class Op, int MC = 0>
+__global__ void __launch_bounds__(ColBounds<Op, MC>::threads, ColBounds<Op, MC>::minb)
     colpass_tma_kernel(const __grid_constant__ CUtensorMap tm, KArgs<typename Op::R> a) {
-  colpass_tma_body<Op>(&tm, a);
+  colpass_tma_body<Op, MC>(&tm, a);
 }
-template <class Op>
-__global__ void __launch_bounds__(ColMaxThreads<Op>::v, ColMaxThreads<Op>::minb)
+template <class Op, int MC = 0>
+__global__ void __launch_bounds__(ColBounds<Op, MC>::threads, ColBounds<Op, MC>::minb)
     colpass_tma_kernel_b(const __grid_constant__ KBatch<typename Op::R> kb) {
-  colpass_tma_body<Op>(&kb.tm[blockIdx.y], kb.k[blockIdx.y]);
+  colpass_tma_body<Op, MC>(&kb.tm[blockIdx.y], kb.k[blockIdx.y]);
 }
 
 struct NoUni {};
@@ -486,14 +510,18 @@ template <class R_, int L_, int AXIS_, bool INV_> struct ColPlain {
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
   static constexpr bool FIRST_INV = INV_;
   static __device__ const C* src(const KArgs<R>& a) { return a.gin; }
+  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int, int, int, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
+                                 C (&v)[1][8], C* sm, const C* tw, SI si, PAcc<R>*) {
     fft_line<C, L, INV, 1>(v, sm, 0, tw, t, si);
 #pragma unroll
     for (int e = 0; e < 8; ++e) a.gout[base + (size_t)Plan<L>::exit_pos(INV, t, e) * ls] = v[0][e];
   }
   static __device__ double* out(const KArgs<R>&, Uni&) { return nullptr; }
   static __device__ void finish(const KArgs<R>&, Uni&) {}
+};
+template <int L_, int AXIS_, bool INV_> struct ColMinB<ColPlain<float, L_, AXIS_, INV_>> {
+  static constexpr int v = 3;
 };
 
 // ----------------------------------------------------------------------------
@@ -608,8 +636,9 @@ template <class R_, int L_> struct ZEg {
   }
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>* acc) {
+                                 C (&v)[1][8], C* sm, const C* tw, SI si, PAcc<R>* acc) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -968,8 +997,9 @@ template <class R_, int L_> struct ZPc {
   }
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni& u, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
+                                 C (&v)[1][8], C* sm, const C* tw, SI si, PAcc<R>*) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -1207,8 +1237,9 @@ template <class R_, int L_> struct ZLc {
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int f, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>* acc) {
+                                 C (&v)[1][8], C* sm, const C* tw, SI si, PAcc<R>* acc) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
@@ -1406,8 +1437,9 @@ template <class R_, int L_> struct ZKin {
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
+                                 C (&v)[1][8], C* sm, const C* tw, SI si, PAcc<R>*) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R exy = a.kin_tab[x] * a.kin_tab[a.nx + y] * a.invN;
 #pragma unroll
@@ -1537,8 +1569,9 @@ template <class R_, int L_> struct ZPg {
   static __device__ void uniform(const KArgs<R>&, Uni&) {}
   static constexpr bool FIRST_INV = false;
   static __device__ const C* src(const KArgs<R>& a) { return a.W; }
+  template <class SI>
   static __device__ void process(const KArgs<R>& a, Uni&, int, int x, int y, size_t base, size_t ls, int t,
-                                 C (&v)[1][8], C* sm, const C* tw, ColIdx si, PAcc<R>*) {
+                                 C (&v)[1][8], C* sm, const C* tw, SI si, PAcc<R>*) {
     fft_line<C, L, false, 1>(v, sm, 0, tw, t, si);
     const R kx = wavenum<R>(x, a.nx, a.dkx), ky = wavenum<R>(y, a.ny, a.dky);
     const R kxy2 = kx * kx + ky * ky;
